@@ -1,0 +1,284 @@
+"""Oracle: plain, slow, single-threaded FP64 CPU implementation of the method.
+
+TEST INFRASTRUCTURE ONLY.  The test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product library
+(``paper_2005_09323_gb300``) never imports this package, and this package never
+imports the product: they share no code.
+
+The C sources (``oracle/*.c``) follow the paper's appendices step by step; see
+the header comment of each file for the passage it restates.  This module only
+compiles them (``build()``) and marshals numpy arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SOURCES = ["philox.c", "lbm.c", "select.c", "ou.c"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C sources into ``oracle/liboracle.so`` (gcc, -O2, IEEE FP64:
+    no contraction into fused multiply-adds, so x86 and Arm hosts round alike)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(_SO):
+        so_m = os.path.getmtime(_SO)
+        if all(os.path.getmtime(s) <= so_m for s in srcs):
+            return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           *[os.path.join(_HERE, s) for s in _SOURCES], "-lm", "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        d, i32, i64, u64, p = C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p
+        L.orc_philox4x64.argtypes = [p, p, p]
+        L.orc_u01.argtypes = [u64]; L.orc_u01.restype = d
+        L.orc_below.argtypes = [u64, u64]; L.orc_below.restype = u64
+        L.orc_feq.argtypes = [d, d, d, p]
+        L.orc_guo.argtypes = [d, d, d, d, p]
+        L.orc_init.argtypes = [p, u64, i32, d, p]
+        L.orc_step.argtypes = [p, p, p, p, p]
+        L.orc_run.argtypes = [p, p, p, i32, p]
+        L.orc_moments.argtypes = [p, p, p, p, p]
+        L.orc_macro.argtypes = [p, p, p, p, p]
+        L.orc_is_solid.argtypes = [p, C.c_int, C.c_int]; L.orc_is_solid.restype = C.c_int
+        L.orc_perturb_alphas.argtypes = [u64, u64, i32, i32, p]
+        L.orc_perturb.argtypes = [p, p, i32, p, p, d, p]
+        L.orc_gktl_weights.argtypes = [i32, p, p, p]; L.orc_gktl_weights.restype = C.c_int
+        L.orc_gktl_select.argtypes = [i32, p, u64, u64, p]; L.orc_gktl_select.restype = C.c_int
+        L.orc_ams_select.argtypes = [i32, p, u64, u64, p, p, p, p]; L.orc_ams_select.restype = C.c_int
+        L.orc_ou_noise.argtypes = [u64, u64, u64, u64]; L.orc_ou_noise.restype = d
+        L.orc_ou_gktl.argtypes = [i32, i32, i32, d, d, u64, p, i32, p]; L.orc_ou_gktl.restype = d
+        L.orc_ou_direct_max.argtypes = [i64, i32, d, u64, i32, p, p]
+        L.orc_ou_ams.argtypes = [i32, i32, d, d, i32, u64, p]; L.orc_ou_ams.restype = d
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Cfg(C.Structure):
+    """Mirror of ``orc_cfg``: channel nx x ny, solid cells [ox0,ox0+ow) x [oy0,oy0+oh)."""
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ox0", C.c_int32), ("oy0", C.c_int32),
+                ("ow", C.c_int32), ("oh", C.c_int32), ("tau", C.c_double), ("gx", C.c_double),
+                ("gy", C.c_double)]
+
+
+def cfg(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0) -> Cfg:
+    ox0, oy0, ow, oh = obstacle
+    return Cfg(nx, ny, ox0, oy0, ow, oh, tau, gx, gy)
+
+
+# ---------------------------------------------------------------- rng
+def philox4x64(ctr, key):
+    c = np.asarray(ctr, dtype=np.uint64).copy()
+    k = np.asarray(key, dtype=np.uint64).copy()
+    o = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64(_ptr(c), _ptr(k), _ptr(o))
+    return o
+
+
+def u01(x: int) -> float:
+    return lib().orc_u01(int(x))
+
+
+def below(x: int, m: int) -> int:
+    return lib().orc_below(int(x), int(m))
+
+
+# ---------------------------------------------------------------- lbm
+def feq(rho, ux, uy):
+    o = np.zeros(9)
+    lib().orc_feq(rho, ux, uy, _ptr(o))
+    return o
+
+
+def guo(ux, uy, gx, gy):
+    o = np.zeros(9)
+    lib().orc_guo(ux, uy, gx, gy, _ptr(o))
+    return o
+
+
+def init(c: Cfg, seed: int, clone: int, amp: float) -> np.ndarray:
+    f = np.zeros((9, c.ny, c.nx))
+    lib().orc_init(C.byref(c), seed, clone, amp, _ptr(f))
+    return f
+
+
+def step(c: Cfg, f: np.ndarray):
+    """One step; returns (f_new, force_on_obstacle[2], force_on_walls[2])."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.empty_like(f)
+    fo = np.zeros(2)
+    fw = np.zeros(2)
+    lib().orc_step(C.byref(c), _ptr(f), _ptr(out), _ptr(fo), _ptr(fw))
+    return out, fo, fw
+
+
+def run(c: Cfg, f: np.ndarray, n: int):
+    """n steps; returns (f_final, drag[n]) with drag[t] the x-force after step t+1."""
+    f = np.ascontiguousarray(f, dtype=np.float64).copy()
+    scratch = np.empty_like(f)
+    drag = np.zeros(max(n, 1))
+    lib().orc_run(C.byref(c), _ptr(f), _ptr(scratch), n, _ptr(drag))
+    return f, drag[:n]
+
+
+def moments(c: Cfg, f: np.ndarray):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    m, px, py = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_moments(C.byref(c), _ptr(f), C.byref(m), C.byref(px), C.byref(py))
+    return m.value, px.value, py.value
+
+
+def macro(c: Cfg, f: np.ndarray):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    rho = np.zeros((c.ny, c.nx)); ux = np.zeros_like(rho); uy = np.zeros_like(rho)
+    lib().orc_macro(C.byref(c), _ptr(f), _ptr(rho), _ptr(ux), _ptr(uy))
+    return rho, ux, uy
+
+
+def solid_mask(c: Cfg) -> np.ndarray:
+    m = np.zeros((c.ny, c.nx), dtype=bool)
+    if c.ow > 0:
+        m[c.oy0:c.oy0 + c.oh, c.ox0:c.ox0 + c.ow] = True
+    return m
+
+
+def perturb_alphas(seed, it, slot, n_s):
+    a = np.zeros(n_s)
+    lib().orc_perturb_alphas(seed, it, slot, n_s, _ptr(a))
+    return a
+
+
+def perturb(c: Cfg, f, snaps, alpha, eps):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    snaps = np.ascontiguousarray(snaps, dtype=np.float64)
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    out = np.empty_like(f)
+    lib().orc_perturb(C.byref(c), _ptr(f), int(len(alpha)), _ptr(snaps), _ptr(alpha), eps, _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------- selection
+def gktl_weights(s):
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    W = np.zeros_like(s)
+    logR = C.c_double()
+    rc = lib().orc_gktl_weights(len(s), _ptr(s), _ptr(W), C.byref(logR))
+    if rc != 0:
+        raise ValueError(f"orc_gktl_weights: status {rc}")
+    return W, logR.value
+
+
+def gktl_select(W, seed, it):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    parent = np.zeros(len(W), dtype=np.int32)
+    rc = lib().orc_gktl_select(len(W), _ptr(W), seed, it, _ptr(parent))
+    if rc != 0:
+        raise ValueError(f"orc_gktl_select: status {rc}")
+    return parent
+
+
+def ams_select(Q, seed, it):
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    n = len(Q)
+    killed = np.zeros(n, dtype=np.int32)
+    surv = np.zeros(n, dtype=np.int32)
+    nk = C.c_int32()
+    z = C.c_double()
+    rc = lib().orc_ams_select(n, _ptr(Q), seed, it, _ptr(killed), C.byref(nk), _ptr(surv), C.byref(z))
+    if rc != 0:
+        raise ValueError(f"orc_ams_select: status {rc}")
+    k = nk.value
+    return killed[:k].copy(), (surv[:k].copy() if k < n else np.zeros(0, np.int32)), z.value
+
+
+# ---------------------------------------------------------------- OU test process
+def ou_gktl(n, n_periods, steps_per_period, dt, k, seed, window_steps=0):
+    fi = np.zeros(n)
+    mm = np.zeros(n)
+    logZ = lib().orc_ou_gktl(n, n_periods, steps_per_period, dt, k, seed, _ptr(fi), window_steps,
+                             _ptr(mm) if window_steps > 0 else None)
+    return logZ, fi, (mm if window_steps > 0 else None)
+
+
+def ou_direct_max(n, n_steps, dt, seed, levels):
+    levels = np.ascontiguousarray(levels, dtype=np.float64)
+    frac = np.zeros_like(levels)
+    lib().orc_ou_direct_max(n, n_steps, dt, seed, len(levels), _ptr(levels), _ptr(frac))
+    return frac
+
+
+def ou_ams(n, n_steps, dt, a, j_max, seed):
+    it = C.c_int32()
+    p = lib().orc_ou_ams(n, n_steps, dt, a, j_max, seed, C.byref(it))
+    return p, it.value
+
+
+# ---------------------------------------------------------------- observables & estimators
+def window_sum(drag: np.ndarray, t0: int, t1: int, k: float) -> np.ndarray:
+    """GKTL exponent of eq. (Weight): k times the time integral of the drag over
+    steps t0 < t <= t1 (dt = 1 lattice step), per trajectory.  drag[n, t-1] is the
+    drag after step t."""
+    return k * np.sum(np.asarray(drag, dtype=np.float64)[:, t0:t1], axis=1)
+
+
+def trailing_mean_max(drag: np.ndarray, window: int, t_end: int | None = None) -> np.ndarray:
+    """max over t in [window, t_end] of (1/window) sum_{s=t-window+1}^{t} drag(s):
+    the time-averaged drag F_T of eq. (def_time_averaged_drag) with T = window
+    steps, maximised along each trajectory (AMS score maximum Q_n; GKTL event
+    amplitude).  -inf when t_end < window."""
+    d = np.asarray(drag, dtype=np.float64)
+    if t_end is None:
+        t_end = d.shape[1]
+    out = np.full(d.shape[0], -np.inf)
+    for n in range(d.shape[0]):
+        for t in range(window, t_end + 1):
+            m = np.sum(d[n, t - window:t]) / window
+            if m > out[n]:
+                out[n] = m
+    return out
+
+
+def gktl_probability(log_z: float, k: float, integrals: np.ndarray, maxima: np.ndarray,
+                     levels: np.ndarray) -> np.ndarray:
+    """App. C.2: P(F_T >= a) ~ (1/N) sum_j Z e^{-k int_0^{T_a} A_j} 1{max F_T^(j) >= a},
+    the biased path measure of eq. (Biased_Path_Approximation) inverted (the
+    printed exponent's sign is read as the inversion requires)."""
+    integrals = np.asarray(integrals, dtype=np.float64)
+    maxima = np.asarray(maxima, dtype=np.float64)
+    w = np.exp(log_z - k * integrals)
+    return np.array([np.sum(w * (maxima >= a)) / len(w) for a in np.atleast_1d(levels)])
+
+
+def return_time(p: np.ndarray, t_a: float, t_window: float) -> np.ndarray:
+    """App. C.2: r(a) = -(T_a - T) / ln(1 - P(F_T >= a))."""
+    p = np.asarray(p, dtype=np.float64)
+    with np.errstate(divide="ignore"):
+        return -(t_a - t_window) / np.log1p(-p)
+
+
+def ams_probability(log_weight: float, maxima: np.ndarray, level: float) -> float:
+    """Generalised AMS estimator: prod_j (1 - |K_j|/N) times the fraction of the
+    final ensemble whose maximum reaches the level."""
+    maxima = np.asarray(maxima, dtype=np.float64)
+    return float(np.exp(log_weight) * np.mean(maxima >= level))

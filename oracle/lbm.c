@@ -1,0 +1,234 @@
+/*
+ * Oracle (test infrastructure): D2Q9 lattice-BGK channel flow, FP64, one thread.
+ *
+ * Follows App. A of the paper step by step:
+ *   moments            rho = sum_i f_i,  rho u = sum_i f_i c_i
+ *   exact streaming    f_i(x + c_i, t+1) = f_i^out(x, t)
+ *   BGK collision      f_i^out = f_i - (f_i - f_i^eq) / tau
+ *                      (the printed formula lacks the leading f_i; the
+ *                      viscosity nu = (tau - 1/2) c_s^2 fixes this reading)
+ *   equilibrium        w_i rho (1 + u.c_i/cs2 + u_a u_b (c_ia c_ib - cs2 d_ab)/(2 cs2^2)),
+ *                      w = 4/9, 1/9 (axis), 1/36 (diagonal), cs2 = 1/3
+ * and Sec. 2: halfway bounce-back no-slip on the channel walls and on the square
+ * obstacle.  The channel is periodic in x and driven by a constant body-force
+ * density F on fluid nodes through the forcing scheme of Guo, Zheng & Shi
+ * (Phys. Rev. E 65, 046308, 2002): the velocity carries half the force,
+ *   rho u = sum_i f_i c_i + F/2,
+ * and the collision adds (1 - 1/(2 tau)) S_i with
+ *   S_i = w_i [ (c_i - u)/cs2 + (c_i.u) c_i / cs2^2 ] . F.
+ * The force on the obstacle is the momentum exchanged by the links that are
+ * bounced back at the next streaming step, 2 c_i f_i^out over fluid nodes x and
+ * directions i with x + c_i inside the obstacle: the surface integral of the
+ * stress of eq. (drag_definition) for the halfway bounce-back surface.
+ */
+#include "oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* D2Q9 velocities: rest, four axis links, four diagonal links */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                            1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+static const double CS2 = 1.0 / 3.0;
+
+#define IDX(c, q, x, y) ((((size_t)(q)) * (c)->ny + (size_t)(y)) * (c)->nx + (size_t)(x))
+
+int orc_is_solid(const orc_cfg* c, int x, int y)
+{
+    return c->ow > 0 && x >= c->ox0 && x < c->ox0 + c->ow && y >= c->oy0 && y < c->oy0 + c->oh;
+}
+
+void orc_feq(double rho, double ux, double uy, double feq[9])
+{
+    for (int i = 0; i < 9; ++i) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        double quad = 0.0; /* u_a u_b (c_ia c_ib - cs2 delta_ab) */
+        quad += ux * ux * (CX[i] * CX[i] - CS2);
+        quad += 2.0 * ux * uy * (CX[i] * CY[i]);
+        quad += uy * uy * (CY[i] * CY[i] - CS2);
+        feq[i] = W[i] * rho * (1.0 + cu / CS2 + quad / (2.0 * CS2 * CS2));
+    }
+}
+
+void orc_guo(double ux, double uy, double gx, double gy, double S[9])
+{
+    for (int i = 0; i < 9; ++i) {
+        double cu = CX[i] * ux + CY[i] * uy;
+        double ax = (CX[i] - ux) / CS2 + cu * CX[i] / (CS2 * CS2);
+        double ay = (CY[i] - uy) / CS2 + cu * CY[i] / (CS2 * CS2);
+        S[i] = W[i] * (ax * gx + ay * gy);
+    }
+}
+
+void orc_init(const orc_cfg* c, uint64_t seed, int32_t clone, double amp, double* f)
+{
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            double feq[9];
+            if (orc_is_solid(c, x, y)) {
+                for (int i = 0; i < 9; ++i) feq[i] = W[i];
+            } else {
+                uint64_t site = (uint64_t)y * (uint64_t)c->nx + (uint64_t)x;
+                uint64_t ctr[4] = {5u, (uint64_t)clone, site, 0u}, key[2] = {seed, 0u}, o[4];
+                orc_philox4x64(ctr, key, o);
+                double ux = amp * (2.0 * orc_u01(o[0]) - 1.0);
+                double uy = amp * (2.0 * orc_u01(o[1]) - 1.0);
+                orc_feq(1.0, ux, uy, feq);
+            }
+            for (int i = 0; i < 9; ++i) f[IDX(c, i, x, y)] = feq[i];
+        }
+}
+
+void orc_macro(const orc_cfg* c, const double* f, double* rho, double* ux, double* uy)
+{
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            double r = 0, jx = 0, jy = 0;
+            for (int i = 0; i < 9; ++i) {
+                double v = f[IDX(c, i, x, y)];
+                r += v;
+                jx += v * CX[i];
+                jy += v * CY[i];
+            }
+            /* the stored populations are post-collision: their momentum carries
+             * the whole force of the step, the fluid velocity half of it */
+            size_t s = (size_t)y * c->nx + x;
+            rho[s] = r;
+            ux[s] = (jx - 0.5 * c->gx) / r;
+            uy[s] = (jy - 0.5 * c->gy) / r;
+        }
+}
+
+static void link_forces(const orc_cfg* c, const double* f, double* fo, double* fw)
+{
+    double ox = 0, oy = 0, wx = 0, wy = 0;
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            if (orc_is_solid(c, x, y)) continue;
+            for (int i = 1; i < 9; ++i) {
+                int xn = ((x + CX[i]) % c->nx + c->nx) % c->nx;
+                int yn = y + CY[i];
+                double v = f[IDX(c, i, x, y)];
+                if (yn < 0 || yn >= c->ny) {
+                    wx += 2.0 * CX[i] * v;
+                    wy += 2.0 * CY[i] * v;
+                } else if (orc_is_solid(c, xn, yn)) {
+                    ox += 2.0 * CX[i] * v;
+                    oy += 2.0 * CY[i] * v;
+                }
+            }
+        }
+    if (fo) { fo[0] = ox; fo[1] = oy; }
+    if (fw) { fw[0] = wx; fw[1] = wy; }
+}
+
+void orc_step(const orc_cfg* c, const double* fin, double* fout, double* force_obs, double* force_wall)
+{
+    const int nx = c->nx, ny = c->ny;
+    /* 1. streaming into fout, links into a wall or the obstacle reflect back
+     *    into the opposite direction at the same node */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (orc_is_solid(c, x, y)) continue;
+            for (int i = 0; i < 9; ++i) {
+                int xn = ((x + CX[i]) % nx + nx) % nx;
+                int yn = y + CY[i];
+                double v = fin[IDX(c, i, x, y)];
+                if (yn < 0 || yn >= ny || orc_is_solid(c, xn, yn))
+                    fout[IDX(c, OPP[i], x, y)] = v;
+                else
+                    fout[IDX(c, i, xn, yn)] = v;
+            }
+        }
+    /* 2. collision at every fluid node; solid nodes hold the rest weights */
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            if (orc_is_solid(c, x, y)) {
+                for (int i = 0; i < 9; ++i) fout[IDX(c, i, x, y)] = W[i];
+                continue;
+            }
+            double f[9], rho = 0, jx = 0, jy = 0;
+            for (int i = 0; i < 9; ++i) {
+                f[i] = fout[IDX(c, i, x, y)];
+                rho += f[i];
+                jx += f[i] * CX[i];
+                jy += f[i] * CY[i];
+            }
+            double ux = (jx + 0.5 * c->gx) / rho;
+            double uy = (jy + 0.5 * c->gy) / rho;
+            double feq[9], S[9];
+            orc_feq(rho, ux, uy, feq);
+            orc_guo(ux, uy, c->gx, c->gy, S);
+            for (int i = 0; i < 9; ++i)
+                fout[IDX(c, i, x, y)] = f[i] - (f[i] - feq[i]) / c->tau + (1.0 - 1.0 / (2.0 * c->tau)) * S[i];
+        }
+    /* 3. momentum exchanged with the obstacle and the walls by the links that
+     *    the next streaming step bounces back */
+    if (force_obs || force_wall) link_forces(c, fout, force_obs, force_wall);
+}
+
+void orc_run(const orc_cfg* c, double* f, double* scratch, int32_t n, double* drag)
+{
+    size_t sz = (size_t)9 * c->nx * c->ny;
+    for (int32_t t = 0; t < n; ++t) {
+        double fo[2];
+        orc_step(c, f, scratch, drag ? fo : NULL, NULL);
+        memcpy(f, scratch, sz * sizeof(double));
+        if (drag) drag[t] = fo[0];
+    }
+}
+
+void orc_moments(const orc_cfg* c, const double* f, double* mass, double* px, double* py)
+{
+    double m = 0, jx = 0, jy = 0;
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            if (orc_is_solid(c, x, y)) continue;
+            for (int i = 0; i < 9; ++i) {
+                double v = f[IDX(c, i, x, y)];
+                m += v;
+                jx += v * CX[i];
+                jy += v * CY[i];
+            }
+        }
+    if (mass) *mass = m;
+    if (px) *px = jx;
+    if (py) *py = jy;
+}
+
+void orc_perturb_alphas(uint64_t seed, uint64_t iter, int32_t slot, int32_t n_s, double* alpha)
+{
+    for (int32_t n = 0; n < n_s; ++n) {
+        uint64_t ctr[4] = {4u, iter, (uint64_t)slot, (uint64_t)n}, key[2] = {seed, 0u}, o[4];
+        orc_philox4x64(ctr, key, o);
+        alpha[n] = orc_u01(o[0]);
+    }
+}
+
+/* App. D, eq. (perturb_pop): add a random combination of snapshots, then
+ * rescale so that the mass of the fluid is that of the unperturbed state */
+void orc_perturb(const orc_cfg* c, const double* f, int32_t n_s, const double* snaps,
+                 const double* alpha, double eps, double* f_out)
+{
+    size_t sz = (size_t)9 * c->nx * c->ny;
+    double m_before, m_after;
+    orc_moments(c, f, &m_before, NULL, NULL);
+    for (size_t k = 0; k < sz; ++k) {
+        double v = f[k];
+        for (int32_t n = 0; n < n_s; ++n) v += eps * alpha[n] * snaps[(size_t)n * sz + k];
+        f_out[k] = v;
+    }
+    orc_moments(c, f_out, &m_after, NULL, NULL);
+    double scale = m_before / m_after;
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x)
+            for (int i = 0; i < 9; ++i) {
+                if (orc_is_solid(c, x, y))
+                    f_out[IDX(c, i, x, y)] = W[i];
+                else
+                    f_out[IDX(c, i, x, y)] *= scale;
+            }
+}

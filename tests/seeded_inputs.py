@@ -1,0 +1,44 @@
+"""Seeded synthetic inputs shared by the oracle tests and the GPU parity tests.
+
+This module holds no arithmetic of the method: it only draws numbers
+(weights, scores, populations) from numpy generators with fixed seeds, so the
+same inputs can be fed to both implementations.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def log_weights(n: int, seed: int, spread: float = 1.0) -> np.ndarray:
+    """GKTL exponents s_n = k * integral, Gaussian with the given spread."""
+    return rng(seed).normal(0.0, spread, size=n)
+
+
+def normalised_weights(n: int, seed: int, spread: float = 1.0) -> np.ndarray:
+    """Positive weights scaled so that they sum to n (the selection input)."""
+    s = log_weights(n, seed, spread)
+    e = np.exp(s - s.max())
+    return n * e / e.sum()
+
+
+def scores(n: int, seed: int, n_ties: int = 0) -> np.ndarray:
+    """AMS maximum scores; n_ties > 0 makes that many entries share the minimum."""
+    q = rng(seed).normal(0.0, 1.0, size=n)
+    if n_ties > 1:
+        idx = rng(seed + 1).choice(n, size=n_ties, replace=False)
+        q[idx] = q.min() - 1.0
+    return q
+
+
+def channel(nx: int, ny: int, side: int, cx: int | None = None):
+    """Square obstacle of the given side centred on the channel's mid-height at x = cx
+    (default nx/4): solid cells [cx - side/2, cx + side/2) x [ny/2 - side/2, ny/2 + side/2)."""
+    if cx is None:
+        cx = nx // 4
+    if side <= 0:
+        return (0, 0, 0, 0)
+    return (cx - side // 2, ny // 2 - side // 2, side, side)
