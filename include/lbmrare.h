@@ -1,0 +1,207 @@
+/*
+ * lbmrare: ensemble lattice-Boltzmann channel flows past a square obstacle,
+ * advanced on one NVIDIA GB300 (sm_103a) and resampled by the GKTL and AMS
+ * rare-event algorithms, after Lestang, Bouchet & Leveque, "Numerical study of
+ * extreme mechanical force exerted by a turbulent flow on a bluff body by
+ * direct and rare-event sampling techniques" (arXiv 2005.09323).
+ *
+ * Conventions for every entry point:
+ *   - returns LBM_OK (0) or a negative lbm_status; lbm_last_error() gives a
+ *     message for the calling thread.  No exception crosses this boundary.
+ *   - arguments named *_dev are device pointers in the ensemble's (or the
+ *     given) stream order; the call enqueues work and returns without waiting.
+ *     Other pointers are host memory, owned by the caller, and the call has
+ *     finished with them when it returns (it synchronises the stream).
+ *   - arguments are validated on the host before anything is enqueued; on
+ *     LBM_ERR_ARG nothing was enqueued and the ensemble is unchanged.
+ *   - population arrays on the host are FP64, [9][ny][nx], direction q with
+ *     velocity c_q: q=0 (0,0); 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1);
+ *     5 (1,1); 6 (-1,1); 7 (-1,-1); 8 (1,-1).
+ *   - time t counts lattice steps; D(t) is the drag of the state after step t.
+ */
+#ifndef LBMRARE_H
+#define LBMRARE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,        /* invalid argument; nothing enqueued */
+    LBM_ERR_CUDA = -2,       /* a CUDA call failed; message names it */
+    LBM_ERR_NONFINITE = -3,  /* a drag value, weight or score is not finite */
+    LBM_ERR_TIMEOUT = -4,    /* a bounded device-side wait ran out */
+    LBM_ERR_OOM = -5,        /* device allocation failed */
+    LBM_ERR_STATE = -6       /* call not valid in the ensemble's current state */
+} lbm_status;
+
+typedef enum {
+    LBM_FP32 = 0,            /* populations f stored as FP32 (72 B per site update) */
+    LBM_FP16_SHIFTED = 1,    /* (f - w_q) * 2^shift_exp stored as FP16 (36 B) */
+    LBM_BF16_SHIFTED = 2     /* (f - w_q) * 2^shift_exp stored as BF16 (36 B) */
+} lbm_storage;
+
+/* One channel flow (Sec. 2 and App. A): D2Q9 lattice-BGK on nx x ny nodes,
+ * periodic in x, no-slip walls halfway below row 0 and above row ny-1, a square
+ * obstacle of solid cells [obs_x0, obs_x0+obs_w) x [obs_y0, obs_y0+obs_h) with
+ * halfway bounce-back on its surface, and a constant body-force density
+ * (gx, gy) on fluid nodes (Guo forcing). */
+typedef struct {
+    int32_t nx, ny;            /* nx a multiple of 8, nx >= 8, ny >= 2 */
+    int32_t obs_x0, obs_y0, obs_w, obs_h;  /* obs_w = 0: no obstacle; else 1 <= obs_x0, obs_x0+obs_w <= nx-1 */
+    double tau;                /* BGK relaxation time (> 1/2); nu = (tau - 1/2)/3 */
+    double gx, gy;             /* force density per fluid node */
+    int32_t storage;           /* lbm_storage */
+    int32_t shift_exp;         /* 16-bit storage scale 2^shift_exp (0 for FP32) */
+    int32_t max_steps;         /* capacity of the drag history per clone */
+    int32_t ckpt_stride;       /* AMS: keep the state every ckpt_stride steps; 0 = none */
+    int32_t n_snapshots;       /* capacity of the App. D snapshot bank (N_s) */
+    double init_amp;           /* initial velocity perturbation amplitude */
+} lbm_config;
+
+typedef struct lbm_ensemble lbm_ensemble;
+
+/* message of the last failure on the calling thread ("" if none) */
+const char* lbm_last_error(void);
+
+/* number of CUDA kernels this library has launched in the process so far */
+int64_t lbm_launch_count(void);
+
+/* ---------------------------------------------------------------- ensemble */
+
+/* Create N independent trajectories of the flow (ensemble of Sec. 4 and
+ * App. C.1) on the current CUDA device and initialise each at equilibrium
+ * (Sec. 2: "initial distributions ... at equilibrium") with rho = 1 and a
+ * seeded velocity u = init_amp * (2 U - 1) per component, U from Philox4x64-10
+ * with counter (5, clone, y*nx + x, 0) and key (seed, 0); solid nodes hold the
+ * rest weights.  The ensemble owns all its device memory; stream may be NULL
+ * (the legacy default stream).  Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, void* stream,
+                        lbm_ensemble** out);
+
+/* Free everything the ensemble owns (waits for its stream). */
+int lbm_ensemble_destroy(lbm_ensemble* e);
+
+/* Advance every clone by n_steps lattice steps (App. A: exact streaming with
+ * halfway bounce-back, then BGK collision with Guo forcing; one fused kernel per
+ * step) and record the momentum-exchange drag of eq. (drag_definition) after each
+ * step.  All clones must be at the same time; t + n_steps <= max_steps.  States
+ * are saved every ckpt_stride steps when checkpoints are enabled.  Asynchronous:
+ * a non-finite drag is reported by the next synchronising call as
+ * LBM_ERR_NONFINITE. */
+int lbm_ensemble_step(lbm_ensemble* e, int32_t n_steps);
+
+/* As lbm_ensemble_step, for the n listed clones only (host array of distinct
+ * indices, all at the same time) - the re-simulation of a branched AMS
+ * trajectory (App. B.1). */
+int lbm_ensemble_step_clones(lbm_ensemble* e, int32_t n_steps, const int32_t* clones, int32_t n);
+
+/* Copy each clone's current time (host int32[N]). */
+int lbm_ensemble_time(lbm_ensemble* e, int32_t* t);
+
+/* Drag history D(t), t0 < t <= t1, of every clone into dst[N][t1-t0] (FP64);
+ * t1 may not exceed the latest clone time, and entries past a clone's own
+ * time are not part of its trajectory.
+ * dst_on_device != 0: dst is a device pointer and the copy is enqueued;
+ * otherwise dst is host memory and the call waits.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_NONFINITE (a recorded drag value was not finite). */
+int lbm_ensemble_drag(lbm_ensemble* e, int32_t t0, int32_t t1, double* dst, int32_t dst_on_device);
+
+/* GKTL exponent of eq. (Weight): out_dev[n] = k * sum_{t0 < t <= t1} D_n(t)
+ * (dt = one lattice step), FP64, fixed summation order. */
+int lbm_ensemble_window_sum(lbm_ensemble* e, int32_t t0, int32_t t1, double k, double* out_dev);
+
+/* Time-averaged drag of eq. (def_time_averaged_drag) with a window of T steps,
+ * F(t) = (1/T) sum_{s=t-T+1}^{t} D(s) for T <= t <= t_end, FP64, stored in the
+ * ensemble; out_dev[n] (may be NULL) receives max_t F_n(t) (-inf if t_end < T):
+ * the AMS score maximum Q_n (App. B.1) and the GKTL event amplitude (App. C.2). */
+int lbm_ensemble_scores(lbm_ensemble* e, int32_t window, int32_t t_end, double* out_dev);
+
+/* First t with F_clone(t) > level in the last lbm_ensemble_scores result (the
+ * AMS branching time of App. B.1); *t = -1 if none.  Host output; waits. */
+int lbm_ensemble_first_crossing(lbm_ensemble* e, int32_t clone, double level, int32_t* t);
+
+/* Fill the App. D snapshot bank with the current states of the n_s listed
+ * clones (host array) and record their masses. */
+int lbm_ensemble_set_snapshots(lbm_ensemble* e, int32_t n_s, const int32_t* clones);
+
+/* GKTL cloning (App. C.1) with the App. D perturbation: every slot s with
+ * parent_dev[s] != s (a killed trajectory) becomes a copy of its parent's state,
+ * time and drag history, perturbed by eq. (perturb_pop),
+ *   f <- (f + eps sum_n alpha_n f^(n)) * M / (M + eps sum_n alpha_n M^(n)),
+ * M the fluid mass, alpha_n uniform from Philox4x64-10 counter (4, iter, s, n),
+ * key (seed, 0).  A parent must keep its own slot (parent_dev[p] == p), as
+ * gktl_select guarantees.  eps = 0 copies exactly.  Needs the snapshot bank
+ * when eps != 0.  A parent index outside [0, N) (a rejected selection writes
+ * -1) leaves that slot unchanged and is reported as LBM_ERR_NONFINITE by the
+ * next synchronising call. */
+int lbm_ensemble_clone(lbm_ensemble* e, const int32_t* parent_dev, double eps, uint64_t seed,
+                       uint64_t iter);
+
+/* AMS branching (App. B.1): trajectory dst becomes a copy of src up to time t_b
+ * (state restored from src's last checkpoint at or before t_b and replayed
+ * bit-for-bit, drag history and checkpoints copied), perturbed as in
+ * lbm_ensemble_clone with counter (4, iter, dst, n); dst is then at time t_b.
+ * Needs ckpt_stride > 0 and src at time >= t_b. */
+int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, double eps,
+                        uint64_t seed, uint64_t iter);
+
+/* Fluid mass and momentum sum_x sum_q f_q (1, c_q) per clone (host double[N]
+ * each; any may be NULL), FP64 deterministic reduction.  Waits. */
+int lbm_ensemble_moments(lbm_ensemble* e, double* mass, double* px, double* py);
+
+/* Read / overwrite one clone's populations as FP64 [9][ny][nx] host arrays
+ * (decoded from, or encoded to, the storage format).  Wait. */
+int lbm_ensemble_get_populations(lbm_ensemble* e, int32_t clone, double* host);
+int lbm_ensemble_set_populations(lbm_ensemble* e, int32_t clone, const double* host);
+
+/* Pick the fastest compiled variant of the fused step (sites per thread, warps
+ * per block) for this ensemble by timing each on its own state; the state and
+ * the drag history are left unchanged.  *variant (may be NULL) gets the index. */
+int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant);
+/* Force a variant by index (-1 restores the default); describe any index. */
+int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant);
+int lbm_step_variant_info(int32_t variant, int32_t* storage, int32_t* vec, int32_t* warps);
+int32_t lbm_step_variant_count(void);
+
+/* Kernel timing: when enabled, every batch of fused-step launches is bracketed
+ * by CUDA events on the ensemble's stream; lbm_ensemble_kernel_time waits and
+ * returns the summed milliseconds and launch count since the last reset. */
+int lbm_ensemble_set_timing(lbm_ensemble* e, int32_t enable);
+int lbm_ensemble_kernel_time(lbm_ensemble* e, double* ms, int64_t* launches, int32_t reset);
+
+/* ---------------------------------------------------------------- selection */
+
+/* GKTL weights, eq. (Weight): with m = max s, W_dev[n] = N e^{s_n - m} / S and
+ * logR_dev[0] = m + ln(S / N), S = sum_n e^{s_n - m} (fixed-order FP64 sum), so
+ * that sum W = N and ln Z = sum over cloning steps of logR (App. C.1).  One
+ * block, N <= 4096.  Writes flag_dev-free: a non-finite s makes every W NaN and
+ * gktl_select then fails with LBM_ERR_NONFINITE. */
+int gktl_weights(int32_t n, const double* s_dev, double* W_dev, double* logR_dev, void* stream);
+
+/* GKTL resampling to N copies with mean copy number W_n (App. C.1; scheme:
+ * residual resampling with a systematic draw of the residuals, uniform from
+ * Philox4x64-10 counter (1, iter, 0, 0), key (seed, 0)); a trajectory with at
+ * least one copy keeps its slot, extra copies fill the emptied slots in
+ * ascending order.  parent_dev[N] receives the parent of each slot.  W must be
+ * finite, non-negative and sum to N (relative 1e-9): otherwise parent_dev is
+ * filled with -1 and status_dev (may be NULL) receives LBM_ERR_NONFINITE or
+ * LBM_ERR_ARG.  One block, N <= 4096. */
+int gktl_select(int32_t n, const double* W_dev, uint64_t seed, uint64_t iter, int32_t* parent_dev,
+                int32_t* status_dev, void* stream);
+
+/* AMS selection (App. B.1): level z = min_n Q_n; every n with Q_n == z is
+ * killed (killed_dev, ascending; *n_killed_dev = their number); for the k-th
+ * killed index, survivor_dev[k] is the r-th non-killed index in ascending order,
+ * r = floor(x * (N - |K|) / 2^64), x word 0 of Philox4x64-10 counter
+ * (3, iter, killed, 0), key (seed, 0).  *n_killed_dev = N means every score
+ * equals z (nothing survives).  A NaN score gives *n_killed_dev = -1. */
+int ams_select(int32_t n, const double* Q_dev, uint64_t seed, uint64_t iter, int32_t* killed_dev,
+               int32_t* n_killed_dev, int32_t* survivor_dev, double* level_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,101 @@
+// Host-side internals shared by the translation units of liblbmrare.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lbmrare.h"
+
+namespace lbm {
+
+void set_error(const std::string& msg);
+// every kernel the library launches is counted (lbm_launch_count)
+void count_launches(int64_t n);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define LBM_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t err_ = (call);                            \
+        if (err_ != cudaSuccess) return cuda_fail(err_, #call); \
+    } while (0)
+
+// Everything one fused stream-collide launch needs.  Populations of clone c
+// live at buf[p] + c * clone_stride, direction q at + q * plane, row y at
+// + y * pitch; p alternates per clone with its own parity.
+struct StepParams {
+    void* buf0;
+    void* buf1;
+    const int32_t* parity;      // [N] current buffer of each clone
+    const int32_t* clone_list;  // clones advanced by this launch
+    int32_t n_list;
+    int32_t nx, ny, pitch;
+    int64_t plane, clone_stride;
+    int32_t nseg;               // row segments of 32*V sites
+    // obstacle: solid cells [ox0, ox1) x [oy0, oy1); ox1 == ox0 for none
+    int32_t ox0, ox1, oy0, oy1;
+    // drag ring: rows [ry0, ry1], segments [rs0, rs1]; one partial per warp
+    int32_t ry0, ry1, rs0, rs1, n_slots, batch_cap;
+    float* partials;            // [N][batch_cap][n_slots]
+    float omega;                // 1/tau
+    float gx, gy;               // body-force density
+    float scale, inv_scale;     // 16-bit shift scale 2^s and its inverse
+    int32_t step_in_batch;
+};
+
+struct StepVariant {
+    int storage;
+    int vec;    // sites per thread
+    int warps;  // warps per block
+    cudaError_t (*launch)(const StepParams&, int grid, cudaStream_t);
+};
+
+// all compiled variants of the fused step (lbm_step.cu)
+const std::vector<StepVariant>& step_variants();
+
+}  // namespace lbm
+
+struct lbm_ensemble {
+    lbm_config cfg;
+    int32_t n;
+    uint64_t seed;
+    cudaStream_t stream;
+    int device;
+    int elem_bytes;
+    int32_t pitch;
+    int64_t plane, clone_stride;  // in elements
+    float scale, inv_scale;
+    void* buf[2];
+    int32_t* parity_dev;
+    int32_t* t_dev;
+    std::vector<int32_t> parity_host, t_host;
+    int32_t* list_dev;        // clone list of the current step call
+    int32_t* all_dev;         // 0..N-1
+    float* partials;          // [N][batch_cap][n_slots]
+    int32_t batch_cap, n_slots;
+    int32_t ry0, ry1, rs0, rs1;
+    double* drag;             // [N][max_steps]
+    int32_t* flag_dev;        // [0]: nonzero once a drag value was not finite; [1]: scratch int
+    // App. D snapshot bank
+    void* snaps;
+    double* snap_mass;        // [n_snapshots]
+    int32_t n_snaps_set;
+    // AMS checkpoints every ckpt_stride steps: [N][n_ckpt] states
+    void* ckpt;
+    int32_t n_ckpt;
+    // scratch for deterministic reductions
+    double* red_partials;     // [N][red_blocks] (or larger)
+    int32_t red_blocks;
+    double* mass_dev;         // [N]
+    double* scores;           // [N][max_steps] trailing means
+    int32_t score_window, score_t_end;  // arguments of the last lbm_ensemble_scores
+    // selected step variant (index into step_variants())
+    int variant;
+    // optional timing of the fused step launches
+    bool timing;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    double timed_ms;
+    int64_t timed_launches;
+};

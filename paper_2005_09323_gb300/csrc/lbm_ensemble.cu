@@ -1,0 +1,1018 @@
+// Ensemble runtime of liblbmrare: device memory, initial state, drag
+// bookkeeping, deterministic reductions, GKTL cloning and AMS branching with
+// the App. D perturbation, checkpoints, and the C ABI around them.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+static thread_local std::string g_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_error = msg; }
+int fail(int code, const std::string& msg)
+{
+    g_error = msg;
+    return code;
+}
+int cuda_fail(cudaError_t err, const char* what)
+{
+    g_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) + ")";
+    return err == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+void register_step_fp32(std::vector<StepVariant>&);
+void register_step_fp16(std::vector<StepVariant>&);
+void register_step_bf16(std::vector<StepVariant>&);
+
+const std::vector<StepVariant>& step_variants()
+{
+    static const std::vector<StepVariant> table = [] {
+        std::vector<StepVariant> v;
+        register_step_fp32(v);
+        register_step_fp16(v);
+        register_step_bf16(v);
+        return v;
+    }();
+    return table;
+}
+
+constexpr int kBatchCap = 512;     // steps per drag-finalisation batch
+constexpr int kRedBlocks = 152;    // blocks of a per-clone reduction (one wave)
+constexpr int kRedThreads = 256;
+
+static int elem_size(int storage) { return storage == kFP32 ? 4 : 2; }
+
+// ---------------------------------------------------------------- kernels
+template <int S>
+__global__ void init_kernel(void* buf, int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx,
+                            int32_t ny, int32_t n, int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1,
+                            uint64_t seed, double amp, float scale)
+{
+    using T = typename Codec<S>::T;
+    T* base = static_cast<T*>(buf);
+    const int64_t sites = (int64_t)nx * ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sites * n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / sites);
+        const int64_t site = i - (int64_t)c * sites;
+        const int y = (int)(site / nx), x = (int)(site - (int64_t)y * nx);
+        double ux = 0.0, uy = 0.0;
+        const bool solid = x >= ox0 && x < ox1 && y >= oy0 && y < oy1;
+        if (!solid) {
+            const u64x4 r = philox(kStreamInit, (uint64_t)c, (uint64_t)site, 0u, seed, 0u);
+            ux = amp * (2.0 * unit_double(r.v[0]) - 1.0);
+            uy = amp * (2.0 * unit_double(r.v[1]) - 1.0);
+        }
+        const double usq = ux * ux + uy * uy;
+        T* cell = base + (int64_t)c * clone_stride + (int64_t)y * pitch + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const double cu = cx(q) * ux + cy(q) * uy;
+            // f^eq(rho = 1, u) - w_q (App. A); zero on solid nodes
+            const double g = wd(q) * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+            T v;
+            if constexpr (S == kFP32)
+                v = (float)(wd(q) + g);
+            else
+                v = Codec<S>::enc((float)g, 0.f, scale);
+            cell[q * plane] = v;
+        }
+    }
+}
+
+// Sum the per-warp drag partials of each step in slot order (FP64), append to
+// the drag history, then advance the clone's time and buffer parity.
+__global__ void finalize_kernel(const float* partials, int32_t batch_cap, int32_t n_slots, int32_t used_slots,
+                                const int32_t* list, int32_t n_steps, double* drag, int32_t max_steps,
+                                int32_t* t, int32_t* parity, int32_t* flag)
+{
+    const int c = list[blockIdx.x];
+    const int t0 = t[c];
+    for (int s = threadIdx.x; s < n_steps; s += blockDim.x) {
+        const float* pp = partials + ((int64_t)c * batch_cap + s) * n_slots;
+        double acc = 0.0;
+        for (int k = 0; k < used_slots; ++k) acc += (double)pp[k];
+        if (!isfinite(acc)) *flag = 1;
+        drag[(int64_t)c * max_steps + t0 + s] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t[c] = t0 + n_steps;
+        parity[c] ^= (n_steps & 1);
+    }
+}
+
+// block-wide FP64 sum in a fixed order (tree over the shared array)
+template <int THREADS>
+__device__ double block_sum(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int off = THREADS / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <int THREADS>
+__device__ double block_max(double v, double* sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int off = THREADS / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + off]);
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void window_sum_kernel(const double* drag, int32_t max_steps, int32_t t0, int32_t t1, double k,
+                                  double* out)
+{
+    __shared__ double sh[kRedThreads];
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += kRedThreads) acc += drag[(int64_t)c * max_steps + t];
+    const double s = block_sum<kRedThreads>(acc, sh);
+    if (threadIdx.x == 0) out[c] = k * s;
+}
+
+// F(t) = (1/W) sum_{s=t-W+1}^{t} D(s); thread i owns a contiguous range of t,
+// opens it with a direct sum and slides the window across it.
+__global__ void scores_kernel(const double* drag, int32_t max_steps, int32_t window, int32_t t_end,
+                              double* scores, double* out_max)
+{
+    __shared__ double sh[kRedThreads];
+    const int c = blockIdx.x;
+    const double* d = drag + (int64_t)c * max_steps;  // d[t-1] = D(t)
+    double* F = scores + (int64_t)c * max_steps;      // F[t-1] = F(t)
+    const int first = window, count = t_end - window + 1;
+    double best = -INFINITY;
+    if (count > 0) {
+        const int chunk = (count + kRedThreads - 1) / kRedThreads;
+        const int ta = first + (int)threadIdx.x * chunk;
+        const int tb = min(ta + chunk - 1, t_end);
+        if (ta <= tb) {
+            double acc = 0.0;
+            for (int s = ta - window + 1; s <= ta; ++s) acc += d[s - 1];
+            for (int t = ta; t <= tb; ++t) {
+                if (t > ta) acc += d[t - 1] - d[t - window - 1];
+                const double m = acc / (double)window;
+                F[t - 1] = m;
+                best = fmax(best, m);
+            }
+        }
+    }
+    for (int t = 1 + (int)threadIdx.x; t < min(first, t_end + 1); t += kRedThreads) F[t - 1] = -INFINITY;
+    const double mx = block_max<kRedThreads>(best, sh);
+    if (threadIdx.x == 0 && out_max) out_max[c] = mx;
+}
+
+__global__ void first_crossing_kernel(const double* F, int32_t t_lo, int32_t t_hi, double level, int32_t* out)
+{
+    __shared__ int sh[kRedThreads];
+    int best = INT32_MAX;
+    for (int t = t_lo + (int)threadIdx.x; t <= t_hi; t += kRedThreads)
+        if (F[t - 1] > level) { best = t; break; }
+    sh[threadIdx.x] = best;
+    __syncthreads();
+    for (int off = kRedThreads / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) sh[threadIdx.x] = min(sh[threadIdx.x], sh[threadIdx.x + off]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0] == INT32_MAX ? -1 : sh[0];
+}
+
+// Per-block FP64 partial sums of mass and momentum over the fluid nodes of
+// each listed clone (the blocks of one clone cover its sites in a fixed way).
+template <int S>
+__global__ void moments_partial_kernel(const void* buf0, const void* buf1, const int32_t* parity, const int32_t* list,
+                                       int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny,
+                                       int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1, float inv_scale,
+                                       double* partial)
+{
+    using T = typename Codec<S>::T;
+    __shared__ double sh[kRedThreads];
+    const int li = blockIdx.y;
+    const int c = list[li];
+    const T* base = static_cast<const T*>(parity[c] ? buf1 : buf0) + (int64_t)c * clone_stride;
+    const int64_t sites = (int64_t)nx * ny;
+    double m = 0.0, px = 0.0, py = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < sites; i += (int64_t)gridDim.x * kRedThreads) {
+        const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
+        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1) continue;
+        const T* cell = base + (int64_t)y * pitch + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const double f = (double)wf(q) + (double)Codec<S>::dec(cell[q * plane], wf(q), inv_scale);
+            m += f;
+            px += cx(q) * f;
+            py += cy(q) * f;
+        }
+    }
+    const double sm = block_sum<kRedThreads>(m, sh);
+    const double sx = block_sum<kRedThreads>(px, sh);
+    const double sy = block_sum<kRedThreads>(py, sh);
+    if (threadIdx.x == 0) {
+        double* o = partial + ((int64_t)c * gridDim.x + blockIdx.x) * 3;
+        o[0] = sm; o[1] = sx; o[2] = sy;
+    }
+}
+
+__global__ void moments_final_kernel(const double* partial, int32_t nblocks, const int32_t* list, double* mass,
+                                     double* px, double* py)
+{
+    const int c = list[blockIdx.x];
+    if (threadIdx.x != 0) return;
+    double m = 0, x = 0, y = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double* o = partial + ((int64_t)c * nblocks + b) * 3;
+        m += o[0]; x += o[1]; y += o[2];
+    }
+    mass[c] = m;
+    if (px) px[c] = x;
+    if (py) py[c] = y;
+}
+
+// App. D: slot s with parent p != s (or s == inplace) becomes
+//   f_s = (f_p + eps sum_n alpha_n f^(n)) * M_p / (M_p + eps sum_n alpha_n M^(n))
+// on fluid nodes, written in the shifted variable g = f - w.
+template <int S>
+__global__ void perturb_kernel(void* buf0, void* buf1, const int32_t* parity, const int32_t* parent, int32_t n_clones,
+                               int32_t* flag, int32_t inplace,
+                               int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny,
+                               int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1, const void* snaps, int32_t n_s,
+                               const double* snap_mass, const double* mass, double eps, uint64_t seed, uint64_t iter,
+                               float scale, float inv_scale)
+{
+    using T = typename Codec<S>::T;
+    const int s = blockIdx.y;
+    const int p = parent[s];
+    if (p < 0 || p >= n_clones) {  // rejected selection: leave the slot alone
+        if (threadIdx.x == 0) flag[0] = 1;
+        return;
+    }
+    if (p == s && s != inplace) return;  // block-uniform
+    __shared__ float alpha_eps[16];
+    __shared__ float sc_m1[2];
+    if (threadIdx.x == 0) {
+        double lin = 0.0;
+        for (int k = 0; k < n_s; ++k) {
+            const u64x4 r = philox(kStreamPerturb, iter, (uint64_t)s, (uint64_t)k, seed, 0u);
+            const double a = unit_double(r.v[0]);
+            alpha_eps[k] = (float)(eps * a);
+            lin += eps * a * snap_mass[k];
+        }
+        const double Mp = mass[p];
+        const double scale_m = eps == 0.0 ? 1.0 : Mp / (Mp + lin);
+        sc_m1[0] = (float)scale_m;
+        sc_m1[1] = (float)(scale_m - 1.0);
+    }
+    __syncthreads();
+    const float sm = sc_m1[0], sm1 = sc_m1[1];
+    const T* from = static_cast<const T*>(parity[p] ? buf1 : buf0) + (int64_t)p * clone_stride;
+    T* to = static_cast<T*>(parity[s] ? buf1 : buf0) + (int64_t)s * clone_stride;
+    const T* sn = static_cast<const T*>(snaps);
+    const int64_t sites = (int64_t)nx * ny;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sites; i += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
+        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1) continue;  // solid: stays at rest
+        const int64_t off = (int64_t)y * pitch + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float w = wf(q);
+            const float g = Codec<S>::dec(from[q * plane + off], w, inv_scale);
+            float add = 0.f;
+            for (int k = 0; k < n_s; ++k)
+                add += alpha_eps[k] * (w + Codec<S>::dec(sn[(int64_t)k * clone_stride + q * plane + off], w, inv_scale));
+            // f_new - w = (g + add) * sm + w * (sm - 1)
+            const float gn = (g + add) * sm + w * sm1;
+            to[q * plane + off] = Codec<S>::enc(gn, w, scale);
+        }
+    }
+}
+
+__global__ void copy_history_kernel(double* drag, int32_t max_steps, const int32_t* parent, int32_t n_clones,
+                                    int32_t n_hist)
+{
+    const int s = blockIdx.y;
+    const int p = parent[s];
+    if (p == s || p < 0 || p >= n_clones) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_hist; t += gridDim.x * blockDim.x)
+        drag[(int64_t)s * max_steps + t] = drag[(int64_t)p * max_steps + t];
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+// ---------------------------------------------------------------- host helpers
+namespace {
+
+struct Ring {
+    int ry0, ry1, rs0, rs1, n_slots;
+};
+
+Ring ring_for(const lbm_config& c, int vec)
+{
+    Ring r{0, -1, 0, -1, 0};
+    if (c.obs_w <= 0) return r;
+    const int seg_w = 32 * vec;
+    r.ry0 = std::max(c.obs_y0 - 1, 0);
+    r.ry1 = std::min(c.obs_y0 + c.obs_h, c.ny - 1);
+    r.rs0 = (c.obs_x0 - 1) / seg_w;
+    r.rs1 = (c.obs_x0 + c.obs_w) / seg_w;
+    r.n_slots = (r.ry1 - r.ry0 + 1) * (r.rs1 - r.rs0 + 1);
+    return r;
+}
+
+int default_variant(int storage)
+{
+    const auto& v = step_variants();
+    const int want_vec = storage == kFP32 ? 4 : 8;
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i].storage == storage && v[i].vec == want_vec && v[i].warps == 4) return (int)i;
+    return -1;
+}
+
+StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_list, int vec, int step)
+{
+    const lbm_config& c = e->cfg;
+    StepParams p{};
+    p.buf0 = e->buf[0];
+    p.buf1 = e->buf[1];
+    p.parity = e->parity_dev;
+    p.clone_list = list;
+    p.n_list = n_list;
+    p.nx = c.nx;
+    p.ny = c.ny;
+    p.pitch = e->pitch;
+    p.plane = e->plane;
+    p.clone_stride = e->clone_stride;
+    p.nseg = (c.nx + 32 * vec - 1) / (32 * vec);
+    p.ox0 = c.obs_x0;
+    p.ox1 = c.obs_w > 0 ? c.obs_x0 + c.obs_w : c.obs_x0;
+    p.oy0 = c.obs_y0;
+    p.oy1 = c.obs_w > 0 ? c.obs_y0 + c.obs_h : c.obs_y0;
+    const Ring r = ring_for(c, vec);
+    p.ry0 = r.ry0;
+    p.ry1 = r.ry1;
+    p.rs0 = r.rs0;
+    p.rs1 = r.rs1;
+    p.n_slots = e->n_slots;
+    p.batch_cap = e->batch_cap;
+    p.partials = e->partials;
+    p.omega = (float)(1.0 / c.tau);
+    p.gx = (float)c.gx;
+    p.gy = (float)c.gy;
+    p.scale = e->scale;
+    p.inv_scale = e->inv_scale;
+    p.step_in_batch = step;
+    return p;
+}
+
+int check_sticky(lbm_ensemble* e)
+{
+    int32_t flag = 0;
+    LBM_CUDA(cudaMemcpyAsync(&flag, e->flag_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    if (flag) return fail(LBM_ERR_NONFINITE, "a drag value of the ensemble is not finite (unstable flow?)");
+    return LBM_OK;
+}
+
+template <typename F>
+int dispatch_storage(int storage, F&& f)
+{
+    switch (storage) {
+    case kFP32: return f(std::integral_constant<int, kFP32>{});
+    case kFP16: return f(std::integral_constant<int, kFP16>{});
+    case kBF16: return f(std::integral_constant<int, kBF16>{});
+    }
+    return fail(LBM_ERR_ARG, "unknown storage");
+}
+
+int solid_bounds(const lbm_config& c, int& ox0, int& ox1, int& oy0, int& oy1)
+{
+    ox0 = c.obs_x0;
+    oy0 = c.obs_y0;
+    ox1 = c.obs_w > 0 ? c.obs_x0 + c.obs_w : c.obs_x0;
+    oy1 = c.obs_w > 0 ? c.obs_y0 + c.obs_h : c.obs_y0;
+    return 0;
+}
+
+// run the fused step n times on the listed clones (all at time t), with drag
+// finalisation per batch and checkpoints at multiples of ckpt_stride
+int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_t>& list, int32_t n_steps)
+{
+    const auto& vars = step_variants();
+    const StepVariant& v = vars[e->variant];
+    const int n_list = (int)list.size();
+    const int nseg = (e->cfg.nx + 32 * v.vec - 1) / (32 * v.vec);
+    const int64_t warps = (int64_t)n_list * e->cfg.ny * nseg;
+    const int grid = (int)((warps + v.warps - 1) / v.warps);
+    const Ring r = ring_for(e->cfg, v.vec);
+    int32_t t = e->t_host[list[0]];
+    int32_t left = n_steps;
+    while (left > 0) {
+        int32_t chunk = std::min(left, e->batch_cap);
+        if (e->cfg.ckpt_stride > 0) {
+            const int32_t to_ckpt = e->cfg.ckpt_stride - (t % e->cfg.ckpt_stride);
+            chunk = std::min(chunk, to_ckpt);
+        }
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (e->timing) {
+            LBM_CUDA(cudaEventCreate(&ev0));
+            LBM_CUDA(cudaEventCreate(&ev1));
+            LBM_CUDA(cudaEventRecord(ev0, e->stream));
+        }
+        for (int s = 0; s < chunk; ++s) {
+            StepParams p = make_params(e, list_dev, n_list, v.vec, s);
+            cudaError_t err = v.launch(p, grid, e->stream);
+            if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
+            count_launches(1);
+        }
+        if (e->timing) {
+            LBM_CUDA(cudaEventRecord(ev1, e->stream));
+            e->events.emplace_back(ev0, ev1);
+            e->timed_launches += chunk;
+        }
+        finalize_kernel<<<n_list, 128, 0, e->stream>>>(e->partials, e->batch_cap, e->n_slots, r.n_slots, list_dev,
+                                                        chunk, e->drag, e->cfg.max_steps, e->t_dev, e->parity_dev,
+                                                        e->flag_dev);
+        count_launches(1);
+        LBM_CUDA(cudaGetLastError());
+        t += chunk;
+        left -= chunk;
+        for (int32_t c : list) {
+            e->t_host[c] = t;
+            e->parity_host[c] ^= (chunk & 1);
+        }
+        if (e->cfg.ckpt_stride > 0 && t % e->cfg.ckpt_stride == 0) {
+            const int k = t / e->cfg.ckpt_stride;
+            if (k < e->n_ckpt) {
+                const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+                for (int32_t c : list) {
+                    const char* from = static_cast<const char*>(e->buf[e->parity_host[c]]) + (size_t)c * bytes;
+                    char* to = static_cast<char*>(e->ckpt) + ((size_t)c * e->n_ckpt + k) * bytes;
+                    LBM_CUDA(cudaMemcpyAsync(to, from, bytes, cudaMemcpyDeviceToDevice, e->stream));
+                }
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+int compute_masses(lbm_ensemble* e, const int32_t* list_dev, int n_list)
+{
+    int ox0, ox1, oy0, oy1;
+    solid_bounds(e->cfg, ox0, ox1, oy0, oy1);
+    return dispatch_storage(e->cfg.storage, [&](auto tag) -> int {
+        constexpr int S = decltype(tag)::value;
+        dim3 grid(e->red_blocks, n_list);
+        moments_partial_kernel<S><<<grid, kRedThreads, 0, e->stream>>>(
+            e->buf[0], e->buf[1], e->parity_dev, list_dev, e->clone_stride, e->plane, e->pitch, e->cfg.nx, e->cfg.ny,
+            ox0, ox1, oy0, oy1, e->inv_scale, e->red_partials);
+        count_launches(1);
+        LBM_CUDA(cudaGetLastError());
+        moments_final_kernel<<<n_list, 32, 0, e->stream>>>(e->red_partials, e->red_blocks, list_dev, e->mass_dev,
+                                                            e->mass_dev + e->n, e->mass_dev + 2 * e->n);
+        count_launches(1);
+        LBM_CUDA(cudaGetLastError());
+        return LBM_OK;
+    });
+}
+
+int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, double eps, uint64_t seed, uint64_t iter)
+{
+    int ox0, ox1, oy0, oy1;
+    solid_bounds(e->cfg, ox0, ox1, oy0, oy1);
+    const int n_s = eps != 0.0 ? e->n_snaps_set : 0;
+    return dispatch_storage(e->cfg.storage, [&](auto tag) -> int {
+        constexpr int S = decltype(tag)::value;
+        const int64_t sites = (int64_t)e->cfg.nx * e->cfg.ny;
+        const int bx = (int)std::min<int64_t>((sites + 255) / 256, 1024);
+        dim3 grid(bx, e->n);
+        perturb_kernel<S><<<grid, 256, 0, e->stream>>>(
+            e->buf[0], e->buf[1], e->parity_dev, parent_dev, e->n, e->flag_dev, inplace, e->clone_stride, e->plane, e->pitch, e->cfg.nx,
+            e->cfg.ny, ox0, ox1, oy0, oy1, e->snaps, n_s, e->snap_mass, e->mass_dev, eps, seed, iter, e->scale,
+            e->inv_scale);
+        count_launches(1);
+        LBM_CUDA(cudaGetLastError());
+        return LBM_OK;
+    });
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* lbm_last_error(void) { return g_error.c_str(); }
+
+int64_t lbm_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int32_t lbm_step_variant_count(void) { return (int32_t)step_variants().size(); }
+
+int lbm_step_variant_info(int32_t variant, int32_t* storage, int32_t* vec, int32_t* warps)
+{
+    const auto& v = step_variants();
+    if (variant < 0 || variant >= (int32_t)v.size()) return fail(LBM_ERR_ARG, "variant index out of range");
+    if (storage) *storage = v[variant].storage;
+    if (vec) *vec = v[variant].vec;
+    if (warps) *warps = v[variant].warps;
+    return LBM_OK;
+}
+
+int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, void* stream, lbm_ensemble** out)
+{
+    if (!cfg || !out) return fail(LBM_ERR_ARG, "null config or output pointer");
+    *out = nullptr;
+    const lbm_config c = *cfg;
+    if (c.nx < 8 || c.nx % 8 != 0) return fail(LBM_ERR_ARG, "nx must be a positive multiple of 8");
+    if (c.ny < 2) return fail(LBM_ERR_ARG, "ny must be at least 2");
+    if (n_clones < 1) return fail(LBM_ERR_ARG, "need at least one clone");
+    if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(LBM_ERR_ARG, "tau must exceed 1/2");
+    if (!std::isfinite(c.gx) || !std::isfinite(c.gy)) return fail(LBM_ERR_ARG, "force must be finite");
+    if (c.storage < 0 || c.storage > 2) return fail(LBM_ERR_ARG, "unknown storage");
+    if (c.max_steps < 1) return fail(LBM_ERR_ARG, "max_steps must be positive");
+    if (c.ckpt_stride < 0) return fail(LBM_ERR_ARG, "ckpt_stride must be >= 0");
+    if (c.n_snapshots < 0 || c.n_snapshots > 16) return fail(LBM_ERR_ARG, "n_snapshots must be in [0, 16]");
+    if (c.shift_exp < -20 || c.shift_exp > 20) return fail(LBM_ERR_ARG, "shift_exp out of range");
+    if (c.obs_w < 0 || c.obs_h < 0 || (c.obs_w > 0) != (c.obs_h > 0)) return fail(LBM_ERR_ARG, "obstacle size");
+    if (c.obs_w > 0) {
+        if (c.obs_x0 < 1 || c.obs_x0 + c.obs_w > c.nx - 1)
+            return fail(LBM_ERR_ARG, "obstacle must leave a fluid column on both sides in x");
+        if (c.obs_y0 < 0 || c.obs_y0 + c.obs_h > c.ny) return fail(LBM_ERR_ARG, "obstacle outside the channel");
+    }
+    int dev = 0;
+    LBM_CUDA(cudaGetDevice(&dev));
+    auto* e = new lbm_ensemble();
+    e->cfg = c;
+    e->n = n_clones;
+    e->seed = seed;
+    e->stream = static_cast<cudaStream_t>(stream);
+    e->device = dev;
+    e->elem_bytes = elem_size(c.storage);
+    e->pitch = ((c.nx + 255) / 256) * 256;
+    e->plane = (int64_t)e->pitch * c.ny;
+    e->clone_stride = 9 * e->plane;
+    e->scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : c.shift_exp);
+    e->inv_scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : -c.shift_exp);
+    e->variant = default_variant(c.storage);
+    e->batch_cap = kBatchCap;
+    e->red_blocks = kRedBlocks;
+    // partial slots: enough for the narrowest segments of any variant
+    int max_slots = 1;
+    for (const auto& v : step_variants())
+        if (v.storage == c.storage) max_slots = std::max(max_slots, ring_for(c, v.vec).n_slots);
+    e->n_slots = max_slots;
+    e->n_ckpt = c.ckpt_stride > 0 ? c.max_steps / c.ckpt_stride + 1 : 0;
+    e->parity_host.assign(n_clones, 0);
+    e->t_host.assign(n_clones, 0);
+
+    auto cleanup = [&](int code) {
+        lbm_ensemble_destroy(e);
+        return code;
+    };
+    const size_t state_bytes = (size_t)e->clone_stride * e->elem_bytes * n_clones;
+    cudaError_t err;
+#define ALLOC(ptr, bytes)                                                         \
+    err = cudaMalloc((void**)&(ptr), (bytes));                                    \
+    if (err != cudaSuccess) return cleanup(cuda_fail(err, "cudaMalloc " #ptr));
+    ALLOC(e->buf[0], state_bytes);
+    ALLOC(e->buf[1], state_bytes);
+    ALLOC(e->parity_dev, sizeof(int32_t) * n_clones);
+    ALLOC(e->t_dev, sizeof(int32_t) * n_clones);
+    ALLOC(e->list_dev, sizeof(int32_t) * n_clones);
+    ALLOC(e->all_dev, sizeof(int32_t) * n_clones);
+    ALLOC(e->partials, sizeof(float) * (size_t)n_clones * e->batch_cap * e->n_slots);
+    ALLOC(e->drag, sizeof(double) * (size_t)n_clones * c.max_steps);
+    ALLOC(e->scores, sizeof(double) * (size_t)n_clones * c.max_steps);
+    ALLOC(e->flag_dev, sizeof(int32_t) * 2);
+    ALLOC(e->red_partials, sizeof(double) * 3 * (size_t)n_clones * e->red_blocks);
+    ALLOC(e->mass_dev, sizeof(double) * 3 * n_clones);
+    if (c.n_snapshots > 0) {
+        ALLOC(e->snaps, (size_t)e->clone_stride * e->elem_bytes * c.n_snapshots);
+        ALLOC(e->snap_mass, sizeof(double) * c.n_snapshots);
+    }
+    if (e->n_ckpt > 0) { ALLOC(e->ckpt, (size_t)e->clone_stride * e->elem_bytes * n_clones * e->n_ckpt); }
+#undef ALLOC
+    std::vector<int32_t> iota(n_clones);
+    for (int i = 0; i < n_clones; ++i) iota[i] = i;
+    auto chk = [&](cudaError_t er, const char* what) { return er == cudaSuccess ? 0 : cleanup(cuda_fail(er, what)); };
+    int rc;
+    if ((rc = chk(cudaMemcpyAsync(e->all_dev, iota.data(), sizeof(int32_t) * n_clones, cudaMemcpyHostToDevice, e->stream), "copy clone index"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->parity_dev, 0, sizeof(int32_t) * n_clones, e->stream), "memset parity"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->t_dev, 0, sizeof(int32_t) * n_clones, e->stream), "memset time"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->flag_dev, 0, sizeof(int32_t) * 2, e->stream), "memset flag"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->buf[0], 0, state_bytes, e->stream), "memset state"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->buf[1], 0, state_bytes, e->stream), "memset state"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->partials, 0, sizeof(float) * (size_t)n_clones * e->batch_cap * e->n_slots, e->stream), "memset partials"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->drag, 0, sizeof(double) * (size_t)n_clones * c.max_steps, e->stream), "memset drag"))) return rc;
+    int ox0, ox1, oy0, oy1;
+    solid_bounds(c, ox0, ox1, oy0, oy1);
+    rc = dispatch_storage(c.storage, [&](auto tag) -> int {
+        constexpr int S = decltype(tag)::value;
+        const int64_t total = (int64_t)c.nx * c.ny * n_clones;
+        const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+        init_kernel<S><<<grid, 256, 0, e->stream>>>(e->buf[0], e->clone_stride, e->plane, e->pitch, c.nx, c.ny,
+                                                    n_clones, ox0, ox1, oy0, oy1, seed, c.init_amp, e->scale);
+        count_launches(1);
+        return chk(cudaGetLastError(), "init kernel");
+    });
+    if (rc) return rc;
+    if (e->n_ckpt > 0) {
+        const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+        for (int i = 0; i < n_clones; ++i) {
+            rc = chk(cudaMemcpyAsync(static_cast<char*>(e->ckpt) + (size_t)i * e->n_ckpt * bytes,
+                                     static_cast<char*>(e->buf[0]) + (size_t)i * bytes, bytes,
+                                     cudaMemcpyDeviceToDevice, e->stream), "checkpoint 0");
+            if (rc) return rc;
+        }
+    }
+    if ((rc = chk(cudaStreamSynchronize(e->stream), "create sync"))) return rc;
+    *out = e;
+    return LBM_OK;
+}
+
+int lbm_ensemble_destroy(lbm_ensemble* e)
+{
+    if (!e) return LBM_OK;
+    cudaStreamSynchronize(e->stream);
+    for (auto& pr : e->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    void* ptrs[] = {e->buf[0], e->buf[1], e->parity_dev, e->t_dev, e->list_dev, e->all_dev, e->partials,
+                    e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete e;
+    return LBM_OK;
+}
+
+int lbm_ensemble_step(lbm_ensemble* e, int32_t n_steps)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    if (n_steps < 0) return fail(LBM_ERR_ARG, "n_steps must be >= 0");
+    const int32_t t = e->t_host[0];
+    for (int i = 1; i < e->n; ++i)
+        if (e->t_host[i] != t) return fail(LBM_ERR_STATE, "clones are at different times; use lbm_ensemble_step_clones");
+    if ((int64_t)t + n_steps > e->cfg.max_steps) return fail(LBM_ERR_ARG, "drag history capacity (max_steps) exceeded");
+    if (n_steps == 0) return LBM_OK;
+    std::vector<int32_t> all(e->n);
+    for (int i = 0; i < e->n; ++i) all[i] = i;
+    return step_list(e, e->all_dev, all, n_steps);
+}
+
+int lbm_ensemble_step_clones(lbm_ensemble* e, int32_t n_steps, const int32_t* clones, int32_t n)
+{
+    if (!e || !clones) return fail(LBM_ERR_ARG, "null argument");
+    if (n < 1 || n > e->n || n_steps < 0) return fail(LBM_ERR_ARG, "bad clone count or step count");
+    std::vector<int32_t> list(clones, clones + n), sorted(list);
+    std::sort(sorted.begin(), sorted.end());
+    for (int i = 0; i < n; ++i) {
+        if (sorted[i] < 0 || sorted[i] >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
+        if (i > 0 && sorted[i] == sorted[i - 1]) return fail(LBM_ERR_ARG, "repeated clone index");
+    }
+    const int32_t t = e->t_host[list[0]];
+    for (int32_t c : list)
+        if (e->t_host[c] != t) return fail(LBM_ERR_STATE, "listed clones are at different times");
+    if ((int64_t)t + n_steps > e->cfg.max_steps) return fail(LBM_ERR_ARG, "drag history capacity (max_steps) exceeded");
+    if (n_steps == 0) return LBM_OK;
+    LBM_CUDA(cudaMemcpyAsync(e->list_dev, list.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, e->stream));
+    int rc = step_list(e, e->list_dev, list, n_steps);
+    if (rc) return rc;
+    // the list buffer is reused by the next call: keep the host copy alive
+    // until the enqueued copy has been consumed
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    return LBM_OK;
+}
+
+int lbm_ensemble_time(lbm_ensemble* e, int32_t* t)
+{
+    if (!e || !t) return fail(LBM_ERR_ARG, "null argument");
+    std::copy(e->t_host.begin(), e->t_host.end(), t);
+    return LBM_OK;
+}
+
+int lbm_ensemble_drag(lbm_ensemble* e, int32_t t0, int32_t t1, double* dst, int32_t dst_on_device)
+{
+    if (!e || !dst) return fail(LBM_ERR_ARG, "null argument");
+    const int32_t tmax = *std::max_element(e->t_host.begin(), e->t_host.end());
+    if (t0 < 0 || t1 < t0 || t1 > tmax) return fail(LBM_ERR_ARG, "drag window outside the recorded history");
+    const int32_t w = t1 - t0;
+    if (w == 0) return LBM_OK;
+    LBM_CUDA(cudaMemcpy2DAsync(dst, sizeof(double) * w, e->drag + t0, sizeof(double) * e->cfg.max_steps,
+                               sizeof(double) * w, e->n,
+                               dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, e->stream));
+    if (!dst_on_device) return check_sticky(e);
+    return LBM_OK;
+}
+
+int lbm_ensemble_window_sum(lbm_ensemble* e, int32_t t0, int32_t t1, double k, double* out_dev)
+{
+    if (!e || !out_dev) return fail(LBM_ERR_ARG, "null argument");
+    const int32_t tmax = *std::max_element(e->t_host.begin(), e->t_host.end());
+    if (t0 < 0 || t1 < t0 || t1 > tmax) return fail(LBM_ERR_ARG, "window outside the recorded history");
+    if (!std::isfinite(k)) return fail(LBM_ERR_ARG, "k must be finite");
+    window_sum_kernel<<<e->n, kRedThreads, 0, e->stream>>>(e->drag, e->cfg.max_steps, t0, t1, k, out_dev);
+    count_launches(1);
+    LBM_CUDA(cudaGetLastError());
+    return LBM_OK;
+}
+
+int lbm_ensemble_scores(lbm_ensemble* e, int32_t window, int32_t t_end, double* out_dev)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    const int32_t tmax = *std::max_element(e->t_host.begin(), e->t_host.end());
+    if (window < 1 || t_end < 0 || t_end > tmax) return fail(LBM_ERR_ARG, "bad window or end time");
+    scores_kernel<<<e->n, kRedThreads, 0, e->stream>>>(e->drag, e->cfg.max_steps, window, t_end, e->scores, out_dev);
+    count_launches(1);
+    LBM_CUDA(cudaGetLastError());
+    e->score_window = window;
+    e->score_t_end = t_end;
+    return LBM_OK;
+}
+
+int lbm_ensemble_first_crossing(lbm_ensemble* e, int32_t clone, double level, int32_t* t)
+{
+    if (!e || !t) return fail(LBM_ERR_ARG, "null argument");
+    if (clone < 0 || clone >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
+    if (e->score_window < 1) return fail(LBM_ERR_STATE, "call lbm_ensemble_scores first");
+    first_crossing_kernel<<<1, kRedThreads, 0, e->stream>>>(e->scores + (int64_t)clone * e->cfg.max_steps,
+                                                           e->score_window, e->score_t_end, level, e->flag_dev + 1);
+    count_launches(1);
+    LBM_CUDA(cudaGetLastError());
+    LBM_CUDA(cudaMemcpyAsync(t, e->flag_dev + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_snapshots(lbm_ensemble* e, int32_t n_s, const int32_t* clones)
+{
+    if (!e || (n_s > 0 && !clones)) return fail(LBM_ERR_ARG, "null argument");
+    if (n_s < 0 || n_s > e->cfg.n_snapshots) return fail(LBM_ERR_ARG, "more snapshots than the bank holds");
+    const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+    std::vector<int32_t> list(clones, clones + n_s);
+    for (int k = 0; k < n_s; ++k) {
+        const int c = list[k];
+        if (c < 0 || c >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
+        LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(e->snaps) + (size_t)k * bytes,
+                                 static_cast<char*>(e->buf[e->parity_host[c]]) + (size_t)c * bytes, bytes,
+                                 cudaMemcpyDeviceToDevice, e->stream));
+    }
+    if (n_s > 0) {
+        LBM_CUDA(cudaMemcpyAsync(e->list_dev, list.data(), sizeof(int32_t) * n_s, cudaMemcpyHostToDevice, e->stream));
+        int rc = compute_masses(e, e->list_dev, n_s);
+        if (rc) return rc;
+        // gather the masses of the listed clones into the bank, in bank order
+        std::vector<double> m(e->n);
+        LBM_CUDA(cudaMemcpyAsync(m.data(), e->mass_dev, sizeof(double) * e->n, cudaMemcpyDeviceToHost, e->stream));
+        LBM_CUDA(cudaStreamSynchronize(e->stream));
+        std::vector<double> sm(n_s);
+        for (int k = 0; k < n_s; ++k) sm[k] = m[list[k]];
+        LBM_CUDA(cudaMemcpyAsync(e->snap_mass, sm.data(), sizeof(double) * n_s, cudaMemcpyHostToDevice, e->stream));
+        LBM_CUDA(cudaStreamSynchronize(e->stream));
+    }
+    e->n_snaps_set = n_s;
+    return LBM_OK;
+}
+
+int lbm_ensemble_clone(lbm_ensemble* e, const int32_t* parent_dev, double eps, uint64_t seed, uint64_t iter)
+{
+    if (!e || !parent_dev) return fail(LBM_ERR_ARG, "null argument");
+    if (!std::isfinite(eps) || eps < 0.0) return fail(LBM_ERR_ARG, "eps must be finite and >= 0");
+    if (eps != 0.0 && e->n_snaps_set < 1) return fail(LBM_ERR_STATE, "perturbation needs the snapshot bank");
+    const int32_t t = e->t_host[0];
+    for (int i = 1; i < e->n; ++i)
+        if (e->t_host[i] != t || e->parity_host[i] != e->parity_host[0])
+            return fail(LBM_ERR_STATE, "cloning needs every clone at the same time");
+    if (eps != 0.0) {
+        int rc = compute_masses(e, e->all_dev, e->n);
+        if (rc) return rc;
+    }
+    int rc = run_perturb(e, parent_dev, -1, eps, seed, iter);
+    if (rc) return rc;
+    if (t > 0) {
+        dim3 grid((unsigned)std::min(64, (t + 255) / 256), e->n);
+        copy_history_kernel<<<grid, 256, 0, e->stream>>>(e->drag, e->cfg.max_steps, parent_dev, e->n, t);
+        count_launches(1);
+        LBM_CUDA(cudaGetLastError());
+    }
+    return LBM_OK;
+}
+
+int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, double eps, uint64_t seed,
+                        uint64_t iter)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    if (dst < 0 || dst >= e->n || src < 0 || src >= e->n || dst == src) return fail(LBM_ERR_ARG, "bad clone indices");
+    if (e->cfg.ckpt_stride <= 0) return fail(LBM_ERR_STATE, "branching needs checkpoints (ckpt_stride > 0)");
+    if (t_b < 0 || t_b > e->t_host[src]) return fail(LBM_ERR_ARG, "branch time beyond the source trajectory");
+    if (!std::isfinite(eps) || eps < 0.0) return fail(LBM_ERR_ARG, "eps must be finite and >= 0");
+    if (eps != 0.0 && e->n_snaps_set < 1) return fail(LBM_ERR_STATE, "perturbation needs the snapshot bank");
+    const int kc = t_b / e->cfg.ckpt_stride;
+    const int32_t tc = kc * e->cfg.ckpt_stride;
+    if (kc >= e->n_ckpt) return fail(LBM_ERR_ARG, "no checkpoint covers the branch time");
+    const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+    char* ck = static_cast<char*>(e->ckpt);
+    // checkpoints 0..kc and the state at tc
+    for (int k = 0; k <= kc; ++k)
+        LBM_CUDA(cudaMemcpyAsync(ck + ((size_t)dst * e->n_ckpt + k) * bytes, ck + ((size_t)src * e->n_ckpt + k) * bytes,
+                                 bytes, cudaMemcpyDeviceToDevice, e->stream));
+    LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(e->buf[e->parity_host[dst]]) + (size_t)dst * bytes,
+                             ck + ((size_t)src * e->n_ckpt + kc) * bytes, bytes, cudaMemcpyDeviceToDevice, e->stream));
+    if (t_b > 0)
+        LBM_CUDA(cudaMemcpyAsync(e->drag + (size_t)dst * e->cfg.max_steps, e->drag + (size_t)src * e->cfg.max_steps,
+                                 sizeof(double) * t_b, cudaMemcpyDeviceToDevice, e->stream));
+    // dst is now the source at time tc; replay to t_b (bitwise the source's path)
+    e->t_host[dst] = tc;
+    LBM_CUDA(cudaMemcpyAsync(e->t_dev + dst, &e->t_host[dst], sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    if (t_b > tc) {
+        int rc = lbm_ensemble_step_clones(e, t_b - tc, &dst, 1);
+        if (rc) return rc;
+    }
+    if (eps != 0.0) {
+        LBM_CUDA(cudaMemcpyAsync(e->list_dev, &dst, sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
+        int rc = compute_masses(e, e->list_dev, 1);
+        if (rc) return rc;
+        rc = run_perturb(e, e->all_dev, dst, eps, seed, iter);
+        if (rc) return rc;
+        LBM_CUDA(cudaStreamSynchronize(e->stream));
+    }
+    return LBM_OK;
+}
+
+int lbm_ensemble_moments(lbm_ensemble* e, double* mass, double* px, double* py)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    int rc = compute_masses(e, e->all_dev, e->n);
+    if (rc) return rc;
+    std::vector<double> h(3 * (size_t)e->n);
+    LBM_CUDA(cudaMemcpyAsync(h.data(), e->mass_dev, sizeof(double) * 3 * e->n, cudaMemcpyDeviceToHost, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    for (int i = 0; i < e->n; ++i) {
+        if (mass) mass[i] = h[i];
+        if (px) px[i] = h[e->n + i];
+        if (py) py[i] = h[2 * e->n + i];
+    }
+    return LBM_OK;
+}
+
+namespace {
+double decode_host(int storage, const void* raw, size_t idx, int q, float inv_scale)
+{
+    const double w = wd(q);
+    if (storage == kFP32) return (double)static_cast<const float*>(raw)[idx];
+    if (storage == kFP16) return w + (double)__half2float(static_cast<const __half*>(raw)[idx]) * inv_scale;
+    return w + (double)__bfloat162float(static_cast<const __nv_bfloat16*>(raw)[idx]) * inv_scale;
+}
+}  // namespace
+
+int lbm_ensemble_get_populations(lbm_ensemble* e, int32_t clone, double* host)
+{
+    if (!e || !host) return fail(LBM_ERR_ARG, "null argument");
+    if (clone < 0 || clone >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
+    const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+    std::vector<char> raw(bytes);
+    LBM_CUDA(cudaMemcpyAsync(raw.data(), static_cast<char*>(e->buf[e->parity_host[clone]]) + (size_t)clone * bytes,
+                             bytes, cudaMemcpyDeviceToHost, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    const int nx = e->cfg.nx, ny = e->cfg.ny;
+    for (int q = 0; q < 9; ++q)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x)
+                host[((size_t)q * ny + y) * nx + x] =
+                    decode_host(e->cfg.storage, raw.data(), (size_t)q * e->plane + (size_t)y * e->pitch + x, q, e->inv_scale);
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_populations(lbm_ensemble* e, int32_t clone, const double* host)
+{
+    if (!e || !host) return fail(LBM_ERR_ARG, "null argument");
+    if (clone < 0 || clone >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
+    const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+    std::vector<char> raw(bytes, 0);
+    const int nx = e->cfg.nx, ny = e->cfg.ny;
+    for (int q = 0; q < 9; ++q)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const double f = host[((size_t)q * ny + y) * nx + x];
+                if (!std::isfinite(f)) return fail(LBM_ERR_NONFINITE, "population not finite");
+                const size_t idx = (size_t)q * e->plane + (size_t)y * e->pitch + x;
+                if (e->cfg.storage == kFP32)
+                    reinterpret_cast<float*>(raw.data())[idx] = (float)f;
+                else if (e->cfg.storage == kFP16)
+                    reinterpret_cast<__half*>(raw.data())[idx] = __float2half_rn((float)((f - wd(q)) * e->scale));
+                else
+                    reinterpret_cast<__nv_bfloat16*>(raw.data())[idx] = __float2bfloat16_rn((float)((f - wd(q)) * e->scale));
+            }
+    LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(e->buf[e->parity_host[clone]]) + (size_t)clone * bytes, raw.data(),
+                             bytes, cudaMemcpyHostToDevice, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    if (variant == -1) {
+        e->variant = default_variant(e->cfg.storage);
+        return LBM_OK;
+    }
+    const auto& v = step_variants();
+    if (variant < 0 || variant >= (int32_t)v.size()) return fail(LBM_ERR_ARG, "variant index out of range");
+    if (v[variant].storage != e->cfg.storage) return fail(LBM_ERR_ARG, "variant is for another storage format");
+    e->variant = variant;
+    return LBM_OK;
+}
+
+int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    const auto& vars = step_variants();
+    std::vector<int32_t> all(e->n);
+    cudaEvent_t a, b;
+    LBM_CUDA(cudaEventCreate(&a));
+    LBM_CUDA(cudaEventCreate(&b));
+    float best_ms = std::numeric_limits<float>::infinity();
+    int best = e->variant;
+    // Every trial launch reads the current buffer and rewrites the other one
+    // at step_in_batch 0: the state does not advance and no drag is recorded.
+    for (size_t i = 0; i < vars.size(); ++i) {
+        const StepVariant& v = vars[i];
+        if (v.storage != e->cfg.storage) continue;
+        const int nseg = (e->cfg.nx + 32 * v.vec - 1) / (32 * v.vec);
+        const int64_t warps = (int64_t)e->n * e->cfg.ny * nseg;
+        const int grid = (int)((warps + v.warps - 1) / v.warps);
+        StepParams p = make_params(e, e->all_dev, e->n, v.vec, 0);
+        const int reps = 5;
+        for (int r = 0; r < 2; ++r) LBM_CUDA(v.launch(p, grid, e->stream));
+        LBM_CUDA(cudaEventRecord(a, e->stream));
+        for (int r = 0; r < reps; ++r) LBM_CUDA(v.launch(p, grid, e->stream));
+        count_launches(2 + reps);
+        LBM_CUDA(cudaEventRecord(b, e->stream));
+        LBM_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        LBM_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = (int)i;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    e->variant = best;
+    if (variant) *variant = best;
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_timing(lbm_ensemble* e, int32_t enable)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    e->timing = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_ensemble_kernel_time(lbm_ensemble* e, double* ms, int64_t* launches, int32_t reset)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    for (auto& pr : e->events) {
+        float t = 0.f;
+        LBM_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+        e->timed_ms += t;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    e->events.clear();
+    if (ms) *ms = e->timed_ms;
+    if (launches) *launches = e->timed_launches;
+    if (reset) {
+        e->timed_ms = 0.0;
+        e->timed_launches = 0;
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"

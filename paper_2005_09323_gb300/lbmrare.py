@@ -1,0 +1,271 @@
+"""ctypes binding of liblbmrare (include/lbmrare.h): argument marshalling only.
+
+Every function keeps the C name and argument order.  Device pointers are
+passed as torch CUDA tensors (checked for device, dtype and contiguity), host
+arrays as numpy arrays; errors raise ``LbmError`` carrying the status and the
+library's message.  The library must have been built (``build.build()``);
+there is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_OOM, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2
+STORAGE = {"fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
+
+EXPORTS = [
+    "lbm_last_error", "lbm_launch_count", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_step",
+    "lbm_ensemble_step_clones", "lbm_ensemble_time", "lbm_ensemble_drag", "lbm_ensemble_window_sum",
+    "lbm_ensemble_scores", "lbm_ensemble_first_crossing", "lbm_ensemble_set_snapshots", "lbm_ensemble_clone",
+    "lbm_ensemble_branch", "lbm_ensemble_moments", "lbm_ensemble_get_populations",
+    "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
+    "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
+    "gktl_weights", "gktl_select", "ams_select",
+]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"lbmrare status {status}: {message}")
+        self.status = status
+
+
+class lbm_config(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("obs_x0", C.c_int32), ("obs_y0", C.c_int32),
+                ("obs_w", C.c_int32), ("obs_h", C.c_int32), ("tau", C.c_double), ("gx", C.c_double),
+                ("gy", C.c_double), ("storage", C.c_int32), ("shift_exp", C.c_int32), ("max_steps", C.c_int32),
+                ("ckpt_stride", C.c_int32), ("n_snapshots", C.c_int32), ("init_amp", C.c_double)]
+
+
+def config(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, storage="fp32", shift_exp=0,
+           max_steps=1000, ckpt_stride=0, n_snapshots=0, init_amp=0.01) -> lbm_config:
+    ox0, oy0, ow, oh = obstacle
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    return lbm_config(nx, ny, ox0, oy0, ow, oh, tau, gx, gy, st, shift_exp, max_steps, ckpt_stride,
+                      n_snapshots, init_amp)
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load liblbmrare.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build it with paper_2005_09323_gb300.build.build()")
+        L = C.CDLL(_build.LIB)
+        i32, i64, u64, d, p = C.c_int32, C.c_int64, C.c_uint64, C.c_double, C.c_void_p
+        sig = {
+            "lbm_last_error": ([], C.c_char_p),
+            "lbm_launch_count": ([], i64),
+            "lbm_ensemble_create": ([p, i32, u64, p, p], C.c_int),
+            "lbm_ensemble_destroy": ([p], C.c_int),
+            "lbm_ensemble_step": ([p, i32], C.c_int),
+            "lbm_ensemble_step_clones": ([p, i32, p, i32], C.c_int),
+            "lbm_ensemble_time": ([p, p], C.c_int),
+            "lbm_ensemble_drag": ([p, i32, i32, p, i32], C.c_int),
+            "lbm_ensemble_window_sum": ([p, i32, i32, d, p], C.c_int),
+            "lbm_ensemble_scores": ([p, i32, i32, p], C.c_int),
+            "lbm_ensemble_first_crossing": ([p, i32, d, p], C.c_int),
+            "lbm_ensemble_set_snapshots": ([p, i32, p], C.c_int),
+            "lbm_ensemble_clone": ([p, p, d, u64, u64], C.c_int),
+            "lbm_ensemble_branch": ([p, i32, i32, i32, d, u64, u64], C.c_int),
+            "lbm_ensemble_moments": ([p, p, p, p], C.c_int),
+            "lbm_ensemble_get_populations": ([p, i32, p], C.c_int),
+            "lbm_ensemble_set_populations": ([p, i32, p], C.c_int),
+            "lbm_ensemble_autotune": ([p, p], C.c_int),
+            "lbm_ensemble_set_variant": ([p, i32], C.c_int),
+            "lbm_step_variant_info": ([i32, p, p, p], C.c_int),
+            "lbm_step_variant_count": ([], i32),
+            "lbm_ensemble_set_timing": ([p, i32], C.c_int),
+            "lbm_ensemble_kernel_time": ([p, p, p, i32], C.c_int),
+            "gktl_weights": ([i32, p, p, p, p], C.c_int),
+            "gktl_select": ([i32, p, u64, u64, p, p, p], C.c_int),
+            "ams_select": ([i32, p, u64, u64, p, p, p, p, p], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != LBM_OK:
+        raise LbmError(rc, lib().lbm_last_error().decode())
+
+
+def _dev(t, dtype):
+    """device pointer of a contiguous torch CUDA tensor of the given dtype (None -> NULL)"""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a torch CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def lbm_launch_count() -> int:
+    return lib().lbm_launch_count()
+
+
+# ---------------------------------------------------------------- ensemble
+def lbm_ensemble_create(cfg: lbm_config, n_clones: int, seed: int, stream=None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().lbm_ensemble_create(C.byref(cfg), n_clones, seed, _stream(stream), C.byref(h)))
+    return h
+
+
+def lbm_ensemble_destroy(e):
+    _check(lib().lbm_ensemble_destroy(e))
+
+
+def lbm_ensemble_step(e, n_steps: int):
+    _check(lib().lbm_ensemble_step(e, n_steps))
+
+
+def lbm_ensemble_step_clones(e, n_steps: int, clones):
+    a = np.ascontiguousarray(clones, dtype=np.int32)
+    _check(lib().lbm_ensemble_step_clones(e, n_steps, _host(a), len(a)))
+
+
+def lbm_ensemble_time(e, n: int) -> np.ndarray:
+    t = np.zeros(n, dtype=np.int32)
+    _check(lib().lbm_ensemble_time(e, _host(t)))
+    return t
+
+
+def lbm_ensemble_drag(e, t0: int, t1: int, dst):
+    """dst: numpy float64 [N, t1-t0] (host, waits) or torch float64 CUDA tensor (enqueued)."""
+    if isinstance(dst, np.ndarray):
+        if dst.dtype != np.float64 or not dst.flags.c_contiguous:
+            raise TypeError("dst must be a contiguous float64 array")
+        _check(lib().lbm_ensemble_drag(e, t0, t1, _host(dst), 0))
+    else:
+        import torch
+        _check(lib().lbm_ensemble_drag(e, t0, t1, _dev(dst, torch.float64), 1))
+    return dst
+
+
+def lbm_ensemble_window_sum(e, t0: int, t1: int, k: float, out_dev):
+    import torch
+    _check(lib().lbm_ensemble_window_sum(e, t0, t1, k, _dev(out_dev, torch.float64)))
+
+
+def lbm_ensemble_scores(e, window: int, t_end: int, out_dev=None):
+    import torch
+    _check(lib().lbm_ensemble_scores(e, window, t_end, _dev(out_dev, torch.float64)))
+
+
+def lbm_ensemble_first_crossing(e, clone: int, level: float) -> int:
+    t = C.c_int32()
+    _check(lib().lbm_ensemble_first_crossing(e, clone, level, C.byref(t)))
+    return t.value
+
+
+def lbm_ensemble_set_snapshots(e, clones):
+    a = np.ascontiguousarray(clones, dtype=np.int32)
+    _check(lib().lbm_ensemble_set_snapshots(e, len(a), _host(a)))
+
+
+def lbm_ensemble_clone(e, parent_dev, eps: float, seed: int, it: int):
+    import torch
+    _check(lib().lbm_ensemble_clone(e, _dev(parent_dev, torch.int32), eps, seed, it))
+
+
+def lbm_ensemble_branch(e, dst: int, src: int, t_b: int, eps: float, seed: int, it: int):
+    _check(lib().lbm_ensemble_branch(e, dst, src, t_b, eps, seed, it))
+
+
+def lbm_ensemble_moments(e, n: int):
+    m = np.zeros(n); px = np.zeros(n); py = np.zeros(n)
+    _check(lib().lbm_ensemble_moments(e, _host(m), _host(px), _host(py)))
+    return m, px, py
+
+
+def lbm_ensemble_get_populations(e, clone: int, nx: int, ny: int) -> np.ndarray:
+    f = np.zeros((9, ny, nx))
+    _check(lib().lbm_ensemble_get_populations(e, clone, _host(f)))
+    return f
+
+
+def lbm_ensemble_set_populations(e, clone: int, f: np.ndarray):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(lib().lbm_ensemble_set_populations(e, clone, _host(f)))
+
+
+def lbm_ensemble_autotune(e) -> int:
+    v = C.c_int32()
+    _check(lib().lbm_ensemble_autotune(e, C.byref(v)))
+    return v.value
+
+
+def lbm_ensemble_set_variant(e, variant: int):
+    _check(lib().lbm_ensemble_set_variant(e, variant))
+
+
+def lbm_step_variant_count() -> int:
+    return lib().lbm_step_variant_count()
+
+
+def lbm_step_variant_info(variant: int):
+    s, v, w = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().lbm_step_variant_info(variant, C.byref(s), C.byref(v), C.byref(w)))
+    return s.value, v.value, w.value
+
+
+def lbm_ensemble_set_timing(e, enable: bool):
+    _check(lib().lbm_ensemble_set_timing(e, int(bool(enable))))
+
+
+def lbm_ensemble_kernel_time(e, reset: bool = False):
+    ms = C.c_double()
+    n = C.c_int64()
+    _check(lib().lbm_ensemble_kernel_time(e, C.byref(ms), C.byref(n), int(bool(reset))))
+    return ms.value, n.value
+
+
+# ---------------------------------------------------------------- selection
+def gktl_weights(s_dev, W_dev, logR_dev, stream=None):
+    import torch
+    _check(lib().gktl_weights(s_dev.numel(), _dev(s_dev, torch.float64), _dev(W_dev, torch.float64),
+                              _dev(logR_dev, torch.float64), _stream(stream)))
+
+
+def gktl_select(W_dev, seed: int, it: int, parent_dev, status_dev=None, stream=None):
+    import torch
+    _check(lib().gktl_select(W_dev.numel(), _dev(W_dev, torch.float64), seed, it, _dev(parent_dev, torch.int32),
+                             _dev(status_dev, torch.int32), _stream(stream)))
+
+
+def ams_select(Q_dev, seed: int, it: int, killed_dev, n_killed_dev, survivor_dev, level_dev, stream=None):
+    import torch
+    _check(lib().ams_select(Q_dev.numel(), _dev(Q_dev, torch.float64), seed, it, _dev(killed_dev, torch.int32),
+                            _dev(n_killed_dev, torch.int32), _dev(survivor_dev, torch.int32),
+                            _dev(level_dev, torch.float64), _stream(stream)))

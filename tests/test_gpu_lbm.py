@@ -1,0 +1,320 @@
+"""GPU parity of the fused lattice-Boltzmann step, drag, reductions, cloning
+and branching against the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 arithmetic and storage): populations 1e-5 relative to their
+largest value, drag series 1e-4 relative to its largest magnitude over the
+first 200 steps.  Reduced-precision storage is compared against FP64 with
+bounds derived from the 16-bit format (see each test)."""
+import numpy as np
+import pytest
+import torch
+
+from tests import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL = 1e-5
+DRAG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2005_09323_gb300 import build, lbmrare
+    build.build()
+    lbmrare.lib()
+    assert torch.cuda.is_available()
+    return lbmrare
+
+
+class Ens:
+    """create/destroy around the C handle"""
+
+    def __init__(self, L, n, seed=0, **kw):
+        self.L = L
+        self.kw = kw
+        self.n = n
+        self.cfg = L.config(**kw)
+        self.stream = torch.cuda.current_stream()
+        self.h = L.lbm_ensemble_create(self.cfg, n, seed, self.stream)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.L.lbm_ensemble_destroy(self.h)
+
+    def pops(self, c):
+        return self.L.lbm_ensemble_get_populations(self.h, c, self.cfg.nx, self.cfg.ny)
+
+    def drag(self, t0, t1):
+        d = np.zeros((self.n, t1 - t0))
+        self.L.lbm_ensemble_drag(self.h, t0, t1, d)
+        return d
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def oracle_cfg(orc, kw):
+    return orc.cfg(kw["nx"], kw["ny"], obstacle=kw.get("obstacle", (0, 0, 0, 0)), tau=kw.get("tau", 0.6),
+                   gx=kw.get("gx", 0.0), gy=kw.get("gy", 0.0))
+
+
+CFG1 = dict(nx=256, ny=64, obstacle=si.channel(256, 64, 8, 64), tau=0.52, gx=1e-6, max_steps=2000)
+RAGGED = dict(nx=200, ny=37, obstacle=(50, 14, 9, 7), tau=0.6, gx=2e-5, gy=-5e-6, max_steps=400)
+
+
+def test_init_matches_oracle(L, orc):
+    with Ens(L, 3, seed=5, **RAGGED, init_amp=0.02) as e:
+        oc = oracle_cfg(orc, RAGGED)
+        for c in range(3):
+            ref = orc.init(oc, 5, c, 0.02)
+            assert np.abs(e.pops(c) - ref).max() < 1e-7
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_cfg1_200_steps_match_oracle(L, orc, seed):
+    """256 x 64 channel, 8 x 8 obstacle at (64, 32), tau 0.52, g 1e-6: FP32
+    populations and drag over 200 steps against FP64."""
+    with Ens(L, 1, seed=seed, **CFG1) as e:
+        L.lbm_ensemble_step(e.h, 200)
+        oc = oracle_cfg(orc, CFG1)
+        f_ref, d_ref = orc.run(oc, orc.init(oc, seed, 0, 0.01), 200)
+        assert rel(e.pops(0), f_ref) < POP_TOL
+        assert rel(e.drag(0, 200)[0], d_ref) < DRAG_TOL
+
+
+def test_every_variant_on_ragged_grid(L, orc):
+    """nx = 200 (not a multiple of the warp width in sites), ny = 37, obstacle
+    away from the centre, force with both components: every compiled FP32
+    variant against the oracle over 60 steps, several clones."""
+    oc = oracle_cfg(orc, RAGGED)
+    refs = [orc.run(oc, orc.init(oc, 9, c, 0.01), 60) for c in range(3)]
+    n_var = L.lbm_step_variant_count()
+    tried = 0
+    for v in range(n_var):
+        st, vec, warps = L.lbm_step_variant_info(v)
+        if st != 0:
+            continue
+        with Ens(L, 3, seed=9, **RAGGED) as e:
+            L.lbm_ensemble_set_variant(e.h, v)
+            L.lbm_ensemble_step(e.h, 60)
+            d = e.drag(0, 60)
+            for c in range(3):
+                assert rel(e.pops(c), refs[c][0]) < POP_TOL, (vec, warps, c)
+                assert rel(d[c], refs[c][1]) < DRAG_TOL, (vec, warps, c)
+        tried += 1
+    assert tried >= 3
+
+
+def test_one_step_from_arbitrary_state(L, orc):
+    """A single step from a non-equilibrium state loaded into the GPU."""
+    kw = dict(nx=96, ny=20, obstacle=(30, 7, 5, 6), tau=0.8, gx=1e-4, gy=2e-5, max_steps=10)
+    oc = oracle_cfg(orc, kw)
+    rng = np.random.default_rng(3)
+    f = orc.init(oc, 1, 0, 0.05) * (1 + 0.01 * rng.standard_normal((9, 20, 96)))
+    f[:, orc.solid_mask(oc)] = orc.feq(1.0, 0.0, 0.0)[:, None]
+    with Ens(L, 2, **kw) as e:
+        L.lbm_ensemble_set_populations(e.h, 1, f)
+        L.lbm_ensemble_step(e.h, 1)
+        g, fo, _ = orc.step(oc, f)
+        assert rel(e.pops(1), g) < 1e-6
+        assert abs(e.drag(0, 1)[1, 0] - fo[0]) < 1e-5 * abs(fo[0]) + 1e-9
+
+
+def test_no_obstacle_and_obstacle_on_wall(L, orc):
+    for obst in [(0, 0, 0, 0), (20, 0, 6, 5)]:
+        kw = dict(nx=64, ny=16, obstacle=obst, tau=0.7, gx=1e-5, max_steps=50)
+        oc = oracle_cfg(orc, kw)
+        with Ens(L, 1, seed=4, **kw) as e:
+            L.lbm_ensemble_step(e.h, 40)
+            f_ref, d_ref = orc.run(oc, orc.init(oc, 4, 0, 0.01), 40)
+            assert rel(e.pops(0), f_ref) < POP_TOL
+            if obst[2]:
+                assert rel(e.drag(0, 40)[0], d_ref) < DRAG_TOL
+            else:
+                assert np.all(e.drag(0, 40) == 0.0)
+
+
+def test_minimum_width_channel(L, orc):
+    kw = dict(nx=8, ny=4, tau=0.9, gx=1e-4, max_steps=30)
+    oc = oracle_cfg(orc, kw)
+    with Ens(L, 1, seed=2, **kw) as e:
+        L.lbm_ensemble_step(e.h, 30)
+        f_ref, _ = orc.run(oc, orc.init(oc, 2, 0, 0.01), 30)
+        assert rel(e.pops(0), f_ref) < POP_TOL
+
+
+def test_mass_conserved_and_moments(L, orc):
+    with Ens(L, 2, seed=1, **CFG1) as e:
+        m0, px0, py0 = L.lbm_ensemble_moments(e.h, 2)
+        oc = oracle_cfg(orc, CFG1)
+        for c in range(2):
+            mr, pxr, pyr = orc.moments(oc, orc.init(oc, 1, c, 0.01))
+            assert abs(m0[c] - mr) < 1e-9 * mr
+            assert abs(px0[c] - pxr) < 1e-6 and abs(py0[c] - pyr) < 1e-6
+        L.lbm_ensemble_step(e.h, 1000)
+        m1, _, _ = L.lbm_ensemble_moments(e.h, 2)
+        # FP32 storage: each step rounds every population (2^-24 relative);
+        # the mass performs a random walk far below this bound
+        assert np.all(np.abs(m1 - m0) / m0 < 1e-5)
+
+
+def test_window_sum_and_scores_match_oracle(L, orc):
+    kw = dict(RAGGED, max_steps=300)
+    with Ens(L, 4, seed=3, **kw) as e:
+        L.lbm_ensemble_step(e.h, 300)
+        d = e.drag(0, 300)
+        out = torch.zeros(4, dtype=torch.float64, device="cuda")
+        L.lbm_ensemble_window_sum(e.h, 100, 250, 3.5, out)
+        ref = orc.window_sum(d, 100, 250, 3.5)
+        assert np.allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-15)
+        for window, t_end in [(50, 300), (7, 123), (300, 300), (301, 300)]:
+            q = torch.zeros(4, dtype=torch.float64, device="cuda")
+            L.lbm_ensemble_scores(e.h, window, t_end, q)
+            ref = orc.trailing_mean_max(d, window, t_end)
+            got = q.cpu().numpy()
+            if window > t_end:
+                assert np.all(np.isneginf(got))
+            else:
+                assert np.allclose(got, ref, rtol=1e-11, atol=1e-14)
+        # first crossing of the last scores: brute force on the host series
+        L.lbm_ensemble_scores(e.h, 20, 300, None)
+        means = np.array([[d[c, t - 20:t].mean() for t in range(20, 301)] for c in range(4)])
+        for c in range(4):
+            level = np.quantile(means[c], 0.8)
+            t = L.lbm_ensemble_first_crossing(e.h, c, level)
+            idx = np.nonzero(means[c] > level * (1 + 1e-12) + 1e-18)[0]
+            assert t == 20 + idx[0] or abs(means[c][t - 20] - level) < 1e-12 * abs(level)
+            assert L.lbm_ensemble_first_crossing(e.h, c, means[c].max() + 1.0) == -1
+
+
+def test_subset_step_equals_full_step(L):
+    kw = dict(RAGGED, max_steps=100)
+    with Ens(L, 4, seed=8, **kw) as a, Ens(L, 4, seed=8, **kw) as b:
+        L.lbm_ensemble_step(a.h, 30)
+        for c in [2, 0]:
+            L.lbm_ensemble_step_clones(b.h, 30, [c])
+        for c in [0, 2]:
+            assert np.array_equal(a.pops(c), b.pops(c))
+        assert np.array_equal(a.drag(0, 30)[[0, 2]], b.drag(0, 30)[[0, 2]])
+        assert list(L.lbm_ensemble_time(b.h, 4)) == [30, 0, 30, 0]
+
+
+def test_clone_exact_copy_and_perturbation(L, orc):
+    kw = dict(RAGGED, max_steps=100, n_snapshots=3)
+    oc = oracle_cfg(orc, kw)
+    with Ens(L, 5, seed=2, **kw) as e:
+        L.lbm_ensemble_step(e.h, 20)
+        before = [e.pops(c) for c in range(5)]
+        hist = e.drag(0, 20)
+        parent = torch.tensor([0, 0, 2, 2, 4], dtype=torch.int32, device="cuda")
+        L.lbm_ensemble_clone(e.h, parent, 0.0, 1, 0)
+        assert np.array_equal(e.pops(1), before[0])
+        assert np.array_equal(e.pops(3), before[2])
+        assert np.array_equal(e.pops(4), before[4])
+        h2 = e.drag(0, 20)
+        assert np.array_equal(h2[1], hist[0]) and np.array_equal(h2[3], hist[2])
+        # App. D perturbation with a snapshot bank of three states
+        L.lbm_ensemble_set_snapshots(e.h, [4, 2, 0])
+        snaps = np.stack([before[4], before[2], before[0]])
+        parent = torch.tensor([0, 4, 2, 3, 4], dtype=torch.int32, device="cuda")
+        L.lbm_ensemble_clone(e.h, parent, 0.002, 77, 5)
+        alpha = orc.perturb_alphas(77, 5, 1, 3)
+        ref = orc.perturb(oc, before[4], snaps, alpha, 0.002)
+        got = e.pops(1)
+        assert rel(got, ref) < 1e-6
+        m_ref, _, _ = orc.moments(oc, before[4])
+        m_got, _, _ = orc.moments(oc, got)
+        assert abs(m_got - m_ref) / m_ref < 1e-6
+        assert np.array_equal(e.pops(3), before[3])  # kept its own slot
+
+
+def test_branch_replays_bitwise(L):
+    """AMS branching restores the last checkpoint and replays: with eps = 0 the
+    branch is the source trajectory, state and drag, bit for bit."""
+    kw = dict(RAGGED, max_steps=200, ckpt_stride=25, n_snapshots=2)
+    with Ens(L, 3, seed=6, **kw) as e:
+        L.lbm_ensemble_step(e.h, 120)
+        src_state = None
+        L.lbm_ensemble_branch(e.h, 1, 2, 87, 0.0, 3, 1)
+        assert list(L.lbm_ensemble_time(e.h, 3)) == [120, 87, 120]
+        L.lbm_ensemble_step_clones(e.h, 33, [1])
+        assert np.array_equal(e.pops(1), e.pops(2))
+        d = e.drag(0, 120)
+        assert np.array_equal(d[1], d[2])
+        # with a perturbation the branch departs from the source after t_b
+        L.lbm_ensemble_set_snapshots(e.h, [0, 2])
+        L.lbm_ensemble_branch(e.h, 1, 2, 50, 0.002, 3, 2)
+        L.lbm_ensemble_step_clones(e.h, 70, [1])
+        d = e.drag(0, 120)
+        assert np.array_equal(d[1, :50], d[2, :50])
+        assert not np.array_equal(d[1, 50:], d[2, 50:])
+
+
+def test_nonfinite_state_is_reported(L):
+    kw = dict(nx=64, ny=16, obstacle=(20, 5, 6, 6), tau=0.6, max_steps=20)
+    with Ens(L, 2, **kw) as e:
+        f = e.pops(0)
+        f[3, 5, 18] = np.inf
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_ensemble_set_populations(e.h, 0, f)
+        assert ei.value.status == L.LBM_ERR_NONFINITE
+        # finite in FP32 but the density of the node next to the obstacle
+        # overflows at the next collision: the drag becomes NaN
+        f = e.pops(0)
+        f[:, 6, 19] = 3e38
+        L.lbm_ensemble_set_populations(e.h, 0, f)
+        L.lbm_ensemble_step(e.h, 10)
+        with pytest.raises(L.LbmError) as ei:
+            e.drag(0, 10)
+        assert ei.value.status == L.LBM_ERR_NONFINITE
+
+
+def test_argument_errors(L):
+    with Ens(L, 2, **dict(RAGGED, max_steps=10)) as e:
+        with pytest.raises(L.LbmError):
+            L.lbm_ensemble_step(e.h, 11)
+        with pytest.raises(L.LbmError):
+            L.lbm_ensemble_step_clones(e.h, 1, [0, 0])
+        with pytest.raises(L.LbmError):
+            L.lbm_ensemble_step_clones(e.h, 1, [2])
+        L.lbm_ensemble_step_clones(e.h, 2, [1])
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_ensemble_step(e.h, 1)
+        assert ei.value.status == L.LBM_ERR_STATE
+        with pytest.raises(L.LbmError):
+            e.drag(0, 5)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 3e-3), ("bf16", 3e-2)])
+def test_reduced_precision_storage(L, orc, storage, tol):
+    """Shifted 16-bit storage: g = f - w in FP16 (11-bit significand) or BF16
+    (8-bit); populations after 200 steps stay within tol of the FP64 oracle
+    relative to the largest |f - w| of the flow."""
+    with Ens(L, 1, seed=0, storage=storage, **CFG1) as e:
+        L.lbm_ensemble_step(e.h, 200)
+        oc = oracle_cfg(orc, CFG1)
+        f_ref, d_ref = orc.run(oc, orc.init(oc, 0, 0, 0.01), 200)
+        w = orc.feq(1.0, 0.0, 0.0)[:, None, None]
+        g_ref = f_ref - w
+        err = np.abs(e.pops(0) - f_ref).max() / np.abs(g_ref).max()
+        assert err < tol
+        assert np.all(np.isfinite(e.drag(0, 200)))
+
+
+def test_full_size_sampled_parity(L, orc):
+    """The GKTL workload's launch shape: 64 clones of 1024 x 256 with a 32 x 32
+    obstacle at x = 256, tau 0.505; two sampled clones against the oracle
+    over 20 steps."""
+    kw = dict(nx=1024, ny=256, obstacle=si.channel(1024, 256, 32, 256), tau=0.505, gx=1e-6, max_steps=40)
+    with Ens(L, 64, seed=12, **kw) as e:
+        L.lbm_ensemble_autotune(e.h)
+        L.lbm_ensemble_step(e.h, 20)
+        d = e.drag(0, 20)
+        oc = oracle_cfg(orc, kw)
+        for c in (0, 63):
+            f_ref, d_ref = orc.run(oc, orc.init(oc, 12, c, 0.01), 20)
+            assert rel(e.pops(c), f_ref) < POP_TOL
+            assert rel(d[c], d_ref) < DRAG_TOL
