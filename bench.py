@@ -180,9 +180,10 @@ def run_reference(args):
 
 
 def workload_config(args):
-    return {"workload": f"GKTL batched ensemble: N={N_CLONES} clones, D2Q9 LBGK FP32, {NX}x{NY}, "
+    n = getattr(args, "clones", N_CLONES)
+    return {"workload": f"GKTL batched ensemble: N={n} clones, D2Q9 LBGK FP32, {NX}x{NY}, "
                         f"32x32 obstacle at x=256, tau={TAU}, g_x={GX}, resample every {PERIOD} steps",
-            "clones": N_CLONES, "grid": [NX, NY], "steps_per_period": PERIOD, "storage": "fp32",
+            "clones": n, "grid": [NX, NY], "steps_per_period": PERIOD, "storage": "fp32",
             "k_sigma": K_SIGMA, "eps": EPS, "n_snapshots": N_SNAP,
             "l2": "working set 1.21 GB of populations per ensemble (>> 129 MB L2); no flush needed",
             "parallelism": f"replicas x{args.gpus}"}
@@ -223,14 +224,15 @@ def run_ours(args):
     total_periods = args.warmup + args.steps + 2 * (args.warmup + args.steps) + 2
     cfg = L.config(NX, NY, obstacle=OBST, tau=TAU, gx=GX, max_steps=PERIOD * total_periods,
                    n_snapshots=N_SNAP, init_amp=0.01)
-    e = L.lbm_ensemble_create(cfg, N_CLONES, 1000 + rank, stream)
+    n_clones = args.clones
+    e = L.lbm_ensemble_create(cfg, n_clones, 1000 + rank, stream)
     variant = L.lbm_ensemble_autotune(e)
     vinfo = L.lbm_step_variant_info(variant)
     k = K_SIGMA / (SIGMA_DRAG * PERIOD)
-    s = torch.zeros(N_CLONES, dtype=torch.float64, device="cuda")
+    s = torch.zeros(n_clones, dtype=torch.float64, device="cuda")
     W = torch.zeros_like(s)
     logR = torch.zeros(1, dtype=torch.float64, device="cuda")
-    parent = torch.zeros(N_CLONES, dtype=torch.int32, device="cuda")
+    parent = torch.zeros(n_clones, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     state = {"t": 0, "it": 0}
 
@@ -279,9 +281,9 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: the drag series goes to
     # the host, the GKTL exponents are formed there and sent back, the parents
     # come back to the host
-    pinned_s = torch.zeros(N_CLONES, dtype=torch.float64).pin_memory()
-    pinned_p = torch.zeros(N_CLONES, dtype=torch.int32).pin_memory()
-    drag_host = np.zeros((N_CLONES, PERIOD))
+    pinned_s = torch.zeros(n_clones, dtype=torch.float64).pin_memory()
+    pinned_p = torch.zeros(n_clones, dtype=torch.int32).pin_memory()
+    drag_host = np.zeros((n_clones, PERIOD))
     e2e_steps = max(1, args.steps // 2)
 
     def e2e_period():
@@ -312,7 +314,7 @@ def run_ours(args):
         tt = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms, e2e_s = tt.tolist()
-    sites = N_CLONES * NX * NY
+    sites = n_clones * NX * NY
     updates = sites * PERIOD * args.steps * world
     value = updates / (ms / 1e3) / 1e9
     e2e_value = sites * PERIOD * e2e_steps * world / e2e_s / 1e9
@@ -333,8 +335,8 @@ def run_ours(args):
                          "kernel": f"step_kernel<fp32, vec={vinfo[1]}, warps={vinfo[2]}>",
                          "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_site": BYTES_PER_SITE,
                          "avg_launch_us": avg_launch_ms * 1e3},
-            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 8 * N_CLONES,
-                    "d2h_bytes_per_step": 8 * N_CLONES * PERIOD + 4 * N_CLONES},
+            "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 8 * n_clones,
+                    "d2h_bytes_per_step": 8 * n_clones * PERIOD + 4 * n_clones},
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -352,6 +354,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--clones", type=int, default=N_CLONES,
+                    help="ensemble size (default: the workload's 64; smaller only for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -228,7 +228,7 @@ def test_clone_exact_copy_and_perturbation(L, orc):
         m_ref, _, _ = orc.moments(oc, before[4])
         m_got, _, _ = orc.moments(oc, got)
         assert abs(m_got - m_ref) / m_ref < 1e-6
-        assert np.array_equal(e.pops(3), before[3])  # kept its own slot
+        assert np.array_equal(e.pops(3), before[2])  # kept its own slot (a copy of 2 since the first call)
 
 
 def test_branch_replays_bitwise(L):
