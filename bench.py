@@ -226,7 +226,11 @@ def run_ours(args):
                    n_snapshots=N_SNAP, init_amp=0.01)
     n_clones = args.clones
     e = L.lbm_ensemble_create(cfg, n_clones, 1000 + rank, stream)
-    variant = L.lbm_ensemble_autotune(e)
+    if args.variant == "auto":
+        variant = L.lbm_ensemble_autotune(e)
+    else:
+        variant = int(args.variant)
+        L.lbm_ensemble_set_variant(e, variant)
     vinfo = L.lbm_step_variant_info(variant)
     k = K_SIGMA / (SIGMA_DRAG * PERIOD)
     s = torch.zeros(n_clones, dtype=torch.float64, device="cuda")
@@ -354,6 +358,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--variant", default="auto",
+                    help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
     ap.add_argument("--clones", type=int, default=N_CLONES,
                     help="ensemble size (default: the workload's 64; smaller only for profiling captures)")
     args = ap.parse_args()

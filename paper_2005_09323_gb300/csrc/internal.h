@@ -49,7 +49,7 @@ struct StepVariant {
     int storage;
     int vec;    // sites per thread
     int warps;  // warps per block
-    cudaError_t (*launch)(const StepParams&, int grid, cudaStream_t);
+    cudaError_t (*launch)(const StepParams&, cudaStream_t);
 };
 
 // all compiled variants of the fused step (lbm_step.cu)

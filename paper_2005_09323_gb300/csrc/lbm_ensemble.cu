@@ -425,9 +425,6 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
     const auto& vars = step_variants();
     const StepVariant& v = vars[e->variant];
     const int n_list = (int)list.size();
-    const int nseg = (e->cfg.nx + 32 * v.vec - 1) / (32 * v.vec);
-    const int64_t warps = (int64_t)n_list * e->cfg.ny * nseg;
-    const int grid = (int)((warps + v.warps - 1) / v.warps);
     const Ring r = ring_for(e->cfg, v.vec);
     int32_t t = e->t_host[list[0]];
     int32_t left = n_steps;
@@ -445,7 +442,7 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
         }
         for (int s = 0; s < chunk; ++s) {
             StepParams p = make_params(e, list_dev, n_list, v.vec, s);
-            cudaError_t err = v.launch(p, grid, e->stream);
+            cudaError_t err = v.launch(p, e->stream);
             if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
             count_launches(1);
         }
@@ -548,7 +545,9 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     const lbm_config c = *cfg;
     if (c.nx < 8 || c.nx % 8 != 0) return fail(LBM_ERR_ARG, "nx must be a positive multiple of 8");
     if (c.ny < 2) return fail(LBM_ERR_ARG, "ny must be at least 2");
-    if (n_clones < 1) return fail(LBM_ERR_ARG, "need at least one clone");
+    if (n_clones < 1 || n_clones > 65535) return fail(LBM_ERR_ARG, "clone count must be in [1, 65535]");
+    if ((int64_t)9 * (((c.nx + 255) / 256) * 256) * c.ny >= ((int64_t)1 << 31))
+        return fail(LBM_ERR_ARG, "one clone must hold fewer than 2^31 population values");
     if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(LBM_ERR_ARG, "tau must exceed 1/2");
     if (!std::isfinite(c.gx) || !std::isfinite(c.gy)) return fail(LBM_ERR_ARG, "force must be finite");
     if (c.storage < 0 || c.storage > 2) return fail(LBM_ERR_ARG, "unknown storage");
@@ -962,14 +961,11 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
     for (size_t i = 0; i < vars.size(); ++i) {
         const StepVariant& v = vars[i];
         if (v.storage != e->cfg.storage) continue;
-        const int nseg = (e->cfg.nx + 32 * v.vec - 1) / (32 * v.vec);
-        const int64_t warps = (int64_t)e->n * e->cfg.ny * nseg;
-        const int grid = (int)((warps + v.warps - 1) / v.warps);
         StepParams p = make_params(e, e->all_dev, e->n, v.vec, 0);
         const int reps = 5;
-        for (int r = 0; r < 2; ++r) LBM_CUDA(v.launch(p, grid, e->stream));
+        for (int r = 0; r < 2; ++r) LBM_CUDA(v.launch(p, e->stream));
         LBM_CUDA(cudaEventRecord(a, e->stream));
-        for (int r = 0; r < reps; ++r) LBM_CUDA(v.launch(p, grid, e->stream));
+        for (int r = 0; r < reps; ++r) LBM_CUDA(v.launch(p, e->stream));
         count_launches(2 + reps);
         LBM_CUDA(cudaEventRecord(b, e->stream));
         LBM_CUDA(cudaEventSynchronize(b));

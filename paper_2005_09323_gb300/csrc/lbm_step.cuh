@@ -12,183 +12,242 @@
 //               (eq. (drag_definition) for the bounce-back surface).
 //
 // Memory layout: structure of arrays, plane q of clone c is a ny x pitch
-// array.  Thread = V consecutive sites of one row; warp = 32 V sites.  Every
-// plane is read with one aligned V-wide vector load per thread (16 bytes when
-// V * sizeof(T) = 16); the one-site shift of directions with c_x = +-1 is
-// done in registers with a warp shuffle, and only the two warp-edge elements
-// are fetched separately (they sit in sectors the neighbouring warp reads, so
-// they come from L2).  Each population value is read once and written once:
-// there is no reuse for shared memory or TMA staging to exploit, the kernel is
-// bound by HBM bandwidth at 2 * 9 * sizeof(T) bytes per site.
+// array.  Thread = V consecutive sites of one row; warp = 32 V sites; block =
+// WARPS rows of the same 32 V-site segment; grid = (segments, row blocks,
+// listed clones), so no index arithmetic needs a division.  Every plane is
+// read with one aligned V-wide vector load per thread (16 bytes for V *
+// sizeof(T) = 16), all nine issued before any is used; the one-site shift of
+// directions with c_x = +-1 is done in registers with a warp shuffle, and only
+// the two warp-edge elements are fetched separately (sectors the neighbouring
+// warp reads, so they come from L2).  Each population value is read once and
+// written once: there is no reuse for shared memory or TMA staging to
+// exploit, and the kernel is bound by HBM bandwidth at 2 * 9 * sizeof(T)
+// bytes per site.
+//
+// Interior warps (no wall row, away from the obstacle) take a path without
+// any boundary test; the few warps on the walls and around the obstacle take
+// the general path, which also produces the drag partial of the warp.
 #pragma once
 #include "internal.h"
 #include "lbm_device.cuh"
 
 namespace lbm {
 
-template <int S, int V, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
+// The collision carries the shifted value g = f - w_q for every storage
+// format.  For FP32 storage the shift is applied on load and undone on store:
+// the float weights do not sum to one exactly (4/9 + 4/9 + 1/9 rounds to
+// 1 + 7.5e-9), and carrying f itself would turn that into a systematic mass
+// drift of om * 7.5e-9 per node and step; with g the same float w_q cancels
+// between load and store.
+template <int S> struct Carry {
+    using T = typename Codec<S>::T;
+    __device__ static float in(T v, float w, float inv_scale) { return Codec<S>::dec(v, w, inv_scale); }
+    __device__ static T out(float g, float w, float scale) { return Codec<S>::enc(g, w, scale); }
+};
+
+template <int S, int V, bool GENERAL>
+__device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
+                                          typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
 {
-    using C = Codec<S>;
-    using T = typename C::T;
-    const int lane = threadIdx.x & 31;
-    const int64_t gwarp = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    const int64_t per_clone = (int64_t)p.ny * p.nseg;
-    const int li = (int)(gwarp / per_clone);
-    if (li >= p.n_list) return;  // warp-uniform
-    const int rem = (int)(gwarp - (int64_t)li * per_clone);
-    const int y = rem / p.nseg;
-    const int seg = rem - y * p.nseg;
-    const int c = p.clone_list[li];
-    const int cur = p.parity[c] ^ (p.step_in_batch & 1);
-    const T* __restrict__ src = static_cast<const T*>(cur ? p.buf1 : p.buf0) + (int64_t)c * p.clone_stride;
-    T* __restrict__ dst = static_cast<T*>(cur ? p.buf0 : p.buf1) + (int64_t)c * p.clone_stride;
+    using T = typename Codec<S>::T;
+    using K = Carry<S>;
     const int x0 = seg * 32 * V + lane * V;
     const bool active = x0 < p.nx;
-    const int64_t row_off = (int64_t)y * p.pitch;
+    const int row = y * p.pitch;
+    const int plane = (int)p.plane;  // a clone holds < 2^31 values (checked at creation)
+    const int ox0 = p.ox0, ox1 = p.ox1, oy0 = p.oy0, oy1 = p.oy1;
 
-    const bool obst = p.ox1 > p.ox0;
-    float g[9][V];
-
+    // ---- phase 1: issue every load
+    Vec<T, V> v[9];
+    T edge[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int ex = cx(q), ey = cy(q);
-        const float wq = wf(q);
-        const int ys = y - ey;
-        if (ys < 0 || ys >= p.ny) {
+        int srow = y - ey;
+        int plane_q = q;
+        if (GENERAL && (srow < 0 || srow >= p.ny)) {
             // the wall sends back the population that left this node
-            const Vec<T, V> v = ld_stream<T, V>(src + opp(q) * p.plane + row_off + x0);
+            srow = y;
+            plane_q = opp(q);
+        }
+        const T* rp = src + plane_q * plane + srow * p.pitch;
+        v[q] = ld_stream<T, V>(rp + x0);
+        if (ex == 1) {
+            const int xs = x0 == 0 ? p.nx - 1 : x0 - 1;
+            if (lane == 0 || x0 == 0) edge[q] = ld_one(rp + xs);
+        } else if (ex == -1) {
+            const int xs = x0 + V >= p.nx ? 0 : x0 + V;
+            if (lane == 31 || x0 + V >= p.nx) edge[q] = ld_one(rp + xs);
+        }
+    }
+
+    // ---- phase 2: assemble the pulled values of the V sites
+    float g[9][V];
 #pragma unroll
-            for (int j = 0; j < V; ++j) g[q][j] = C::dec(v.e[j], wq, p.inv_scale);
+    for (int q = 0; q < 9; ++q) {
+        const int ex = cx(q), ey = cy(q);
+        const bool wall = GENERAL && ((y - ey) < 0 || (y - ey) >= p.ny);
+        float d[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) d[j] = K::in(v[q].e[j], wf(q), p.inv_scale);
+        if (ex == 0 || wall) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) g[q][j] = d[j];
+        } else if (ex == 1) {
+            float e = __shfl_up_sync(0xffffffffu, d[V - 1], 1);
+            if (lane == 0 || x0 == 0) e = K::in(edge[q], wf(q), p.inv_scale);
+            g[q][0] = e;
+#pragma unroll
+            for (int j = 1; j < V; ++j) g[q][j] = d[j - 1];
         } else {
-            const T* row = src + q * p.plane + (int64_t)ys * p.pitch;
-            const Vec<T, V> v = ld_stream<T, V>(row + x0);
-            float d[V];
+            float e = __shfl_down_sync(0xffffffffu, d[0], 1);
+            if (lane == 31 || x0 + V >= p.nx) e = K::in(edge[q], wf(q), p.inv_scale);
 #pragma unroll
-            for (int j = 0; j < V; ++j) d[j] = C::dec(v.e[j], wq, p.inv_scale);
-            if (ex == 0) {
+            for (int j = 0; j < V - 1; ++j) g[q][j] = d[j + 1];
+            g[q][V - 1] = e;
+        }
+    }
+    if (GENERAL && ox1 > ox0) {
+        // links whose upstream node is solid bounce back at this node
 #pragma unroll
-                for (int j = 0; j < V; ++j) g[q][j] = d[j];
-            } else if (ex == 1) {
-                // site x pulls from x - 1
-                float edge = __shfl_up_sync(0xffffffffu, d[V - 1], 1);
-                if (lane == 0 || x0 == 0) {
-                    const int xs = x0 == 0 ? p.nx - 1 : x0 - 1;
-                    edge = C::dec(ld_one(row + xs), wq, p.inv_scale);
-                }
-                g[q][0] = edge;
+        for (int q = 1; q < 9; ++q) {
+            const int ex = cx(q), ys = y - cy(q);
+            if (ys < oy0 || ys >= oy1) continue;
+            bool any = false;
 #pragma unroll
-                for (int j = 1; j < V; ++j) g[q][j] = d[j - 1];
-            } else {
-                // site x pulls from x + 1
-                float edge = __shfl_down_sync(0xffffffffu, d[0], 1);
-                if (lane == 31 || x0 + V >= p.nx) {
-                    const int xs = x0 + V >= p.nx ? 0 : x0 + V;
-                    edge = C::dec(ld_one(row + xs), wq, p.inv_scale);
-                }
-#pragma unroll
-                for (int j = 0; j < V - 1; ++j) g[q][j] = d[j + 1];
-                g[q][V - 1] = edge;
+            for (int j = 0; j < V; ++j) {
+                const int xs = x0 + j - ex;
+                any |= (xs >= ox0 && xs < ox1);
             }
-            // links whose upstream node is solid bounce back at this node
-            if (obst && ys >= p.oy0 && ys < p.oy1) {
-                bool any = false;
+            if (any) {
+                const Vec<T, V> o = ld_stream<T, V>(src + opp(q) * plane + row + x0);
 #pragma unroll
                 for (int j = 0; j < V; ++j) {
                     const int xs = x0 + j - ex;
-                    any |= (xs >= p.ox0 && xs < p.ox1);
-                }
-                if (any) {
-                    const Vec<T, V> o = ld_stream<T, V>(src + opp(q) * p.plane + row_off + x0);
-#pragma unroll
-                    for (int j = 0; j < V; ++j) {
-                        const int xs = x0 + j - ex;
-                        if (xs >= p.ox0 && xs < p.ox1) g[q][j] = C::dec(o.e[j], wq, p.inv_scale);
-                    }
+                    if (xs >= ox0 && xs < ox1) g[q][j] = K::in(o.e[j], wf(q), p.inv_scale);
                 }
             }
         }
     }
 
-    // BGK collision with Guo forcing, in the shifted variables g = f - w
-    const float om = p.omega;
-    const float src_coef = 1.0f - 0.5f * om;
+    // ---- phase 3: BGK collision with Guo forcing.
+    // With drho = rho - 1 = sum g and the carried value g = f - w:
+    //   g*_q = (1 - om) g_q + w_q [a0 + 3k cF_q + cu (3 om rho + 9k cF_q + 4.5 om rho cu)]
+    //   a0 = om drho - 1.5 om rho u.u - 3k u.F,
+    // k = 1 - om/2, cu = c_q.u, cF_q = c_q.F: the equilibrium of App. A plus
+    // the Guo source, expanded.
+    const float om = p.omega, one_m_om = 1.0f - om, kap3 = 3.0f * (1.0f - 0.5f * om);
     const float gx = p.gx, gy = p.gy;
-    const bool row_has_solid = obst && y >= p.oy0 && y < p.oy1;
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-        float drho = 0.f, jx = 0.f, jy = 0.f;
+        float sum = 0.f, jx = 0.f, jy = 0.f;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            drho += g[q][j];
-            if (cx(q) != 0) jx += (float)cx(q) * g[q][j];
-            if (cy(q) != 0) jy += (float)cy(q) * g[q][j];
+            sum += g[q][j];
+            if (cx(q) > 0) jx += g[q][j];
+            if (cx(q) < 0) jx -= g[q][j];
+            if (cy(q) > 0) jy += g[q][j];
+            if (cy(q) < 0) jy -= g[q][j];
         }
+        const float drho = sum;
         const float rho = 1.0f + drho;
-        const float inv = __frcp_rn(rho);
+        const float inv = __fdividef(1.0f, rho);
         const float ux = (jx + 0.5f * gx) * inv;
         const float uy = (jy + 0.5f * gy) * inv;
-        const float usq15 = 1.5f * (ux * ux + uy * uy);
-        const float uF = ux * gx + uy * gy;
+        const float omr = om * rho;
+        const float P = 3.0f * omr, Qc = 4.5f * omr;
+        const float a0 = om * drho - 1.5f * omr * (ux * ux + uy * uy) - kap3 * (ux * gx + uy * gy);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const float wq = wf(q);
-            const float cu = (float)cx(q) * ux + (float)cy(q) * uy;
-            const float cF = (float)cx(q) * gx + (float)cy(q) * gy;
-            const float geq = wq * (drho + rho * (cu * (3.0f + 4.5f * cu) - usq15));
-            const float Sq = wq * (3.0f * (cF - uF) + 9.0f * cu * cF);
-            g[q][j] = g[q][j] + om * (geq - g[q][j]) + src_coef * Sq;
-        }
-        if (row_has_solid) {
-            const int x = x0 + j;
-            if (x >= p.ox0 && x < p.ox1) {
-#pragma unroll
-                for (int q = 0; q < 9; ++q) g[q][j] = 0.f;  // solid node: rest state
+            if (q == 0) {
+                g[0][j] = fmaf(wq, a0, one_m_om * g[0][j]);
+                continue;
             }
+            const float cu = (cx(q) == 0 ? 0.f : (float)cx(q) * ux) + (cy(q) == 0 ? 0.f : (float)cy(q) * uy);
+            const float cF = (cx(q) == 0 ? 0.f : (float)cx(q) * gx) + (cy(q) == 0 ? 0.f : (float)cy(q) * gy);
+            const float t = fmaf(Qc, cu, fmaf(3.0f * kap3, cF, P));
+            const float t2 = fmaf(cu, t, fmaf(kap3, cF, a0));
+            g[q][j] = fmaf(wq, t2, one_m_om * g[q][j]);
         }
     }
 
-    // momentum exchange with the obstacle, one partial per warp of the ring
-    if (obst && y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1) {
-        float acc = 0.f;
-        if (active) {
+    if (GENERAL && ox1 > ox0) {
+        if (y >= oy0 && y < oy1) {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const int x = x0 + j;
-                const bool solid_here = y >= p.oy0 && y < p.oy1 && x >= p.ox0 && x < p.ox1;
-                if (solid_here) continue;
+                if (x >= ox0 && x < ox1) {
 #pragma unroll
-                for (int q = 1; q < 9; ++q) {
-                    if (cx(q) == 0) continue;
-                    const int xn = x + cx(q), yn = y + cy(q);
-                    if (xn >= p.ox0 && xn < p.ox1 && yn >= p.oy0 && yn < p.oy1)
-                        acc += 2.0f * (float)cx(q) * (wf(q) + g[q][j]);
+                    for (int q = 0; q < 9; ++q) g[q][j] = 0.f;  // solid node: rest state f = w
                 }
             }
         }
+        // momentum exchange with the obstacle, one partial per warp of the ring
+        if (y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1) {
+            float acc = 0.f;
+            if (active) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) {
-            const int slot = (y - p.ry0) * (p.rs1 - p.rs0 + 1) + (seg - p.rs0);
-            p.partials[((int64_t)c * p.batch_cap + p.step_in_batch) * p.n_slots + slot] = acc;
+                for (int j = 0; j < V; ++j) {
+                    const int x = x0 + j;
+                    if (y >= oy0 && y < oy1 && x >= ox0 && x < ox1) continue;
+#pragma unroll
+                    for (int q = 1; q < 9; ++q) {
+                        if (cx(q) == 0) continue;
+                        const int xn = x + cx(q), yn = y + cy(q);
+                        if (xn >= ox0 && xn < ox1 && yn >= oy0 && yn < oy1) {
+                            acc += 2.0f * (float)cx(q) * (wf(q) + g[q][j]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (lane == 0) {
+                const int slot = (y - p.ry0) * (p.rs1 - p.rs0 + 1) + (seg - p.rs0);
+                p.partials[((int64_t)c * p.batch_cap + p.step_in_batch) * p.n_slots + slot] = acc;
+            }
         }
     }
 
+    // ---- phase 4: store
     if (active) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             Vec<T, V> o;
 #pragma unroll
-            for (int j = 0; j < V; ++j) o.e[j] = C::enc(g[q][j], wf(q), p.scale);
-            st_stream<T, V>(dst + q * p.plane + row_off + x0, o);
+            for (int j = 0; j < V; ++j) o.e[j] = K::out(g[q][j], wf(q), p.scale);
+            st_stream<T, V>(dst + q * plane + row + x0, o);
         }
     }
 }
 
 template <int S, int V, int WARPS>
-cudaError_t launch_step(const StepParams& p, int grid, cudaStream_t s)
+__global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
 {
-    step_kernel<S, V, WARPS><<<grid, WARPS * 32, 0, s>>>(p);
+    using T = typename Codec<S>::T;
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * WARPS + threadIdx.y;
+    if (y >= p.ny) return;  // warp-uniform
+    const int seg = blockIdx.x;
+    const int c = p.clone_list[blockIdx.z];
+    const int cur = p.parity[c] ^ (p.step_in_batch & 1);
+    const T* src = static_cast<const T*>(cur ? p.buf1 : p.buf0) + (int64_t)c * p.clone_stride;
+    T* dst = static_cast<T*>(cur ? p.buf0 : p.buf1) + (int64_t)c * p.clone_stride;
+    const bool wall_row = y == 0 || y == p.ny - 1;
+    const bool ring = p.ox1 > p.ox0 && y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1;
+    if (wall_row || ring)
+        step_warp<S, V, true>(p, src, dst, c, y, seg, lane);
+    else
+        step_warp<S, V, false>(p, src, dst, c, y, seg, lane);
+}
+
+template <int S, int V, int WARPS>
+cudaError_t launch_step(const StepParams& p, cudaStream_t s)
+{
+    const dim3 block(32, WARPS);
+    const dim3 grid(p.nseg, (p.ny + WARPS - 1) / WARPS, p.n_list);
+    step_kernel<S, V, WARPS><<<grid, block, 0, s>>>(p);
     return cudaGetLastError();
 }
 
