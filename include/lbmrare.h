@@ -172,6 +172,33 @@ int32_t lbm_step_variant_count(void);
 int lbm_ensemble_set_timing(lbm_ensemble* e, int32_t enable);
 int lbm_ensemble_kernel_time(lbm_ensemble* e, double* ms, int64_t* launches, int32_t reset);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* One fused step (as lbm_ensemble_step, for one time step) over population
+ * buffers the caller owns, for callers that cannot allocate device memory: a
+ * program whose device memory belongs to another allocator (a framework's
+ * pool, an arena fixed at start-up) or a loop that cannot afford the implicit
+ * synchronisation of cudaMalloc.  The paper has no counterpart; it is an
+ * interface of this library only.
+ *   f_in_dev / f_out_dev: device arrays [n_clones][9][ny][pitch] in cfg->storage
+ *     (FP32 f, or 16-bit (f - w_q) * 2^shift_exp), pitch = nx rounded up to a
+ *     multiple of 256 elements, 16-byte aligned, distinct; padding columns are
+ *     read but never written.  f_out_dev receives the state one step later.
+ *   drag_dev: device double[n_clones], the momentum-exchange drag of the new
+ *     state (eq. (drag_definition)).
+ *   cfg: the flow (max_steps, ckpt_stride and n_snapshots are ignored).
+ * The call allocates nothing: its scratch (the per-warp drag partials and two
+ * index tables) is a fixed 1 MiB device array inside the library, which every
+ * device that loads the library holds until the process exits.  Sizes whose
+ * scratch exceeds 1 MiB (n_clones x drag slots x 4 bytes plus the tables) are
+ * rejected with LBM_ERR_ARG.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture.  Every call uses the same array:
+ * calls that may overlap on the GPU (different streams without ordering)
+ * race on it.  Enqueued on stream; returns without waiting. */
+int lbm_step_noalloc(const lbm_config* cfg, int32_t n_clones, const void* f_in_dev, void* f_out_dev,
+                     double* drag_dev, void* stream);
+
 /* ---------------------------------------------------------------- selection */
 
 /* GKTL weights, eq. (Weight): with m = max s, W_dev[n] = N e^{s_n - m} / S and

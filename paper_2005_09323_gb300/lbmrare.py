@@ -26,7 +26,7 @@ EXPORTS = [
     "lbm_ensemble_branch", "lbm_ensemble_moments", "lbm_ensemble_get_populations",
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
-    "gktl_weights", "gktl_select", "ams_select",
+    "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
 ]
 
 
@@ -93,6 +93,7 @@ def lib():
             "gktl_weights": ([i32, p, p, p, p], C.c_int),
             "gktl_select": ([i32, p, u64, u64, p, p, p], C.c_int),
             "ams_select": ([i32, p, u64, u64, p, p, p, p, p], C.c_int),
+            "lbm_step_noalloc": ([p, i32, p, p, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -249,6 +250,23 @@ def lbm_ensemble_kernel_time(e, reset: bool = False):
     n = C.c_int64()
     _check(lib().lbm_ensemble_kernel_time(e, C.byref(ms), C.byref(n), int(bool(reset))))
     return ms.value, n.value
+
+
+# ---------------------------------------------------------------- no allocation
+def lbm_step_noalloc(cfg: lbm_config, n_clones: int, f_in_dev, f_out_dev, drag_dev, stream=None):
+    """One fused step over caller-owned buffers [n_clones][9][ny][pitch] (torch
+    CUDA tensors of the storage dtype); drag_dev: float64 [n_clones]."""
+    import torch
+    for t in (f_in_dev, f_out_dev):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("population buffers must be contiguous torch CUDA tensors")
+    _check(lib().lbm_step_noalloc(C.byref(cfg), n_clones, C.c_void_p(f_in_dev.data_ptr()),
+                                  C.c_void_p(f_out_dev.data_ptr()), _dev(drag_dev, torch.float64), _stream(stream)))
+
+
+def noalloc_pitch(nx: int) -> int:
+    """row pitch (elements) of the buffers lbm_step_noalloc takes"""
+    return ((nx + 255) // 256) * 256
 
 
 # ---------------------------------------------------------------- selection
