@@ -39,7 +39,7 @@ BYTES_PER_SITE = 72      # FP32: 9 loads + 9 stores of 4 bytes
 METRIC = "Ensemble D2Q9 GLUPS & HBM-roofline fraction; time-to-return-time vs plain"
 # DRAM traffic of one fused-step launch measured by ncu on this workload, and
 # the kernel source it was measured on (reported only while the source matches)
-NCU_TRAFFIC = {"sha": None, "bytes_per_site": None}
+NCU_TRAFFIC = {"sha": "12cee4d507c8406e", "bytes_per_site": 68.5474}  # mean of 3 launches, 64 clones
 
 
 def kernel_sha() -> str:
