@@ -29,9 +29,29 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-NX, NY, N_CLONES, PERIOD = 1024, 256, 64, 500
-OBST = (256 - 16, 128 - 16, 32, 32)
+PERIOD = 500
 TAU, GX = 0.505, 1e-6
+# the synthetic workloads: channel nx x ny, clones, obstacle side at x = nx/4,
+# and whether a step includes GKTL cloning (the default is the GKTL workload)
+WORKLOADS = {
+    "gktl": dict(nx=1024, ny=256, clones=64, side=32, cloning=True,
+                 name="GKTL batched ensemble: N={n} clones, D2Q9 LBGK {st}, 1024x256, 32x32 obstacle at x=256, "
+                      "tau=0.505, g_x=1e-06, resample every 500 steps"),
+    "precision": dict(nx=2048, ny=512, clones=16, side=64, cloning=False,
+                      name="Precision sweep: N={n} clones, 2048x512, 64x64 obstacle at x=512, tau=0.505, g_x=1e-06, "
+                           "populations stored as {st}, 500 steps per step"),
+    "ams": dict(nx=512, ny=128, clones=256, side=16, cloning=False,
+                name="AMS initial ensemble: N={n} trajectories, 512x128, 16x16 obstacle at x=128, tau=0.505, "
+                     "g_x=1e-06, {st}, 500 steps per step"),
+}
+
+
+def workload(args):
+    w = dict(WORKLOADS[args.workload])
+    w["clones"] = args.clones or w["clones"]
+    nx, ny, side = w["nx"], w["ny"], w["side"]
+    w["obst"] = (nx // 4 - side // 2, ny // 2 - side // 2, side, side)
+    return w
 EPS, N_SNAP = 0.002, 10
 K_SIGMA = 1.0
 SIGMA_DRAG = 1e-3        # drag scale used to set k (k = K_SIGMA / (SIGMA_DRAG * PERIOD))
@@ -113,11 +133,10 @@ class Clocks:
 
 # ---------------------------------------------------------------- CPU oracle
 def _oracle_worker(args):
-    steps, seed, barrier = args
+    steps, seed, barrier, nx, ny, obst = args
     sys.path.insert(0, ROOT)
     import oracle
-    from tests import seeded_inputs as si  # noqa: F401  (same input recipe as the tests)
-    c = oracle.cfg(NX, NY, obstacle=OBST, tau=TAU, gx=GX)
+    c = oracle.cfg(nx, ny, obstacle=obst, tau=TAU, gx=GX)
     f = oracle.init(c, seed, 0, 0.01)
     if barrier is not None:
         barrier.wait()
@@ -126,21 +145,22 @@ def _oracle_worker(args):
     return time.perf_counter() - t0
 
 
-def oracle_rate(steps_per_proc: int, procs: int):
+def oracle_rate(steps_per_proc: int, procs: int, w):
     """Aggregate oracle GLUPS over `procs` single-threaded processes (spawned),
-    each advancing one 1024 x 256 clone by steps_per_proc steps."""
+    each advancing one clone of the workload's channel by steps_per_proc steps."""
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
+    geo = (w["nx"], w["ny"], w["obst"])
     if procs == 1:
-        dt = _oracle_worker((steps_per_proc, 0, None))
+        dt = _oracle_worker((steps_per_proc, 0, None) + geo)
         times = [dt]
     else:
         with ctx.Manager() as m:
             barrier = m.Barrier(procs)
             with ctx.Pool(procs) as pool:
-                times = pool.map(_oracle_worker, [(steps_per_proc, s, barrier) for s in range(procs)])
-    updates = NX * NY * steps_per_proc * procs
+                times = pool.map(_oracle_worker, [(steps_per_proc, s, barrier) + geo for s in range(procs)])
+    updates = w["nx"] * w["ny"] * steps_per_proc * procs
     wall = max(times)
     return updates / wall / 1e9, wall, sum(times)
 
@@ -157,17 +177,18 @@ def run_reference(args):
     if rank != 0:
         return
     cores = cpu_cores()
-    steps_per_proc = 20
+    w = workload(args)
+    steps_per_proc = max(1, int(20 * 1024 * 256 / (w["nx"] * w["ny"])))
     vals, walls = [], []
     for _ in range(args.warmup):
-        oracle_rate(2, 1)
+        oracle_rate(1, 1, w)
     for _ in range(args.steps):
-        v, wall, _ = oracle_rate(steps_per_proc, cores)
+        v, wall, _ = oracle_rate(steps_per_proc, cores, w)
         vals.append(v)
         walls.append(wall)
     value = statistics.median(vals)
-    sample = (f"{cores} processes x 1 clone of {NX}x{NY} x {steps_per_proc} steps per step "
-              f"(of {N_CLONES} clones x {PERIOD} steps per GKTL period)")
+    sample = (f"{cores} processes x 1 clone of {w['nx']}x{w['ny']} x {steps_per_proc} steps per step "
+              f"(of {w['clones']} clones x {PERIOD} steps per workload step)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls),
@@ -180,13 +201,16 @@ def run_reference(args):
 
 
 def workload_config(args):
-    n = getattr(args, "clones", N_CLONES)
-    return {"workload": f"GKTL batched ensemble: N={n} clones, D2Q9 LBGK FP32, {NX}x{NY}, "
-                        f"32x32 obstacle at x=256, tau={TAU}, g_x={GX}, resample every {PERIOD} steps",
-            "clones": n, "grid": [NX, NY], "steps_per_period": PERIOD, "storage": "fp32",
-            "k_sigma": K_SIGMA, "eps": EPS, "n_snapshots": N_SNAP,
-            "l2": "working set 1.21 GB of populations per ensemble (>> 129 MB L2); no flush needed",
-            "parallelism": f"replicas x{args.gpus}"}
+    w = workload(args)
+    st = {"fp32": "FP32", "fp16": "shifted FP16", "bf16": "shifted BF16"}[args.storage]
+    state_gb = 2 * w["clones"] * 9 * w["nx"] * w["ny"] * (4 if args.storage == "fp32" else 2) / 1e9
+    cfg = {"workload": w["name"].format(n=w["clones"], st=st), "clones": w["clones"], "grid": [w["nx"], w["ny"]],
+           "steps_per_step": PERIOD, "storage": args.storage,
+           "l2": f"working set {state_gb:.2f} GB of populations (two buffers, >> 129 MB L2); no flush needed",
+           "parallelism": f"replicas x{args.gpus}"}
+    if w["cloning"]:
+        cfg.update({"k_sigma": K_SIGMA, "eps": EPS, "n_snapshots": N_SNAP})
+    return cfg
 
 
 # ---------------------------------------------------------------- GPU
@@ -212,19 +236,22 @@ def run_ours(args):
     L.lib()
 
     # CPU baseline first (spawned processes, before the GPU is touched)
+    w = workload(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = cpu_cores()
-        v, wall, cpu_s = oracle_rate(20, cores)
+        spp = max(1, int(20 * 1024 * 256 / (w["nx"] * w["ny"])))
+        v, wall, cpu_s = oracle_rate(spp, cores, w)
         cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{cores} single-threaded oracle processes, each one clone of {NX}x{NY} for 20 steps "
-                         f"({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)"}
+               "sample": f"{cores} single-threaded oracle processes, each one clone of {w['nx']}x{w['ny']} for "
+                         f"{spp} steps ({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)"}
 
     stream = torch.cuda.current_stream()
     total_periods = args.warmup + args.steps + 2 * (args.warmup + args.steps) + 2
-    cfg = L.config(NX, NY, obstacle=OBST, tau=TAU, gx=GX, max_steps=PERIOD * total_periods,
-                   n_snapshots=N_SNAP, init_amp=0.01)
-    n_clones = args.clones
+    nx, ny = w["nx"], w["ny"]
+    cfg = L.config(nx, ny, obstacle=w["obst"], tau=TAU, gx=GX, max_steps=PERIOD * total_periods,
+                   n_snapshots=N_SNAP, init_amp=0.01, storage=args.storage)
+    n_clones = w["clones"]
     e = L.lbm_ensemble_create(cfg, n_clones, 1000 + rank, stream)
     if args.variant == "auto":
         variant = L.lbm_ensemble_autotune(e)
@@ -244,9 +271,10 @@ def run_ours(args):
         t0 = state["t"]
         L.lbm_ensemble_step(e, PERIOD)
         L.lbm_ensemble_window_sum(e, t0, t0 + PERIOD, k, s)
-        L.gktl_weights(s, W, logR, stream)
-        L.gktl_select(W, 7, state["it"], parent, status, stream)
-        L.lbm_ensemble_clone(e, parent, EPS, 7, state["it"])
+        if w["cloning"]:
+            L.gktl_weights(s, W, logR, stream)
+            L.gktl_select(W, 7, state["it"], parent, status, stream)
+            L.lbm_ensemble_clone(e, parent, EPS, 7, state["it"])
         state["t"] += PERIOD
         state["it"] += 1
 
@@ -296,10 +324,11 @@ def run_ours(args):
         L.lbm_ensemble_drag(e, t0, t0 + PERIOD, drag_host)       # D2H, waits
         pinned_s.numpy()[:] = k * drag_host.sum(axis=1)
         s.copy_(pinned_s, non_blocking=True)                      # H2D
-        L.gktl_weights(s, W, logR, stream)
-        L.gktl_select(W, 7, state["it"], parent, status, stream)
-        pinned_p.copy_(parent, non_blocking=True)                 # D2H
-        L.lbm_ensemble_clone(e, parent, EPS, 7, state["it"])
+        if w["cloning"]:
+            L.gktl_weights(s, W, logR, stream)
+            L.gktl_select(W, 7, state["it"], parent, status, stream)
+            pinned_p.copy_(parent, non_blocking=True)             # D2H
+            L.lbm_ensemble_clone(e, parent, EPS, 7, state["it"])
         torch.cuda.current_stream().synchronize()
         state["t"] += PERIOD
         state["it"] += 1
@@ -318,15 +347,17 @@ def run_ours(args):
         tt = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms, e2e_s = tt.tolist()
-    sites = n_clones * NX * NY
+    sites = n_clones * nx * ny
     updates = sites * PERIOD * args.steps * world
     value = updates / (ms / 1e3) / 1e9
     e2e_value = sites * PERIOD * e2e_steps * world / e2e_s / 1e9
     hbm, peak_kind = peaks()
     avg_launch_ms = st_ms / max(st_launches, 1)
-    achieved = BYTES_PER_SITE * sites / (avg_launch_ms / 1e3) / 1e9
+    bytes_per_site = BYTES_PER_SITE if args.storage == "fp32" else BYTES_PER_SITE // 2
+    achieved = bytes_per_site * sites / (avg_launch_ms / 1e3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["sha"] == kernel_sha() and NCU_TRAFFIC["bytes_per_site"]:
+    if (NCU_TRAFFIC["sha"] == kernel_sha() and NCU_TRAFFIC["bytes_per_site"] and args.workload == "gktl"
+            and args.storage == "fp32"):
         traffic = NCU_TRAFFIC["bytes_per_site"] * sites
     clocks = clk.summary()
     if rank == 0:
@@ -336,8 +367,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": f"step_kernel<fp32, vec={vinfo[1]}, warps={vinfo[2]}>",
-                         "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_site": BYTES_PER_SITE,
+                         "kernel": f"step_kernel<{args.storage}, vec={vinfo[1]}, warps={vinfo[2]}>",
+                         "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_site": bytes_per_site,
                          "avg_launch_us": avg_launch_ms * 1e3},
             "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 8 * n_clones,
                     "d2h_bytes_per_step": 8 * n_clones * PERIOD + 4 * n_clones},
@@ -360,8 +391,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--variant", default="auto",
                     help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
-    ap.add_argument("--clones", type=int, default=N_CLONES,
-                    help="ensemble size (default: the workload's 64; smaller only for profiling captures)")
+    ap.add_argument("--clones", type=int, default=0,
+                    help="ensemble size (default: the workload's; smaller only for profiling captures)")
+    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -114,10 +114,11 @@ int lbm_ensemble_drag(lbm_ensemble* e, int32_t t0, int32_t t1, double* dst, int3
 int lbm_ensemble_window_sum(lbm_ensemble* e, int32_t t0, int32_t t1, double k, double* out_dev);
 
 /* Time-averaged drag of eq. (def_time_averaged_drag) with a window of T steps,
- * F(t) = (1/T) sum_{s=t-T+1}^{t} D(s) for T <= t <= t_end, FP64, stored in the
- * ensemble; out_dev[n] (may be NULL) receives max_t F_n(t) (-inf if t_end < T):
- * the AMS score maximum Q_n (App. B.1) and the GKTL event amplitude (App. C.2). */
-int lbm_ensemble_scores(lbm_ensemble* e, int32_t window, int32_t t_end, double* out_dev);
+ * F(t) = (1/T) sum_{s=t-T+1}^{t} D(s) for t_begin + T <= t <= t_end (the
+ * trajectory starts at t_begin), FP64, stored in the ensemble; out_dev[n] (may
+ * be NULL) receives max_t F_n(t) (-inf if t_end < t_begin + T): the AMS score
+ * maximum Q_n (App. B.1) and the GKTL event amplitude (App. C.2). */
+int lbm_ensemble_scores(lbm_ensemble* e, int32_t window, int32_t t_begin, int32_t t_end, double* out_dev);
 
 /* First t with F_clone(t) > level in the last lbm_ensemble_scores result (the
  * AMS branching time of App. B.1); *t = -1 if none.  Host output; waits. */
@@ -171,6 +172,64 @@ int32_t lbm_step_variant_count(void);
  * returns the summed milliseconds and launch count since the last reset. */
 int lbm_ensemble_set_timing(lbm_ensemble* e, int32_t enable);
 int lbm_ensemble_kernel_time(lbm_ensemble* e, double* ms, int64_t* launches, int32_t reset);
+
+/* ---------------------------------------------------------------- drivers */
+
+/* GKTL run (App. C.1), from the ensemble's current time t0 (all clones equal):
+ * n_periods times, advance period steps, form s_n = k sum_{period} D_n(t)
+ * (gktl exponent of eq. (Weight)), the weights and log R_i, resample
+ * (gktl_select with iter = i) and clone with the App. D perturbation eps
+ * (lbm_ensemble_clone, iter = i).  Device outputs: logR_dev[n_periods] (their
+ * sum is ln Z), parent_dev[n_periods][N] (the genealogy), and, when non-NULL,
+ * integral_dev[N] = sum_{t0 < t <= t_end} D_n(t) of each final trajectory
+ * (histories follow the clones) and maxima_dev[N] = max_t F_T(t) with T =
+ * window steps (lbm_ensemble_scores from t0).  Waits at the end; a rejected
+ * resampling or a non-finite drag returns LBM_ERR_NONFINITE / LBM_ERR_ARG. */
+typedef struct {
+    int32_t period;       /* cloning period tau, in steps */
+    int32_t n_periods;    /* T_a / tau */
+    double k;             /* bias per step of drag (exponent k * sum D) */
+    double eps;           /* App. D perturbation amplitude; 0 copies exactly */
+    uint64_t seed;        /* selection and perturbation streams */
+    int32_t window;       /* T of the time-averaged drag for maxima_dev (0: none) */
+} lbm_gktl_params;
+int lbm_gktl_run(lbm_ensemble* e, const lbm_gktl_params* p, double* logR_dev, int32_t* parent_dev,
+                 double* integral_dev, double* maxima_dev);
+
+/* GKTL return-time estimator (App. C.2, sign read as the inversion of eq.
+ * (Biased_Path_Approximation) requires): for each level a_j,
+ *   p_dev[j] = (1/N) sum_n exp(ln Z - k I_n) 1{A_n >= a_j},  ln Z = sum_i logR_dev[i],
+ *   r_dev[j] = -(t_a - t_window) / ln(1 - p_dev[j])   (r_dev may be NULL),
+ * I_n = integral_dev[n], A_n = maxima_dev[n].  FP64, fixed summation order. */
+int gktl_probability(int32_t n, double k, const double* logR_dev, int32_t n_periods, const double* integral_dev,
+                     const double* maxima_dev, int32_t n_levels, const double* levels_dev, double t_a,
+                     double t_window, double* p_dev, double* r_dev, void* stream);
+
+/* AMS run (App. B.1) on trajectories of t_a steps from the ensemble's current
+ * time t0 (all clones equal, t0 a multiple of ckpt_stride): advance every
+ * clone t_a steps, score = time-averaged drag over window steps; then for
+ * j = 1..max_iter: ams_select (iter = j), stop if the level z_j >= level or
+ * every score ties, else branch each killed trajectory from its survivor at
+ * the first time the survivor's score exceeds z_j (perturbation eps, iter = j)
+ * and re-simulate it to t0 + t_a.  Outputs: *iterations (kills done),
+ * *log_weight = sum_j ln(1 - |K_j|/N), Q_dev[N] the final score maxima, and
+ * on the host levels[j-1] = z_j and n_killed[j-1] = |K_j| (either may be NULL;
+ * max_iter entries; ties at the minimum are killed together).  Waits. */
+typedef struct {
+    int32_t t_a;          /* trajectory duration, steps */
+    int32_t window;       /* score window T, steps */
+    int32_t max_iter;     /* J */
+    double level;         /* stop once the killed level reaches it (+inf: run J) */
+    double eps;           /* App. D perturbation amplitude at branching */
+    uint64_t seed;
+} lbm_ams_params;
+int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* p, int32_t* iterations, double* log_weight, double* Q_dev,
+                double* levels, int32_t* n_killed);
+
+/* AMS estimator (generalised AMS, Brehier-Lelievre-Rousset 2016; the paper
+ * states none): p_dev[j] = exp(log_weight) * (1/N) #{n : Q_n >= a_j}. */
+int ams_probability(int32_t n, double log_weight, const double* Q_dev, int32_t n_levels, const double* levels_dev,
+                    double* p_dev, void* stream);
 
 /* ---------------------------------------------------------------- no allocation */
 

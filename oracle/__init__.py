@@ -242,17 +242,18 @@ def window_sum(drag: np.ndarray, t0: int, t1: int, k: float) -> np.ndarray:
     return k * np.sum(np.asarray(drag, dtype=np.float64)[:, t0:t1], axis=1)
 
 
-def trailing_mean_max(drag: np.ndarray, window: int, t_end: int | None = None) -> np.ndarray:
-    """max over t in [window, t_end] of (1/window) sum_{s=t-window+1}^{t} drag(s):
+def trailing_mean_max(drag: np.ndarray, window: int, t_end: int | None = None, t_begin: int = 0) -> np.ndarray:
+    """max over t in [t_begin + window, t_end] of (1/window) sum_{s=t-window+1}^{t} drag(s):
     the time-averaged drag F_T of eq. (def_time_averaged_drag) with T = window
-    steps, maximised along each trajectory (AMS score maximum Q_n; GKTL event
-    amplitude).  -inf when t_end < window."""
+    steps, maximised along each trajectory that starts at t_begin (AMS score
+    maximum Q_n; GKTL event amplitude).  -inf when t_end < t_begin + window.
+    drag[n, t-1] is the drag after step t."""
     d = np.asarray(drag, dtype=np.float64)
     if t_end is None:
         t_end = d.shape[1]
     out = np.full(d.shape[0], -np.inf)
     for n in range(d.shape[0]):
-        for t in range(window, t_end + 1):
+        for t in range(t_begin + window, t_end + 1):
             m = np.sum(d[n, t - window:t]) / window
             if m > out[n]:
                 out[n] = m

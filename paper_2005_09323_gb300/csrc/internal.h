@@ -90,7 +90,7 @@ struct lbm_ensemble {
     int32_t red_blocks;
     double* mass_dev;         // [N]
     double* scores;           // [N][max_steps] trailing means
-    int32_t score_window, score_t_end;  // arguments of the last lbm_ensemble_scores
+    int32_t score_window, score_t_begin, score_t_end;  // arguments of the last lbm_ensemble_scores
     // selected step variant (index into step_variants())
     int variant;
     // optional timing of the fused step launches

@@ -157,14 +157,14 @@ __global__ void window_sum_kernel(const double* drag, int32_t max_steps, int32_t
 
 // F(t) = (1/W) sum_{s=t-W+1}^{t} D(s); thread i owns a contiguous range of t,
 // opens it with a direct sum and slides the window across it.
-__global__ void scores_kernel(const double* drag, int32_t max_steps, int32_t window, int32_t t_end,
+__global__ void scores_kernel(const double* drag, int32_t max_steps, int32_t window, int32_t t_begin, int32_t t_end,
                               double* scores, double* out_max)
 {
     __shared__ double sh[kRedThreads];
     const int c = blockIdx.x;
     const double* d = drag + (int64_t)c * max_steps;  // d[t-1] = D(t)
     double* F = scores + (int64_t)c * max_steps;      // F[t-1] = F(t)
-    const int first = window, count = t_end - window + 1;
+    const int first = t_begin + window, count = t_end - first + 1;
     double best = -INFINITY;
     if (count > 0) {
         const int chunk = (count + kRedThreads - 1) / kRedThreads;
@@ -181,7 +181,7 @@ __global__ void scores_kernel(const double* drag, int32_t max_steps, int32_t win
             }
         }
     }
-    for (int t = 1 + (int)threadIdx.x; t < min(first, t_end + 1); t += kRedThreads) F[t - 1] = -INFINITY;
+    for (int t = t_begin + 1 + (int)threadIdx.x; t < min(first, t_end + 1); t += kRedThreads) F[t - 1] = -INFINITY;
     const double mx = block_max<kRedThreads>(best, sh);
     if (threadIdx.x == 0 && out_max) out_max[c] = mx;
 }
@@ -739,15 +739,17 @@ int lbm_ensemble_window_sum(lbm_ensemble* e, int32_t t0, int32_t t1, double k, d
     return LBM_OK;
 }
 
-int lbm_ensemble_scores(lbm_ensemble* e, int32_t window, int32_t t_end, double* out_dev)
+int lbm_ensemble_scores(lbm_ensemble* e, int32_t window, int32_t t_begin, int32_t t_end, double* out_dev)
 {
     if (!e) return fail(LBM_ERR_ARG, "null ensemble");
     const int32_t tmax = *std::max_element(e->t_host.begin(), e->t_host.end());
-    if (window < 1 || t_end < 0 || t_end > tmax) return fail(LBM_ERR_ARG, "bad window or end time");
-    scores_kernel<<<e->n, kRedThreads, 0, e->stream>>>(e->drag, e->cfg.max_steps, window, t_end, e->scores, out_dev);
+    if (window < 1 || t_begin < 0 || t_end < t_begin || t_end > tmax) return fail(LBM_ERR_ARG, "bad window or time range");
+    scores_kernel<<<e->n, kRedThreads, 0, e->stream>>>(e->drag, e->cfg.max_steps, window, t_begin, t_end, e->scores,
+                                                       out_dev);
     count_launches(1);
     LBM_CUDA(cudaGetLastError());
     e->score_window = window;
+    e->score_t_begin = t_begin;
     e->score_t_end = t_end;
     return LBM_OK;
 }
@@ -758,7 +760,8 @@ int lbm_ensemble_first_crossing(lbm_ensemble* e, int32_t clone, double level, in
     if (clone < 0 || clone >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
     if (e->score_window < 1) return fail(LBM_ERR_STATE, "call lbm_ensemble_scores first");
     first_crossing_kernel<<<1, kRedThreads, 0, e->stream>>>(e->scores + (int64_t)clone * e->cfg.max_steps,
-                                                           e->score_window, e->score_t_end, level, e->flag_dev + 1);
+                                                           e->score_t_begin + e->score_window, e->score_t_end, level,
+                                                           e->flag_dev + 1);
     count_launches(1);
     LBM_CUDA(cudaGetLastError());
     LBM_CUDA(cudaMemcpyAsync(t, e->flag_dev + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));

@@ -27,6 +27,7 @@ EXPORTS = [
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
     "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
+    "lbm_gktl_run", "gktl_probability", "lbm_ams_run", "ams_probability",
 ]
 
 
@@ -41,6 +42,16 @@ class lbm_config(C.Structure):
                 ("obs_w", C.c_int32), ("obs_h", C.c_int32), ("tau", C.c_double), ("gx", C.c_double),
                 ("gy", C.c_double), ("storage", C.c_int32), ("shift_exp", C.c_int32), ("max_steps", C.c_int32),
                 ("ckpt_stride", C.c_int32), ("n_snapshots", C.c_int32), ("init_amp", C.c_double)]
+
+
+class lbm_gktl_params(C.Structure):
+    _fields_ = [("period", C.c_int32), ("n_periods", C.c_int32), ("k", C.c_double), ("eps", C.c_double),
+                ("seed", C.c_uint64), ("window", C.c_int32)]
+
+
+class lbm_ams_params(C.Structure):
+    _fields_ = [("t_a", C.c_int32), ("window", C.c_int32), ("max_iter", C.c_int32), ("level", C.c_double),
+                ("eps", C.c_double), ("seed", C.c_uint64)]
 
 
 def config(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, storage="fp32", shift_exp=0,
@@ -76,7 +87,7 @@ def lib():
             "lbm_ensemble_time": ([p, p], C.c_int),
             "lbm_ensemble_drag": ([p, i32, i32, p, i32], C.c_int),
             "lbm_ensemble_window_sum": ([p, i32, i32, d, p], C.c_int),
-            "lbm_ensemble_scores": ([p, i32, i32, p], C.c_int),
+            "lbm_ensemble_scores": ([p, i32, i32, i32, p], C.c_int),
             "lbm_ensemble_first_crossing": ([p, i32, d, p], C.c_int),
             "lbm_ensemble_set_snapshots": ([p, i32, p], C.c_int),
             "lbm_ensemble_clone": ([p, p, d, u64, u64], C.c_int),
@@ -94,6 +105,10 @@ def lib():
             "gktl_select": ([i32, p, u64, u64, p, p, p], C.c_int),
             "ams_select": ([i32, p, u64, u64, p, p, p, p, p], C.c_int),
             "lbm_step_noalloc": ([p, i32, p, p, p, p], C.c_int),
+            "lbm_gktl_run": ([p, p, p, p, p, p], C.c_int),
+            "gktl_probability": ([i32, d, p, i32, p, p, i32, p, d, d, p, p, p], C.c_int),
+            "lbm_ams_run": ([p, p, p, p, p, p, p], C.c_int),
+            "ams_probability": ([i32, d, p, i32, p, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -179,9 +194,9 @@ def lbm_ensemble_window_sum(e, t0: int, t1: int, k: float, out_dev):
     _check(lib().lbm_ensemble_window_sum(e, t0, t1, k, _dev(out_dev, torch.float64)))
 
 
-def lbm_ensemble_scores(e, window: int, t_end: int, out_dev=None):
+def lbm_ensemble_scores(e, window: int, t_begin: int, t_end: int, out_dev=None):
     import torch
-    _check(lib().lbm_ensemble_scores(e, window, t_end, _dev(out_dev, torch.float64)))
+    _check(lib().lbm_ensemble_scores(e, window, t_begin, t_end, _dev(out_dev, torch.float64)))
 
 
 def lbm_ensemble_first_crossing(e, clone: int, level: float) -> int:
@@ -250,6 +265,45 @@ def lbm_ensemble_kernel_time(e, reset: bool = False):
     n = C.c_int64()
     _check(lib().lbm_ensemble_kernel_time(e, C.byref(ms), C.byref(n), int(bool(reset))))
     return ms.value, n.value
+
+
+# ---------------------------------------------------------------- drivers
+def lbm_gktl_run(e, period: int, n_periods: int, k: float, eps: float, seed: int, window: int,
+                 logR_dev, parent_dev, integral_dev=None, maxima_dev=None):
+    import torch
+    prm = lbm_gktl_params(period, n_periods, k, eps, seed, window)
+    _check(lib().lbm_gktl_run(e, C.byref(prm), _dev(logR_dev, torch.float64), _dev(parent_dev, torch.int32),
+                              _dev(integral_dev, torch.float64), _dev(maxima_dev, torch.float64)))
+
+
+def gktl_probability(k: float, logR_dev, integral_dev, maxima_dev, levels_dev, t_a: float, t_window: float,
+                     p_dev, r_dev=None, stream=None):
+    import torch
+    _check(lib().gktl_probability(integral_dev.numel(), k, _dev(logR_dev, torch.float64), logR_dev.numel(),
+                                  _dev(integral_dev, torch.float64), _dev(maxima_dev, torch.float64),
+                                  levels_dev.numel(), _dev(levels_dev, torch.float64), t_a, t_window,
+                                  _dev(p_dev, torch.float64), _dev(r_dev, torch.float64), _stream(stream)))
+
+
+def lbm_ams_run(e, t_a: int, window: int, max_iter: int, level: float, eps: float, seed: int, Q_dev,
+                with_kills: bool = False):
+    """returns (iterations, log_weight, levels z_1..z_iterations[, kills per iteration])"""
+    import torch
+    prm = lbm_ams_params(t_a, window, max_iter, level, eps, seed)
+    it = C.c_int32()
+    lw = C.c_double()
+    levels = np.zeros(max(max_iter, 1))
+    kills = np.zeros(max(max_iter, 1), dtype=np.int32)
+    _check(lib().lbm_ams_run(e, C.byref(prm), C.byref(it), C.byref(lw), _dev(Q_dev, torch.float64), _host(levels),
+                             _host(kills)))
+    out = (it.value, lw.value, levels[:it.value].copy())
+    return out + (kills[:it.value].copy(),) if with_kills else out
+
+
+def ams_probability(log_weight: float, Q_dev, levels_dev, p_dev, stream=None):
+    import torch
+    _check(lib().ams_probability(Q_dev.numel(), log_weight, _dev(Q_dev, torch.float64), levels_dev.numel(),
+                                 _dev(levels_dev, torch.float64), _dev(p_dev, torch.float64), _stream(stream)))
 
 
 # ---------------------------------------------------------------- no allocation

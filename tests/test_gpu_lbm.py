@@ -172,7 +172,7 @@ def test_window_sum_and_scores_match_oracle(L, orc):
         assert np.allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-15)
         for window, t_end in [(50, 300), (7, 123), (300, 300), (301, 300)]:
             q = torch.zeros(4, dtype=torch.float64, device="cuda")
-            L.lbm_ensemble_scores(e.h, window, t_end, q)
+            L.lbm_ensemble_scores(e.h, window, 0, t_end, q)
             ref = orc.trailing_mean_max(d, window, t_end)
             got = q.cpu().numpy()
             if window > t_end:
@@ -180,7 +180,7 @@ def test_window_sum_and_scores_match_oracle(L, orc):
             else:
                 assert np.allclose(got, ref, rtol=1e-11, atol=1e-14)
         # first crossing of the last scores: brute force on the host series
-        L.lbm_ensemble_scores(e.h, 20, 300, None)
+        L.lbm_ensemble_scores(e.h, 20, 0, 300, None)
         means = np.array([[d[c, t - 20:t].mean() for t in range(20, 301)] for c in range(4)])
         for c in range(4):
             level = np.quantile(means[c], 0.8)
