@@ -77,20 +77,45 @@ enum Storage : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
 
 template <int S> struct Codec;
 
+// dec2/enc2 move two neighbouring elements with one packed conversion.
 template <> struct Codec<kFP32> {
     using T = float;
     __device__ static float dec(T v, float w, float) { return v - w; }
     __device__ static T enc(float g, float w, float) { return g + w; }
+    __device__ static float2 dec2(const T* v, float w, float) { return make_float2(v[0] - w, v[1] - w); }
+    __device__ static void enc2(T* out, float a, float b, float w, float)
+    {
+        out[0] = a + w;
+        out[1] = b + w;
+    }
 };
 template <> struct Codec<kFP16> {
     using T = __half;
     __device__ static float dec(T v, float, float inv_scale) { return __half2float(v) * inv_scale; }
     __device__ static T enc(float g, float, float scale) { return __float2half_rn(g * scale); }
+    __device__ static float2 dec2(const T* v, float, float inv_scale)
+    {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(v));
+        return make_float2(f.x * inv_scale, f.y * inv_scale);
+    }
+    __device__ static void enc2(T* out, float a, float b, float, float scale)
+    {
+        *reinterpret_cast<__half2*>(out) = __floats2half2_rn(a * scale, b * scale);
+    }
 };
 template <> struct Codec<kBF16> {
     using T = __nv_bfloat16;
     __device__ static float dec(T v, float, float inv_scale) { return __bfloat162float(v) * inv_scale; }
     __device__ static T enc(float g, float, float scale) { return __float2bfloat16_rn(g * scale); }
+    __device__ static float2 dec2(const T* v, float, float inv_scale)
+    {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(v));
+        return make_float2(f.x * inv_scale, f.y * inv_scale);
+    }
+    __device__ static void enc2(T* out, float a, float b, float, float scale)
+    {
+        *reinterpret_cast<__nv_bfloat162*>(out) = __floats2bfloat162_rn(a * scale, b * scale);
+    }
 };
 
 // V consecutive stored elements moved as one aligned vector access.

@@ -39,18 +39,27 @@ namespace lbm {
 // 1 + 7.5e-9), and carrying f itself would turn that into a systematic mass
 // drift of om * 7.5e-9 per node and step; with g the same float w_q cancels
 // between load and store.
-template <int S> struct Carry {
+// SCALED = false compiles the 2^s storage scale out (s = 0).
+template <int S, bool SCALED> struct Carry {
     using T = typename Codec<S>::T;
-    __device__ static float in(T v, float w, float inv_scale) { return Codec<S>::dec(v, w, inv_scale); }
-    __device__ static T out(float g, float w, float scale) { return Codec<S>::enc(g, w, scale); }
+    __device__ static float in(T v, float w, float inv_scale) { return Codec<S>::dec(v, w, SCALED ? inv_scale : 1.0f); }
+    __device__ static T out(float g, float w, float scale) { return Codec<S>::enc(g, w, SCALED ? scale : 1.0f); }
+    __device__ static float2 in2(const T* v, float w, float inv_scale)
+    {
+        return Codec<S>::dec2(v, w, SCALED ? inv_scale : 1.0f);
+    }
+    __device__ static void out2(T* o, float a, float b, float w, float scale)
+    {
+        Codec<S>::enc2(o, a, b, w, SCALED ? scale : 1.0f);
+    }
 };
 
-template <int S, int V, bool GENERAL>
+template <int S, int V, bool GENERAL, bool SCALED>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
                                           typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
 {
     using T = typename Codec<S>::T;
-    using K = Carry<S>;
+    using K = Carry<S, SCALED>;
     const int x0 = seg * 32 * V + lane * V;
     const bool active = x0 < p.nx;
     const int row = y * p.pitch;
@@ -88,8 +97,17 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
         const int ex = cx(q), ey = cy(q);
         const bool wall = GENERAL && ((y - ey) < 0 || (y - ey) >= p.ny);
         float d[V];
+        if constexpr (V % 2 == 0) {
 #pragma unroll
-        for (int j = 0; j < V; ++j) d[j] = K::in(v[q].e[j], wf(q), p.inv_scale);
+            for (int j = 0; j < V; j += 2) {
+                const float2 f = K::in2(&v[q].e[j], wf(q), p.inv_scale);
+                d[j] = f.x;
+                d[j + 1] = f.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) d[j] = K::in(v[q].e[j], wf(q), p.inv_scale);
+        }
         if (ex == 0 || wall) {
 #pragma unroll
             for (int j = 0; j < V; ++j) g[q][j] = d[j];
@@ -215,14 +233,19 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             Vec<T, V> o;
+            if constexpr (V % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < V; ++j) o.e[j] = K::out(g[q][j], wf(q), p.scale);
+                for (int j = 0; j < V; j += 2) K::out2(&o.e[j], g[q][j], g[q][j + 1], wf(q), p.scale);
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j) o.e[j] = K::out(g[q][j], wf(q), p.scale);
+            }
             st_stream<T, V>(dst + q * plane + row + x0, o);
         }
     }
 }
 
-template <int S, int V, int WARPS>
+template <int S, int V, int WARPS, bool SCALED>
 __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
 {
     using T = typename Codec<S>::T;
@@ -237,9 +260,9 @@ __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
     const bool wall_row = y == 0 || y == p.ny - 1;
     const bool ring = p.ox1 > p.ox0 && y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1;
     if (wall_row || ring)
-        step_warp<S, V, true>(p, src, dst, c, y, seg, lane);
+        step_warp<S, V, true, SCALED>(p, src, dst, c, y, seg, lane);
     else
-        step_warp<S, V, false>(p, src, dst, c, y, seg, lane);
+        step_warp<S, V, false, SCALED>(p, src, dst, c, y, seg, lane);
 }
 
 template <int S, int V, int WARPS>
@@ -247,7 +270,14 @@ cudaError_t launch_step(const StepParams& p, cudaStream_t s)
 {
     const dim3 block(32, WARPS);
     const dim3 grid(p.nseg, (p.ny + WARPS - 1) / WARPS, p.n_list);
-    step_kernel<S, V, WARPS><<<grid, block, 0, s>>>(p);
+    if constexpr (S == kFP32) {
+        step_kernel<S, V, WARPS, false><<<grid, block, 0, s>>>(p);
+    } else {
+        if (p.scale == 1.0f)
+            step_kernel<S, V, WARPS, false><<<grid, block, 0, s>>>(p);
+        else
+            step_kernel<S, V, WARPS, true><<<grid, block, 0, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
