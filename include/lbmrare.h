@@ -192,18 +192,24 @@ typedef struct {
     double eps;           /* App. D perturbation amplitude; 0 copies exactly */
     uint64_t seed;        /* selection and perturbation streams */
     int32_t window;       /* T of the time-averaged drag for maxima_dev (0: none) */
+    double kappa;         /* learned pre-screen: exponent += kappa (V(t_i) - V(t_{i-1})), V the
+                             attached learned score; 0 = off */
 } lbm_gktl_params;
+/* correction_dev[N] (may be NULL) receives kappa (V(t_end) - V(t0)) of each final
+ * trajectory: the log-weight the estimator removes (gktl_probability). */
 int lbm_gktl_run(lbm_ensemble* e, const lbm_gktl_params* p, double* logR_dev, int32_t* parent_dev,
-                 double* integral_dev, double* maxima_dev);
+                 double* integral_dev, double* maxima_dev, double* correction_dev);
 
 /* GKTL return-time estimator (App. C.2, sign read as the inversion of eq.
  * (Biased_Path_Approximation) requires): for each level a_j,
- *   p_dev[j] = (1/N) sum_n exp(ln Z - k I_n) 1{A_n >= a_j},  ln Z = sum_i logR_dev[i],
+ *   p_dev[j] = (1/N) sum_n exp(ln Z - k I_n - c_n) 1{A_n >= a_j},  ln Z = sum_i logR_dev[i],
  *   r_dev[j] = -(t_a - t_window) / ln(1 - p_dev[j])   (r_dev may be NULL),
- * I_n = integral_dev[n], A_n = maxima_dev[n].  FP64, fixed summation order. */
+ * I_n = integral_dev[n], A_n = maxima_dev[n], c_n = correction_dev[n] (NULL: 0).
+ * FP64, fixed summation order. */
 int gktl_probability(int32_t n, double k, const double* logR_dev, int32_t n_periods, const double* integral_dev,
-                     const double* maxima_dev, int32_t n_levels, const double* levels_dev, double t_a,
-                     double t_window, double* p_dev, double* r_dev, void* stream);
+                     const double* maxima_dev, const double* correction_dev, int32_t n_levels,
+                     const double* levels_dev, double t_a, double t_window, double* p_dev, double* r_dev,
+                     void* stream);
 
 /* AMS run (App. B.1) on trajectories of t_a steps from the ensemble's current
  * time t0 (all clones equal, t0 a multiple of ckpt_stride): advance every
@@ -222,6 +228,9 @@ typedef struct {
     double level;         /* stop once the killed level reaches it (+inf: run J) */
     double eps;           /* App. D perturbation amplitude at branching */
     uint64_t seed;
+    int32_t score_kind;   /* 0: time-averaged drag over window (every step);
+                             1: the attached learned score at every checkpoint
+                             (branching then restores a checkpoint exactly) */
 } lbm_ams_params;
 int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* p, int32_t* iterations, double* log_weight, double* Q_dev,
                 double* levels, int32_t* n_killed);
@@ -230,6 +239,79 @@ int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* p, int32_t* iterations, d
  * states none): p_dev[j] = exp(log_weight) * (1/N) #{n : Q_n >= a_j}. */
 int ams_probability(int32_t n, double log_weight, const double* Q_dev, int32_t n_levels, const double* levels_dev,
                     double* p_dev, void* stream);
+
+/* ---------------------------------------------------------------- learned score */
+
+/* A CNN surrogate of the future time-averaged drag: the paper's conclusion
+ * proposes learning the score function of the rare-event algorithms; this is
+ * that function, trained on trajectories the method itself produces.
+ * Network: conv3x3(8 -> 32) + ReLU, 3 x [conv3x3(32 -> 32) + ReLU], global mean
+ * pool, linear 32 -> 1.  Input x_dev: BF16 [batch][height][width][8] (NHWC;
+ * channels 0..2 the fields of lbm_ensemble_fields, 3..7 zero).  BF16 weights
+ * and activations, FP32 tensor-core accumulation, FP32 master parameters and
+ * Adam.  Parameter vector (FP32, cnn_param_count entries): for conv layer l,
+ * W_l[co][k] with k = (3 ky + kx) * C_in + ci (C_in = 8, then 32), the bias at
+ * k = 9 C_in, zero padding to 80 (layer 0) or 304 columns; then the head
+ * weights v[32] and its bias.  height % 8 == 0, width % 16 == 0. */
+typedef struct cnn_model cnn_model;
+int cnn_create(int32_t height, int32_t width, int32_t max_batch, uint64_t seed, cnn_model** out);
+int cnn_destroy(cnn_model* m);
+int64_t cnn_param_count(const cnn_model* m);
+int cnn_get_params(cnn_model* m, float* host);        /* waits */
+int cnn_set_params(cnn_model* m, const float* host);  /* waits; rejects non-finite values */
+/* pred_dev[b] (FP32) for a batch of inputs */
+int cnn_forward(cnn_model* m, const void* x_dev, int32_t batch, float* pred_dev, void* stream);
+/* gradient of the mean squared error (1/B) sum_b (pred_b - y_b)^2 with respect
+ * to every parameter, into the model's gradient buffer; *loss_dev (may be NULL)
+ * receives the loss.  cnn_get_gradient copies it to the host (waits). */
+int cnn_gradient(cnn_model* m, const void* x_dev, const float* y_dev, int32_t batch, float* loss_dev, void* stream);
+int cnn_get_gradient(cnn_model* m, float* host);
+/* Adam (Kingma & Ba 2015) with bias correction on the master parameters */
+int cnn_adam_step(cnn_model* m, float lr, float beta1, float beta2, float eps, void* stream);
+/* cnn_gradient then cnn_adam_step(lr, 0.9, 0.999, 1e-8) */
+int cnn_train_step(cnn_model* m, const void* x_dev, const float* y_dev, int32_t batch, float lr, float* loss_dev,
+                   void* stream);
+
+int cnn_shape(const cnn_model* m, int32_t* height, int32_t* width, int32_t* max_batch);
+/* predictions for n inputs (any n; evaluated in batches of max_batch) */
+int cnn_predict(cnn_model* m, const void* x_dev, int64_t n, float* pred_dev, void* stream);
+/* epochs of minibatch Adam over a data set x_dev [n][H][W][8], y_dev[n] (FP32):
+ * each epoch visits the samples in a Fisher-Yates order from Philox4x64-10
+ * stream 8 (key (seed, 0), counter (8, epoch, i, 0)); epoch_loss[ep] (host, may
+ * be NULL) gets the mean minibatch loss.  Waits. */
+int cnn_fit(cnn_model* m, const void* x_dev, const float* y_dev, int64_t n, int32_t batch, int32_t epochs, float lr,
+            uint64_t seed, float* epoch_loss, void* stream);
+
+/* Attach a learned score to an ensemble (m = NULL detaches; the model stays the
+ * caller's): from now on every checkpointed state of every stepped clone is
+ * scored, the series following branches (lbm_ams_run with score_kind 1), and
+ * lbm_gktl_run may use it as a pre-screen potential (kappa).  The model input is
+ * the ensemble's fields downsampled by factor; its height and width must be
+ * ny/factor and nx/factor. */
+int lbm_ensemble_attach_score(lbm_ensemble* e, cnn_model* m, int32_t factor, float rho_scale, float u_scale);
+/* score of every clone now, into out_dev[N] (device) */
+int lbm_ensemble_evaluate_score(lbm_ensemble* e, double* out_dev);
+/* the checkpoint score series, host double[N][max_steps/ckpt_stride + 1] (NaN where
+ * not evaluated).  Waits. */
+int lbm_ensemble_score_history(lbm_ensemble* e, double* host);
+
+/* Training data for the learned score from an ensemble run: n_snaps snapshots
+ * of every clone, every `every` steps from the current time t0, as network
+ * inputs x_dev [n_snaps * N][ny/factor][nx/factor][8] (snapshot-major), with
+ * labels y_dev[i * N + c] = the time-averaged drag of clone c over the next
+ * `horizon` steps (eq. (def_time_averaged_drag)), normalised to zero mean and unit
+ * variance; *label_mean, *label_std (may be NULL) receive the scaling.  The
+ * ensemble advances (n_snaps - 1) * every + horizon steps.  Waits. */
+int lbm_surrogate_dataset(lbm_ensemble* e, int32_t n_snaps, int32_t every, int32_t horizon, int32_t factor,
+                          float rho_scale, float u_scale, void* x_dev, float* y_dev, double* label_mean,
+                          double* label_std);
+
+/* Network input of the listed clones (host array): the block mean over
+ * factor x factor nodes of (rho - 1) * rho_scale, u_x * u_scale, u_y * u_scale,
+ * with u = (sum f c - F/2)/rho the velocity of the stored post-collision state,
+ * into dst_dev BF16 [n][ny/factor][nx/factor][8] (channels 3..7 zero).  Waits. */
+int lbm_ensemble_fields(lbm_ensemble* e, const int32_t* clones, int32_t n, int32_t factor, float rho_scale,
+                        float u_scale, void* dst_dev);
 
 /* ---------------------------------------------------------------- no allocation */
 

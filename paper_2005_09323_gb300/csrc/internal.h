@@ -55,7 +55,15 @@ struct StepVariant {
 // all compiled variants of the fused step (lbm_step.cu)
 const std::vector<StepVariant>& step_variants();
 
+// network input of clones listed on the device (cnn.cu); no synchronisation
+int fields_launch(lbm_ensemble* e, const int32_t* list_dev, int32_t n, int32_t factor, float rho_scale, float u_scale,
+                  void* dst_dev);
+// learned score of the listed clones (host list) into out[c * stride + k] (surrogate.cu)
+int score_clones(lbm_ensemble* e, const int32_t* clones, int32_t n, double* out, int32_t stride, int32_t k);
+
 }  // namespace lbm
+
+struct cnn_model;
 
 struct lbm_ensemble {
     lbm_config cfg;
@@ -91,6 +99,16 @@ struct lbm_ensemble {
     double* mass_dev;         // [N]
     double* scores;           // [N][max_steps] trailing means
     int32_t score_window, score_t_begin, score_t_end;  // arguments of the last lbm_ensemble_scores
+    int32_t* fields_list_dev; // clone list of field extractions
+    // learned score attached to the ensemble (lbm_ensemble_attach_score)
+    cnn_model* cnn;
+    int32_t cnn_factor;
+    float cnn_rho_scale, cnn_u_scale;
+    void* cnn_x;              // [max_batch][H][W][8] BF16 network input
+    float* cnn_pred;          // [max_batch]
+    double* cnn_score;        // [N][n_ckpt] score at every checkpoint (NaN until evaluated)
+    double* pot[3];           // GKTL potential: now, previous, start (per slot)
+    double* pot_tmp[2];
     // selected step variant (index into step_variants())
     int variant;
     // optional timing of the fused step launches

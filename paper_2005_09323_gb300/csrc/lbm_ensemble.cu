@@ -471,6 +471,10 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
                     char* to = static_cast<char*>(e->ckpt) + ((size_t)c * e->n_ckpt + k) * bytes;
                     LBM_CUDA(cudaMemcpyAsync(to, from, bytes, cudaMemcpyDeviceToDevice, e->stream));
                 }
+                if (e->cnn) {  // learned score of every checkpointed state
+                    int rc = score_clones(e, list.data(), (int32_t)list.size(), e->cnn_score, e->n_ckpt, k);
+                    if (rc) return rc;
+                }
             }
         }
     }
@@ -602,6 +606,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     ALLOC(e->t_dev, sizeof(int32_t) * n_clones);
     ALLOC(e->list_dev, sizeof(int32_t) * n_clones);
     ALLOC(e->all_dev, sizeof(int32_t) * n_clones);
+    ALLOC(e->fields_list_dev, sizeof(int32_t) * n_clones);
     ALLOC(e->partials, sizeof(float) * (size_t)n_clones * e->batch_cap * e->n_slots);
     ALLOC(e->drag, sizeof(double) * (size_t)n_clones * c.max_steps);
     ALLOC(e->scores, sizeof(double) * (size_t)n_clones * c.max_steps);
@@ -661,7 +666,9 @@ int lbm_ensemble_destroy(lbm_ensemble* e)
         cudaEventDestroy(pr.second);
     }
     void* ptrs[] = {e->buf[0], e->buf[1], e->parity_dev, e->t_dev, e->list_dev, e->all_dev, e->partials,
-                    e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt};
+                    e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt,
+                    e->fields_list_dev, e->cnn_x, e->cnn_pred, e->cnn_score, e->pot[0], e->pot[1], e->pot[2],
+                    e->pot_tmp[0], e->pot_tmp[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete e;
@@ -846,6 +853,9 @@ int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, 
     if (t_b > 0)
         LBM_CUDA(cudaMemcpyAsync(e->drag + (size_t)dst * e->cfg.max_steps, e->drag + (size_t)src * e->cfg.max_steps,
                                  sizeof(double) * t_b, cudaMemcpyDeviceToDevice, e->stream));
+    if (e->cnn_score)  // the learned score of the shared checkpoints
+        LBM_CUDA(cudaMemcpyAsync(e->cnn_score + (size_t)dst * e->n_ckpt, e->cnn_score + (size_t)src * e->n_ckpt,
+                                 sizeof(double) * (kc + 1), cudaMemcpyDeviceToDevice, e->stream));
     // dst is now the source at time tc; replay to t_b (bitwise the source's path)
     e->t_host[dst] = tc;
     LBM_CUDA(cudaMemcpyAsync(e->t_dev + dst, &e->t_host[dst], sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));

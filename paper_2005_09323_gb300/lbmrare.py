@@ -28,6 +28,10 @@ EXPORTS = [
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
     "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
     "lbm_gktl_run", "gktl_probability", "lbm_ams_run", "ams_probability",
+    "cnn_create", "cnn_destroy", "cnn_param_count", "cnn_get_params", "cnn_set_params", "cnn_forward",
+    "cnn_gradient", "cnn_get_gradient", "cnn_adam_step", "cnn_train_step", "lbm_ensemble_fields",
+    "cnn_shape", "cnn_predict", "cnn_fit", "lbm_ensemble_attach_score", "lbm_ensemble_evaluate_score",
+    "lbm_ensemble_score_history", "lbm_surrogate_dataset",
 ]
 
 
@@ -46,12 +50,12 @@ class lbm_config(C.Structure):
 
 class lbm_gktl_params(C.Structure):
     _fields_ = [("period", C.c_int32), ("n_periods", C.c_int32), ("k", C.c_double), ("eps", C.c_double),
-                ("seed", C.c_uint64), ("window", C.c_int32)]
+                ("seed", C.c_uint64), ("window", C.c_int32), ("kappa", C.c_double)]
 
 
 class lbm_ams_params(C.Structure):
     _fields_ = [("t_a", C.c_int32), ("window", C.c_int32), ("max_iter", C.c_int32), ("level", C.c_double),
-                ("eps", C.c_double), ("seed", C.c_uint64)]
+                ("eps", C.c_double), ("seed", C.c_uint64), ("score_kind", C.c_int32)]
 
 
 def config(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, storage="fp32", shift_exp=0,
@@ -105,10 +109,28 @@ def lib():
             "gktl_select": ([i32, p, u64, u64, p, p, p], C.c_int),
             "ams_select": ([i32, p, u64, u64, p, p, p, p, p], C.c_int),
             "lbm_step_noalloc": ([p, i32, p, p, p, p], C.c_int),
-            "lbm_gktl_run": ([p, p, p, p, p, p], C.c_int),
-            "gktl_probability": ([i32, d, p, i32, p, p, i32, p, d, d, p, p, p], C.c_int),
+            "lbm_gktl_run": ([p, p, p, p, p, p, p], C.c_int),
+            "gktl_probability": ([i32, d, p, i32, p, p, p, i32, p, d, d, p, p, p], C.c_int),
             "lbm_ams_run": ([p, p, p, p, p, p, p], C.c_int),
             "ams_probability": ([i32, d, p, i32, p, p, p], C.c_int),
+            "cnn_create": ([i32, i32, i32, u64, p], C.c_int),
+            "cnn_destroy": ([p], C.c_int),
+            "cnn_param_count": ([p], i64),
+            "cnn_get_params": ([p, p], C.c_int),
+            "cnn_set_params": ([p, p], C.c_int),
+            "cnn_forward": ([p, p, i32, p, p], C.c_int),
+            "cnn_gradient": ([p, p, p, i32, p, p], C.c_int),
+            "cnn_get_gradient": ([p, p], C.c_int),
+            "cnn_adam_step": ([p, C.c_float, C.c_float, C.c_float, C.c_float, p], C.c_int),
+            "cnn_train_step": ([p, p, p, i32, C.c_float, p, p], C.c_int),
+            "lbm_ensemble_fields": ([p, p, i32, i32, C.c_float, C.c_float, p], C.c_int),
+            "cnn_shape": ([p, p, p, p], C.c_int),
+            "cnn_predict": ([p, p, i64, p, p], C.c_int),
+            "cnn_fit": ([p, p, p, i64, i32, i32, C.c_float, u64, p, p], C.c_int),
+            "lbm_ensemble_attach_score": ([p, p, i32, C.c_float, C.c_float], C.c_int),
+            "lbm_ensemble_evaluate_score": ([p, p], C.c_int),
+            "lbm_ensemble_score_history": ([p, p], C.c_int),
+            "lbm_surrogate_dataset": ([p, i32, i32, i32, i32, C.c_float, C.c_float, p, p, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -269,27 +291,29 @@ def lbm_ensemble_kernel_time(e, reset: bool = False):
 
 # ---------------------------------------------------------------- drivers
 def lbm_gktl_run(e, period: int, n_periods: int, k: float, eps: float, seed: int, window: int,
-                 logR_dev, parent_dev, integral_dev=None, maxima_dev=None):
+                 logR_dev, parent_dev, integral_dev=None, maxima_dev=None, kappa: float = 0.0, correction_dev=None):
     import torch
-    prm = lbm_gktl_params(period, n_periods, k, eps, seed, window)
+    prm = lbm_gktl_params(period, n_periods, k, eps, seed, window, kappa)
     _check(lib().lbm_gktl_run(e, C.byref(prm), _dev(logR_dev, torch.float64), _dev(parent_dev, torch.int32),
-                              _dev(integral_dev, torch.float64), _dev(maxima_dev, torch.float64)))
+                              _dev(integral_dev, torch.float64), _dev(maxima_dev, torch.float64),
+                              _dev(correction_dev, torch.float64)))
 
 
 def gktl_probability(k: float, logR_dev, integral_dev, maxima_dev, levels_dev, t_a: float, t_window: float,
-                     p_dev, r_dev=None, stream=None):
+                     p_dev, r_dev=None, stream=None, correction_dev=None):
     import torch
     _check(lib().gktl_probability(integral_dev.numel(), k, _dev(logR_dev, torch.float64), logR_dev.numel(),
                                   _dev(integral_dev, torch.float64), _dev(maxima_dev, torch.float64),
-                                  levels_dev.numel(), _dev(levels_dev, torch.float64), t_a, t_window,
+                                  _dev(correction_dev, torch.float64), levels_dev.numel(),
+                                  _dev(levels_dev, torch.float64), t_a, t_window,
                                   _dev(p_dev, torch.float64), _dev(r_dev, torch.float64), _stream(stream)))
 
 
 def lbm_ams_run(e, t_a: int, window: int, max_iter: int, level: float, eps: float, seed: int, Q_dev,
-                with_kills: bool = False):
+                with_kills: bool = False, score_kind: int = 0):
     """returns (iterations, log_weight, levels z_1..z_iterations[, kills per iteration])"""
     import torch
-    prm = lbm_ams_params(t_a, window, max_iter, level, eps, seed)
+    prm = lbm_ams_params(t_a, window, max_iter, level, eps, seed, score_kind)
     it = C.c_int32()
     lw = C.c_double()
     levels = np.zeros(max(max_iter, 1))
@@ -304,6 +328,161 @@ def ams_probability(log_weight: float, Q_dev, levels_dev, p_dev, stream=None):
     import torch
     _check(lib().ams_probability(Q_dev.numel(), log_weight, _dev(Q_dev, torch.float64), levels_dev.numel(),
                                  _dev(levels_dev, torch.float64), _dev(p_dev, torch.float64), _stream(stream)))
+
+
+# ---------------------------------------------------------------- learned score
+CNN_LAYER_K = (80, 304, 304, 304)   # padded columns of each conv layer's weight matrix
+CNN_LAYER_CIN = (8, 32, 32, 32)
+
+
+_cnn_shapes: dict = {}   # handle -> (height, width, max_batch), to check tensor shapes before a launch
+
+
+def cnn_create(height: int, width: int, max_batch: int, seed: int):
+    h = C.c_void_p()
+    _check(lib().cnn_create(height, width, max_batch, seed, C.byref(h)))
+    _cnn_shapes[h.value] = (height, width, max_batch)
+    return h
+
+
+def cnn_destroy(m):
+    _cnn_shapes.pop(m.value, None)
+    _check(lib().cnn_destroy(m))
+
+
+def _cnn_input(m, x):
+    ptr = _bf16_input(x)
+    H, W, mb = _cnn_shapes[m.value]
+    if tuple(x.shape[1:3]) != (H, W):
+        raise TypeError(f"network input is {tuple(x.shape)}, the model takes [B][{H}][{W}][8]")
+    return ptr
+
+
+def cnn_param_count(m) -> int:
+    return lib().cnn_param_count(m)
+
+
+def cnn_get_params(m) -> np.ndarray:
+    a = np.zeros(cnn_param_count(m), dtype=np.float32)
+    _check(lib().cnn_get_params(m, _host(a)))
+    return a
+
+
+def cnn_set_params(m, params: np.ndarray):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != cnn_param_count(m):
+        raise ValueError("parameter vector has the wrong length")
+    _check(lib().cnn_set_params(m, _host(a)))
+
+
+def _bf16_input(x):
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.bfloat16 or not x.is_contiguous():
+        raise TypeError("network input must be a contiguous bfloat16 CUDA tensor [B][H][W][8]")
+    if x.dim() != 4 or x.shape[3] != 8:
+        raise TypeError("network input must have shape [B][H][W][8]")
+    return C.c_void_p(x.data_ptr())
+
+
+def _need(t, n, what):
+    if t.numel() < n:
+        raise TypeError(f"{what} holds {t.numel()} values, needs {n}")
+
+
+def cnn_forward(m, x_dev, pred_dev, stream=None):
+    import torch
+    ptr = _cnn_input(m, x_dev)
+    _need(pred_dev, x_dev.shape[0], "pred_dev")
+    _check(lib().cnn_forward(m, ptr, x_dev.shape[0], _dev(pred_dev, torch.float32), _stream(stream)))
+
+
+def cnn_gradient(m, x_dev, y_dev, loss_dev=None, stream=None):
+    import torch
+    ptr = _cnn_input(m, x_dev)
+    _need(y_dev, x_dev.shape[0], "y_dev")
+    _check(lib().cnn_gradient(m, ptr, _dev(y_dev, torch.float32), x_dev.shape[0],
+                              _dev(loss_dev, torch.float32), _stream(stream)))
+
+
+def cnn_get_gradient(m) -> np.ndarray:
+    a = np.zeros(cnn_param_count(m), dtype=np.float32)
+    _check(lib().cnn_get_gradient(m, _host(a)))
+    return a
+
+
+def cnn_adam_step(m, lr: float, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().cnn_adam_step(m, lr, beta1, beta2, eps, _stream(stream)))
+
+
+def cnn_train_step(m, x_dev, y_dev, lr: float, loss_dev=None, stream=None):
+    import torch
+    ptr = _cnn_input(m, x_dev)
+    _need(y_dev, x_dev.shape[0], "y_dev")
+    _check(lib().cnn_train_step(m, ptr, _dev(y_dev, torch.float32), x_dev.shape[0], lr,
+                                _dev(loss_dev, torch.float32), _stream(stream)))
+
+
+def lbm_ensemble_fields(e, clones, factor: int, rho_scale: float, u_scale: float, dst_dev, nx: int, ny: int):
+    """dst_dev: bfloat16 CUDA tensor [len(clones)][ny/factor][nx/factor][8]"""
+    a = np.ascontiguousarray(clones, dtype=np.int32)
+    ptr = _bf16_input(dst_dev)
+    if factor < 1 or nx % factor or ny % factor:
+        raise ValueError("factor must divide nx and ny")
+    if tuple(dst_dev.shape) != (len(a), ny // factor, nx // factor, 8):
+        raise TypeError(f"dst_dev is {tuple(dst_dev.shape)}, needs {(len(a), ny // factor, nx // factor, 8)}")
+    _check(lib().lbm_ensemble_fields(e, _host(a), len(a), factor, rho_scale, u_scale, ptr))
+
+
+def cnn_shape(m):
+    h, w, b = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().cnn_shape(m, C.byref(h), C.byref(w), C.byref(b)))
+    return h.value, w.value, b.value
+
+
+def cnn_predict(m, x_dev, pred_dev, stream=None):
+    import torch
+    ptr = _cnn_input(m, x_dev)
+    _need(pred_dev, x_dev.shape[0], "pred_dev")
+    _check(lib().cnn_predict(m, ptr, x_dev.shape[0], _dev(pred_dev, torch.float32), _stream(stream)))
+
+
+def cnn_fit(m, x_dev, y_dev, batch: int, epochs: int, lr: float, seed: int, stream=None) -> np.ndarray:
+    import torch
+    ptr = _cnn_input(m, x_dev)
+    _need(y_dev, x_dev.shape[0], "y_dev")
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(lib().cnn_fit(m, ptr, _dev(y_dev, torch.float32), x_dev.shape[0], batch, epochs, lr, seed,
+                         _host(losses), _stream(stream)))
+    return losses[:epochs]
+
+
+def lbm_ensemble_attach_score(e, m, factor: int, rho_scale: float, u_scale: float):
+    _check(lib().lbm_ensemble_attach_score(e, m, factor, rho_scale, u_scale))
+
+
+def lbm_ensemble_evaluate_score(e, out_dev):
+    import torch
+    _check(lib().lbm_ensemble_evaluate_score(e, _dev(out_dev, torch.float64)))
+
+
+def lbm_ensemble_score_history(e, n: int, n_ckpt: int) -> np.ndarray:
+    a = np.zeros((n, n_ckpt))
+    _check(lib().lbm_ensemble_score_history(e, _host(a)))
+    return a
+
+
+def lbm_surrogate_dataset(e, n_snaps: int, every: int, horizon: int, factor: int, rho_scale: float, u_scale: float,
+                          x_dev, y_dev, n_clones: int, nx: int, ny: int):
+    """returns (label_mean, label_std); x_dev [n_snaps*N][ny/f][nx/f][8] bf16, y_dev [n_snaps*N] fp32"""
+    import torch
+    ptr = _bf16_input(x_dev)
+    if tuple(x_dev.shape) != (n_snaps * n_clones, ny // factor, nx // factor, 8):
+        raise TypeError("x_dev has the wrong shape")
+    _need(y_dev, n_snaps * n_clones, "y_dev")
+    mu, sd = C.c_double(), C.c_double()
+    _check(lib().lbm_surrogate_dataset(e, n_snaps, every, horizon, factor, rho_scale, u_scale, ptr,
+                                       _dev(y_dev, torch.float32), C.byref(mu), C.byref(sd)))
+    return mu.value, sd.value
 
 
 # ---------------------------------------------------------------- no allocation

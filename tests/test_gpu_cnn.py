@@ -1,0 +1,157 @@
+"""GPU CNN surrogate (BF16 tensor-core convolutions, FP32 accumulation) against
+the FP64 oracle: forward, gradients of every layer, one Adam step, the field
+extraction from populations, and a training run that fits a known target.
+
+Tolerances: BF16 activations and data gradients carry 8 significant bits; the
+prediction is compared to 1e-2 of its scale, gradients to 3e-2 in relative L2
+norm per layer (the oracle sees the same BF16-rounded weights and inputs)."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2005_09323_gb300 import build, lbmrare
+    build.build()
+    lbmrare.lib()
+    return lbmrare
+
+
+def bf16_round(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def conv_layers_bf16(p):
+    """the GPU multiplies BF16 copies of the conv weights (biases included)"""
+    from oracle import cnn
+    off, n = cnn.offsets()
+    q = np.asarray(p, dtype=np.float64).copy()
+    q[:off[4]] = bf16_round(q[:off[4]])
+    return q
+
+
+def inputs(B, H, W, seed):
+    rng = np.random.default_rng(seed)
+    x = np.zeros((B, H, W, 8), dtype=np.float32)
+    x[..., :3] = rng.normal(0, 1, (B, H, W, 3))
+    xt = torch.tensor(x).to(torch.bfloat16).cuda().contiguous()
+    return xt, xt.float().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture()
+def model(L):
+    m = L.cnn_create(16, 32, 8, 42)
+    yield m
+    L.cnn_destroy(m)
+
+
+def test_forward_matches_oracle(L, orc, model):
+    from oracle import cnn
+    xt, x = inputs(6, 16, 32, 1)
+    pred = torch.zeros(6, dtype=torch.float32, device="cuda")
+    L.cnn_forward(model, xt, pred)
+    p = conv_layers_bf16(L.cnn_get_params(model))
+    ref, _ = cnn.forward(p, x)
+    got = pred.cpu().numpy()
+    scale = np.abs(ref).max() + np.abs(ref - ref.mean()).max()
+    assert np.abs(got - ref).max() <= 1e-2 * scale, (got, ref)
+
+
+def test_gradient_matches_oracle(L, orc, model):
+    """Gradients of every layer against the oracle in two ways.  (1) The oracle
+    with BF16 storage of activations and pre-activation gradients (what the
+    kernels store between layers): same values up to FP32 accumulation order
+    and rounding ties, 1.5e-2 relative L2 per layer.  (2) Pure FP64: the BF16
+    storage error compounds down the backward chain (deeper layers, larger
+    error); bound = 2 x the error that the BF16-storage oracle itself has
+    against FP64, plus 1e-2."""
+    from oracle import cnn
+    xt, x = inputs(4, 16, 32, 2)
+    y = np.array([0.3, -1.2, 0.8, 0.1], dtype=np.float32)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    L.cnn_gradient(model, xt, torch.tensor(y, device="cuda"), loss)
+    g = L.cnn_get_gradient(model).astype(np.float64)
+    p = conv_layers_bf16(L.cnn_get_params(model))
+    ref_loss, ref = cnn.loss_and_grad(p, x, y.astype(np.float64))
+    _, ref16 = cnn.loss_and_grad(p, x, y.astype(np.float64), store=bf16_round)
+    assert abs(loss.item() - ref_loss) <= 2e-2 * ref_loss
+    off, n = cnn.offsets()
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+    for l in range(4):
+        sl = slice(off[l], off[l + 1])
+        assert rel(g[sl], ref16[sl]) < 1.5e-2, (l, rel(g[sl], ref16[sl]))
+        assert rel(g[sl], ref[sl]) < 2 * rel(ref16[sl], ref[sl]) + 1e-2, (l, rel(g[sl], ref[sl]))
+    assert rel(g[off[4]:], ref[off[4]:]) < 1e-2
+
+
+def test_adam_step_matches_oracle(L, model):
+    from oracle import cnn
+    xt, _ = inputs(4, 16, 32, 3)
+    y = torch.tensor([0.5, 0.0, -0.5, 1.0], device="cuda")
+    p0 = L.cnn_get_params(model).astype(np.float64)
+    L.cnn_gradient(model, xt, y)
+    g = L.cnn_get_gradient(model).astype(np.float64)
+    L.cnn_adam_step(model, 1e-3)
+    p1 = L.cnn_get_params(model).astype(np.float64)
+    ref = cnn.Adam(len(p0), 1e-3).step(p0, g)
+    assert np.abs(p1 - ref).max() <= 1e-6
+
+
+def test_training_fits_a_known_target(L, model):
+    """Target: a fixed linear functional of the field means; 300 Adam steps on
+    fresh random batches bring the loss down by over an order of magnitude."""
+    torch.manual_seed(0)
+    losses = []
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for step in range(300):
+        x = torch.zeros((8, 16, 32, 8), device="cuda")
+        x[..., :3] = torch.randn((8, 16, 32, 3), device="cuda") * 0.5 + torch.randn((8, 1, 1, 3), device="cuda")
+        xb = x.to(torch.bfloat16).contiguous()
+        m = xb.float().mean(dim=(1, 2))
+        y = (m[:, 0] - 0.5 * m[:, 1] + 0.25 * m[:, 2]).contiguous()
+        L.cnn_train_step(model, xb, y, 3e-3, loss)
+        losses.append(loss.item())
+    assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:20]), (losses[:5], losses[-5:])
+
+
+def test_fields_match_oracle(L, orc):
+    from oracle import cnn
+    nx, ny = 128, 32
+    kw = dict(nx=nx, ny=ny, obstacle=(30, 12, 8, 8), tau=0.6, gx=2e-5, max_steps=20)
+    cfg = L.config(**kw)
+    e = L.lbm_ensemble_create(cfg, 3, 5, torch.cuda.current_stream())
+    try:
+        L.lbm_ensemble_step(e, 15)
+        dst = torch.zeros((2, ny // 4, nx // 4, 8), dtype=torch.bfloat16, device="cuda")
+        L.lbm_ensemble_fields(e, [2, 0], 4, 1000.0, 50.0, dst, nx, ny)
+        oc = orc.cfg(nx, ny, obstacle=(30, 12, 8, 8), tau=0.6, gx=2e-5)
+        for i, c in enumerate([2, 0]):
+            f = L.lbm_ensemble_get_populations(e, c, nx, ny)
+            ref = cnn.fields(oc, f, 4, 1000.0, 50.0)
+            got = dst[i].float().cpu().numpy()
+            for ch in range(3):
+                scale = np.abs(ref[..., ch]).max()
+                assert np.abs(got[..., ch] - ref[..., ch]).max() <= 1e-2 * scale + 1e-6, ch
+            assert np.all(got[..., 3:] == 0)
+    finally:
+        L.lbm_ensemble_destroy(e)
+
+
+def test_cnn_argument_errors(L, model):
+    with pytest.raises(L.LbmError):
+        L.cnn_create(12, 32, 4, 0)  # height not a multiple of 8
+    x = torch.zeros((9, 16, 32, 8), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(L.LbmError):  # batch beyond max_batch
+        L.cnn_forward(model, x, torch.zeros(9, device="cuda"))
+    with pytest.raises(TypeError):  # wrong image size is caught before any launch
+        L.cnn_forward(model, torch.zeros((2, 8, 32, 8), dtype=torch.bfloat16, device="cuda"),
+                      torch.zeros(2, device="cuda"))
+    bad = L.cnn_get_params(model)
+    bad[5] = np.nan
+    with pytest.raises(L.LbmError):
+        L.cnn_set_params(model, bad)
