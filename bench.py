@@ -266,6 +266,7 @@ def run_ours(args):
     parent = torch.zeros(n_clones, dtype=torch.int32, device="cuda")
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     state = {"t": 0, "it": 0}
+    bank = [i * n_clones // N_SNAP for i in range(N_SNAP)]
 
     def gktl_period():
         t0 = state["t"]
@@ -274,6 +275,7 @@ def run_ours(args):
         if w["cloning"]:
             L.gktl_weights(s, W, logR, stream)
             L.gktl_select(W, 7, state["it"], parent, status, stream)
+            L.lbm_ensemble_set_snapshots(e, bank)  # contemporaneous App. D directions
             L.lbm_ensemble_clone(e, parent, EPS, 7, state["it"])
         state["t"] += PERIOD
         state["it"] += 1
@@ -281,7 +283,7 @@ def run_ours(args):
     # snapshot bank from the initial ensemble (App. D: arbitrary flow states)
     L.lbm_ensemble_step(e, PERIOD)
     state["t"] += PERIOD
-    L.lbm_ensemble_set_snapshots(e, list(range(N_SNAP)))
+    L.lbm_ensemble_set_snapshots(e, bank)
     for _ in range(args.warmup):
         gktl_period()
     torch.cuda.synchronize()
@@ -328,6 +330,7 @@ def run_ours(args):
             L.gktl_weights(s, W, logR, stream)
             L.gktl_select(W, 7, state["it"], parent, status, stream)
             pinned_p.copy_(parent, non_blocking=True)             # D2H
+            L.lbm_ensemble_set_snapshots(e, bank)
             L.lbm_ensemble_clone(e, parent, EPS, 7, state["it"])
         torch.cuda.current_stream().synchronize()
         state["t"] += PERIOD
@@ -382,6 +385,272 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- precision report
+def run_precision_report(args):
+    """Reduced-precision storage against FP32 (and FP32 against the FP64
+    oracle): the precision sweep, 16 clones of 2048 x 512 with a 64 x 64
+    obstacle, tau = 0.505, g_x = 1e-6, 5000 steps from identical seeded states."""
+    import numpy as np
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = WORKLOADS["precision"]
+    nx, ny, n = w["nx"], w["ny"], w["clones"]
+    obst = (nx // 4 - w["side"] // 2, ny // 2 - w["side"] // 2, w["side"], w["side"])
+    T = max(200, args.steps)
+    stream = torch.cuda.current_stream()
+    series, mass = {}, {}
+    storages = ["fp32", "fp16", "bf16"] + [s_ for s_ in ("fp16_sr", "bf16_sr") if s_ in L.STORAGE_NAMES]
+    for st in storages:
+        cfg = L.config(nx, ny, obstacle=obst, tau=TAU, gx=GX, max_steps=T, storage=st)
+        e = L.lbm_ensemble_create(cfg, n, 21, stream)
+        m0, _, _ = L.lbm_ensemble_moments(e, n)
+        L.lbm_ensemble_step(e, T)
+        d = np.zeros((n, T))
+        L.lbm_ensemble_drag(e, 0, T, d)
+        m1, _, _ = L.lbm_ensemble_moments(e, n)
+        series[st], mass[st] = d, float(np.max(np.abs(m1 - m0) / m0))
+        L.lbm_ensemble_destroy(e)
+    # FP32 against the FP64 oracle, one clone, first 100 steps
+    import oracle
+    oc = oracle.cfg(nx, ny, obstacle=obst, tau=TAU, gx=GX)
+    cfg = L.config(nx, ny, obstacle=obst, tau=TAU, gx=GX, max_steps=100)
+    e = L.lbm_ensemble_create(cfg, 1, 21, stream)
+    L.lbm_ensemble_step(e, 100)
+    d32 = np.zeros((1, 100))
+    L.lbm_ensemble_drag(e, 0, 100, d32)
+    f32 = L.lbm_ensemble_get_populations(e, 0, nx, ny)
+    L.lbm_ensemble_destroy(e)
+    f64, d64 = oracle.run(oc, oracle.init(oc, 21, 0, 0.01), 100)
+    ref = series["fp32"]
+    half = T // 2
+    report = {"fp32_vs_fp64_oracle_100_steps": {
+        "population_rel_err": float(np.abs(f32 - f64).max() / np.abs(f64).max()),
+        "drag_rel_err": float(np.abs(d32[0] - d64).max() / np.abs(d64).max())}}
+
+    def ks(a, b):
+        a, b = np.sort(a), np.sort(b)
+        grid = np.concatenate([a, b])
+        return float(np.max(np.abs(np.searchsorted(a, grid, side="right") / len(a)
+                                   - np.searchsorted(b, grid, side="right") / len(b))))
+    for st, d in series.items():
+        tail, rtail = d[:, half:].ravel(), ref[:, half:].ravel()
+        report[st] = {
+            "drag_series_rel_err_vs_fp32": float(np.abs(d - ref).max() / np.abs(ref).max()),
+            "drag_series_rel_err_first_200": float(np.abs(d[:, :200] - ref[:, :200]).max()
+                                                   / np.abs(ref[:, :200]).max()),
+            "mass_drift": mass[st],
+            "drag_mean_rel_dev": float((tail.mean() - rtail.mean()) / abs(rtail.mean())),
+            "drag_std_rel_dev": float((tail.std() - rtail.std()) / rtail.std()),
+            "drag_ks_vs_fp32": ks(tail, rtail),
+            "drag_mean_second_half": float(tail.mean()), "drag_std_second_half": float(tail.std())}
+    print(json.dumps({"metric": "reduced-precision storage error report", "steps": T,
+                      "config": {"workload": f"Precision sweep: N={n} clones, {nx}x{ny}, {w['side']}x{w['side']} "
+                                             f"obstacle, tau={TAU}, g_x={GX}, {T} steps"},
+                      "report": report}))
+
+
+# ---------------------------------------------------------------- time to return time
+def run_return_time(args):
+    """Wall time for a return-time estimate of extreme time-averaged drag at 20%
+    relative error, plain FP32 direct sampling against the batched GKTL form
+    (FP32, FP32 + learned potential, FP16 storage + learned potential).
+
+    Workload: the GKTL ensemble (64 clones of 1024 x 256, 32 x 32 obstacle,
+    tau 0.505, g_x 1e-6) after a 2000-step spin-up, with the averaging window
+    equal to the horizon as in the paper's GKTL experiments: T_a = T = 10000
+    steps, cloning every 500 steps, so that the tilted integral is T F_T.
+    k sigma_I = 2 with sigma_I the spread of that integral over direct runs.
+    Levels a = mean + z sigma of F_T (z = 2, 3) from the direct runs; the
+    direct estimate's relative error is binomial at the Gaussian tail
+    probability (the paper's unbiased reference), the GKTL one is measured over
+    independent replicas.  Wall time to 20% = seconds per replica x (relative
+    error / 0.2)^2."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = WORKLOADS["gktl"]
+    nx, ny, n = w["nx"], w["ny"], w["clones"]
+    obst = (nx // 4 - w["side"] // 2, ny // 2 - w["side"] // 2, w["side"], w["side"])
+    spin, t_a, periods = 2000, 10000, 20
+    window = t_a
+    R = max(3, args.steps)
+    stream = torch.cuda.current_stream()
+    factor, rho_s, u_s = 4, 1000.0, 50.0
+    zs = (2.0, 3.0)
+
+    def make(storage, seed, extra=0):
+        cfg = L.config(nx, ny, obstacle=obst, tau=TAU, gx=GX, max_steps=spin + t_a + extra, n_snapshots=N_SNAP,
+                       storage=storage)
+        return L.lbm_ensemble_create(cfg, n, seed, stream)
+
+    # learned score, trained on an ensemble run of its own (cost reported)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter()
+    H, W = ny // factor, nx // factor
+    m = L.cnn_create(H, W, 64, 1)
+    e = make("fp32", 777, extra=40 * 250 + 2000)
+    L.lbm_ensemble_step(e, spin)
+    n_snaps = 40
+    x = torch.zeros((n_snaps * n, H, W, 8), dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros(n_snaps * n, dtype=torch.float32, device="cuda")
+    L.lbm_surrogate_dataset(e, n_snaps, 250, 2000, factor, rho_s, u_s, x, y, n, nx, ny)
+    L.lbm_ensemble_destroy(e)
+    losses = L.cnn_fit(m, x, y, 64, 10, 1e-3, 3)
+    del x, y
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+
+    def replica(storage, k, kappa, learned, seed):
+        e = make(storage, seed)
+        if learned:
+            L.lbm_ensemble_attach_score(e, m, factor, rho_s, u_s)
+        L.lbm_ensemble_step(e, spin)
+        L.lbm_ensemble_set_snapshots(e, list(range(N_SNAP)))
+        logR = torch.zeros(periods, dtype=torch.float64, device="cuda")
+        parent = torch.zeros(periods * n, dtype=torch.int32, device="cuda")
+        integ = torch.zeros(n, dtype=torch.float64, device="cuda")
+        maxima = torch.zeros(n, dtype=torch.float64, device="cuda")
+        corr = torch.zeros(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.lbm_gktl_run(e, PERIOD, periods, k, EPS, seed, window, logR, parent, integ, maxima,
+                       kappa=kappa, correction_dev=corr, refresh_snapshots=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        par = parent.cpu().numpy().reshape(periods, n)
+        anc = np.arange(n)
+        for i in range(periods - 1, -1, -1):
+            anc = par[i][anc]
+        L.lbm_ensemble_destroy(e)
+        return dict(dt=dt, logR=logR, integ=integ, maxima=maxima, corr=corr, k=k, ancestors=len(set(anc.tolist())))
+
+    direct = [replica("fp32", 0.0, 0.0, False, 100 + r) for r in range(R)]
+    F = torch.cat([d["maxima"] for d in direct]).cpu().numpy()
+    I = torch.cat([d["integ"] for d in direct]).cpu().numpy()
+    mu, sd, sd_i = float(F.mean()), float(F.std()), float(I.std())
+    k = 2.0 / sd_i
+    levels = [mu + z * sd for z in zs]
+    p_gauss = [0.5 * math.erfc(z / math.sqrt(2.0)) for z in zs]
+    variants = {"fp32_gktl": ("fp32", 0.0, False), "fp32_gktl_learned": ("fp32", 0.5, True),
+                "fp16_gktl_learned": ("fp16", 0.5, True)}
+    runs = {"plain_fp32_direct": direct}
+    for name, (st, kappa, learned) in variants.items():
+        runs[name] = [replica(st, k, kappa, learned, 200 + r) for r in range(R)]
+    L.cnn_destroy(m)
+    lv = torch.tensor(levels, dtype=torch.float64, device="cuda")
+    out = {}
+    for name, rs in runs.items():
+        ps = []
+        for d in rs:
+            p = torch.zeros(len(levels), dtype=torch.float64, device="cuda")
+            L.gktl_probability(d["k"], d["logR"], d["integ"], d["maxima"], lv, float(t_a), float(window), p,
+                               correction_dev=d["corr"])
+            ps.append(p.cpu().numpy())
+        ps = np.array(ps)  # [R][levels]
+        t_rep = float(np.mean([d["dt"] for d in rs]))
+        per_level = []
+        for j, z in enumerate(zs):
+            mean = float(ps[:, j].mean())
+            if name == "plain_fp32_direct":
+                cv = math.sqrt((1 - p_gauss[j]) / (n * p_gauss[j]))
+            else:
+                cv = float(ps[:, j].std(ddof=1) / mean) if mean > 0 else float("inf")
+            need = (cv / 0.2) ** 2
+            per_level.append({"z": z, "level": levels[j], "P_mean": mean, "P_gauss": p_gauss[j],
+                              "relative_error_per_replica": cv, "replicas_for_20pct": need,
+                              "seconds_to_20pct": t_rep * need,
+                              # one window per trajectory: waiting time in windows of T steps
+                              "return_time_steps": (-window / math.log1p(-mean)) if 0 < mean < 1 else None})
+        out[name] = {"seconds_per_replica": t_rep, "levels": per_level,
+                     "distinct_ancestors_mean": float(np.mean([d["ancestors"] for d in rs]))}
+    j3 = len(zs) - 1
+    plain = out["plain_fp32_direct"]["levels"][j3]["seconds_to_20pct"]
+    best_name = min(variants, key=lambda v: out[v]["levels"][j3]["seconds_to_20pct"])
+    best = out[best_name]["levels"][j3]["seconds_to_20pct"]
+    print(json.dumps({
+        "metric": "time to a 20%-accurate return-time estimate of extreme time-averaged drag",
+        "value": best, "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": R, "warmup": 0,
+        "data": "synthetic", "dtype": "per variant",
+        "config": {"workload": f"GKTL batched ensemble: N={n} clones, {nx}x{ny}, T_a=T={t_a} steps, cloning every "
+                               f"{PERIOD} steps, k sigma_I = 2, eps={EPS}, spin-up {spin} steps; levels mean + z sigma "
+                               f"of F_T, z = {zs}", "replicas": R, "k_per_step": k, "F_T_mean": mu, "F_T_std": sd},
+        "variants": out, "best_variant_at_highest_level": best_name,
+        "speedup_vs_plain_at_highest_level": plain / best if best > 0 else None,
+        "surrogate_training": {"seconds": t_train, "samples": n_snaps * n, "epochs": len(losses),
+                               "loss_first_last": [float(losses[0]), float(losses[-1])]}}))
+
+
+# ---------------------------------------------------------------- CNN
+def cnn_flops_per_sample(H, W, train: bool) -> float:
+    """algorithmic FLOPs of the surrogate on one H x W input (3 real input
+    channels): 2 x pixels x 32 x taps per conv layer; training adds the weight
+    gradient of every layer and the data gradient of layers 1..3"""
+    P = H * W
+    fwd = 2 * P * 32 * (9 * 3) + 3 * 2 * P * 32 * (9 * 32)
+    if not train:
+        return fwd
+    return fwd + fwd + 3 * 2 * P * 32 * (9 * 32)
+
+
+def run_cnn(args):
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    H, W, B = 64, 256, 256
+    m = L.cnn_create(H, W, B, 1)
+    stream = torch.cuda.current_stream()
+    x = torch.zeros((B, H, W, 8), device="cuda")
+    x[..., :3] = torch.randn((B, H, W, 3), device="cuda")
+    x = x.to(torch.bfloat16).contiguous()
+    y = torch.randn(B, device="cuda")
+    pred = torch.zeros(B, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(args.warmup):
+        L.cnn_forward(m, x, pred, stream)
+        L.cnn_train_step(m, x, y, 1e-4, None, stream)
+    torch.cuda.synchronize()
+    launches0 = L.lbm_launch_count()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        L.cnn_forward(m, x, pred, stream)
+    ev[1].record(stream)
+    for _ in range(args.steps):
+        L.cnn_train_step(m, x, y, 1e-4, None, stream)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    launches = L.lbm_launch_count() - launches0
+    fwd_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    trn_ms = ev[1].elapsed_time(ev[2]) / args.steps
+    L.cnn_destroy(m)
+    fwd_tf = cnn_flops_per_sample(H, W, False) * B / (fwd_ms / 1e3) / 1e12
+    trn_tf = cnn_flops_per_sample(H, W, True) * B / (trn_ms / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    print(json.dumps({
+        "metric": "learned-score CNN throughput", "value": B / (trn_ms / 1e3), "unit": "training samples/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": trn_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"CNN 4x conv3x3 32 ch on {H}x{W} inputs (4x-downsampled 1024x256), batch {B}"},
+        "forward": {"ms_per_batch": fwd_ms, "samples_per_s": B / (fwd_ms / 1e3), "tflops": fwd_tf},
+        "train": {"ms_per_batch": trn_ms, "tflops": trn_tf},
+        "roofline": {"bound": "tensor", "achieved": trn_tf, "peak": peak, "unit": "TFLOP/s", "frac": trn_tf / peak,
+                     "traffic": None, "peak_kind": kind},
+        "gpu_launches": launches}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,11 +662,17 @@ def main():
                     help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "cnn":
+        run_cnn(args)
+    elif args.workload == "return-time":
+        run_return_time(args)
+    elif args.workload == "precision-report":
+        run_precision_report(args)
     else:
         run_ours(args)
 

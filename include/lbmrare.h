@@ -128,6 +128,10 @@ int lbm_ensemble_first_crossing(lbm_ensemble* e, int32_t clone, double level, in
  * clones (host array) and record their masses. */
 int lbm_ensemble_set_snapshots(lbm_ensemble* e, int32_t n_s, const int32_t* clones);
 
+/* As lbm_ensemble_set_snapshots, from the states the listed clones held at
+ * checkpoint k (time k * ckpt_stride). */
+int lbm_ensemble_set_snapshots_from_checkpoint(lbm_ensemble* e, int32_t n_s, const int32_t* clones, int32_t k);
+
 /* GKTL cloning (App. C.1) with the App. D perturbation: every slot s with
  * parent_dev[s] != s (a killed trajectory) becomes a copy of its parent's state,
  * time and drag history, perturbed by eq. (perturb_pop),
@@ -194,6 +198,9 @@ typedef struct {
     int32_t window;       /* T of the time-averaged drag for maxima_dev (0: none) */
     double kappa;         /* learned pre-screen: exponent += kappa (V(t_i) - V(t_{i-1})), V the
                              attached learned score; 0 = off */
+    int32_t refresh_snapshots;  /* 1: before each cloning step refill the App. D bank from the
+                             current states of evenly spaced clones (needed when the flow is not
+                             stationary: stale snapshots pull clones toward an earlier mean flow) */
 } lbm_gktl_params;
 /* correction_dev[N] (may be NULL) receives kappa (V(t_end) - V(t0)) of each final
  * trajectory: the log-weight the estimator removes (gktl_probability). */
@@ -231,6 +238,8 @@ typedef struct {
     int32_t score_kind;   /* 0: time-averaged drag over window (every step);
                              1: the attached learned score at every checkpoint
                              (branching then restores a checkpoint exactly) */
+    int32_t refresh_snapshots;  /* 1: before each branch refill the App. D bank with the states of
+                             evenly spaced trajectories at the branching checkpoint */
 } lbm_ams_params;
 int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* p, int32_t* iterations, double* log_weight, double* Q_dev,
                 double* levels, int32_t* n_killed);

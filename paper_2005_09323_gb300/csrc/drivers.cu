@@ -160,6 +160,10 @@ int lbm_gktl_run(lbm_ensemble* e, const lbm_gktl_params* prm, double* logR_dev, 
     int rc;
     std::vector<int32_t> all(e->n);
     for (int i = 0; i < e->n; ++i) all[i] = i;
+    // clones whose current states refill the App. D bank (evenly spaced)
+    std::vector<int32_t> bank;
+    const int n_bank = std::min(e->cfg.n_snapshots, e->n);
+    for (int i = 0; i < n_bank; ++i) bank.push_back((int32_t)((int64_t)i * e->n / n_bank));
     const int nb = (e->n + 127) / 128;
     if (pot) {  // V at the start of every trajectory: pot[2] (start) and pot[1] (previous)
         if ((rc = score_clones(e, all.data(), e->n, e->pot[2], 1, 0))) return rc;
@@ -178,6 +182,9 @@ int lbm_gktl_run(lbm_ensemble* e, const lbm_gktl_params* prm, double* logR_dev, 
         }
         if ((rc = gktl_weights(e->n, s, W, logR_dev + i, e->stream))) return rc;
         if ((rc = gktl_select(e->n, W, p.seed, (uint64_t)i, par, status, e->stream))) return rc;
+        if (p.refresh_snapshots && p.eps != 0.0) {  // contemporaneous perturbation directions
+            if ((rc = lbm_ensemble_set_snapshots(e, (int32_t)bank.size(), bank.data()))) return rc;
+        }
         if ((rc = lbm_ensemble_clone(e, par, p.eps, p.seed, (uint64_t)i))) return rc;
         if (pot) {
             gather2_kernel<<<nb, 128, 0, e->stream>>>(par, e->pot[0], e->pot[2], e->pot_tmp[0], e->pot_tmp[1], e->n);
@@ -233,6 +240,9 @@ int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* prm, int32_t* iterations,
     const int32_t C = e->cfg.ckpt_stride, k0 = t0 / C, k1 = t_end / C;
     std::vector<int32_t> all(e->n);
     for (int i = 0; i < e->n; ++i) all[i] = i;
+    std::vector<int32_t> bank;
+    const int n_bank = std::min(e->cfg.n_snapshots, e->n);
+    for (int i = 0; i < n_bank; ++i) bank.push_back((int32_t)((int64_t)i * e->n / n_bank));
     // score maxima of the current ensemble
     auto maxima = [&]() -> int {
         if (!learned) return lbm_ensemble_scores(e, p.window, t0, t_end, Q_dev);
@@ -286,6 +296,11 @@ int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* prm, int32_t* iterations,
             if (tb[i] < 0) return fail(LBM_ERR_STATE, "lbm_ams_run: survivor never exceeds the level");
         }
         for (int32_t i = 0; i < nk; ++i) {
+            if (p.refresh_snapshots && p.eps != 0.0) {  // states of the flow at the branching checkpoint
+                const int32_t kc = tb[i] / C;
+                if ((rc = lbm_ensemble_set_snapshots_from_checkpoint(e, (int32_t)bank.size(), bank.data(), kc)))
+                    return rc;
+            }
             if ((rc = lbm_ensemble_branch(e, hk[i], hs[i], tb[i], p.eps, p.seed, (uint64_t)j))) return rc;
             if (t_end > tb[i] && (rc = lbm_ensemble_step_clones(e, t_end - tb[i], &hk[i], 1))) return rc;
         }

@@ -252,6 +252,37 @@ __global__ void moments_final_kernel(const double* partial, int32_t nblocks, con
     if (py) py[c] = y;
 }
 
+// fluid mass of every state in the snapshot bank (fixed-order FP64 partials)
+template <int S>
+__global__ void bank_mass_partial_kernel(const void* snaps, int64_t clone_stride, int64_t plane, int32_t pitch,
+                                         int32_t nx, int32_t ny, int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1,
+                                         float inv_scale, double* partial)
+{
+    using T = typename Codec<S>::T;
+    __shared__ double sh[kRedThreads];
+    const int k = blockIdx.y;
+    const T* base = static_cast<const T*>(snaps) + (int64_t)k * clone_stride;
+    const int64_t sites = (int64_t)nx * ny;
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < sites; i += (int64_t)gridDim.x * kRedThreads) {
+        const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
+        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1) continue;
+        const T* cell = base + (int64_t)y * pitch + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) m += (double)wf(q) + (double)Codec<S>::dec(cell[q * plane], wf(q), inv_scale);
+    }
+    const double sm = block_sum<kRedThreads>(m, sh);
+    if (threadIdx.x == 0) partial[(int64_t)k * gridDim.x + blockIdx.x] = sm;
+}
+
+__global__ void bank_mass_final_kernel(const double* partial, int32_t nblocks, double* snap_mass)
+{
+    if (threadIdx.x != 0) return;
+    double m = 0.0;
+    for (int b = 0; b < nblocks; ++b) m += partial[(int64_t)blockIdx.x * nblocks + b];
+    snap_mass[blockIdx.x] = m;
+}
+
 // App. D: slot s with parent p != s (or s == inplace) becomes
 //   f_s = (f_p + eps sum_n alpha_n f^(n)) * M_p / (M_p + eps sum_n alpha_n M^(n))
 // on fluid nodes, written in the shifted variable g = f - w.
@@ -497,6 +528,23 @@ int compute_masses(lbm_ensemble* e, const int32_t* list_dev, int n_list)
                                                             e->mass_dev + e->n, e->mass_dev + 2 * e->n);
         count_launches(1);
         LBM_CUDA(cudaGetLastError());
+        return LBM_OK;
+    });
+}
+
+int bank_masses(lbm_ensemble* e, int n_s)
+{
+    int ox0, ox1, oy0, oy1;
+    solid_bounds(e->cfg, ox0, ox1, oy0, oy1);
+    return dispatch_storage(e->cfg.storage, [&](auto tag) -> int {
+        constexpr int S = decltype(tag)::value;
+        bank_mass_partial_kernel<S><<<dim3(e->red_blocks, n_s), kRedThreads, 0, e->stream>>>(
+            e->snaps, e->clone_stride, e->plane, e->pitch, e->cfg.nx, e->cfg.ny, ox0, ox1, oy0, oy1, e->inv_scale,
+            e->red_partials);
+        LBM_CUDA(cudaGetLastError());
+        bank_mass_final_kernel<<<n_s, 32, 0, e->stream>>>(e->red_partials, e->red_blocks, e->snap_mass);
+        LBM_CUDA(cudaGetLastError());
+        count_launches(2);
         return LBM_OK;
     });
 }
@@ -790,17 +838,29 @@ int lbm_ensemble_set_snapshots(lbm_ensemble* e, int32_t n_s, const int32_t* clon
                                  cudaMemcpyDeviceToDevice, e->stream));
     }
     if (n_s > 0) {
-        LBM_CUDA(cudaMemcpyAsync(e->list_dev, list.data(), sizeof(int32_t) * n_s, cudaMemcpyHostToDevice, e->stream));
-        int rc = compute_masses(e, e->list_dev, n_s);
+        int rc = bank_masses(e, n_s);
         if (rc) return rc;
-        // gather the masses of the listed clones into the bank, in bank order
-        std::vector<double> m(e->n);
-        LBM_CUDA(cudaMemcpyAsync(m.data(), e->mass_dev, sizeof(double) * e->n, cudaMemcpyDeviceToHost, e->stream));
-        LBM_CUDA(cudaStreamSynchronize(e->stream));
-        std::vector<double> sm(n_s);
-        for (int k = 0; k < n_s; ++k) sm[k] = m[list[k]];
-        LBM_CUDA(cudaMemcpyAsync(e->snap_mass, sm.data(), sizeof(double) * n_s, cudaMemcpyHostToDevice, e->stream));
-        LBM_CUDA(cudaStreamSynchronize(e->stream));
+    }
+    e->n_snaps_set = n_s;
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_snapshots_from_checkpoint(lbm_ensemble* e, int32_t n_s, const int32_t* clones, int32_t k)
+{
+    if (!e || (n_s > 0 && !clones)) return fail(LBM_ERR_ARG, "null argument");
+    if (n_s < 0 || n_s > e->cfg.n_snapshots) return fail(LBM_ERR_ARG, "more snapshots than the bank holds");
+    if (e->n_ckpt < 1 || k < 0 || k >= e->n_ckpt) return fail(LBM_ERR_ARG, "no such checkpoint");
+    const size_t bytes = (size_t)e->clone_stride * e->elem_bytes;
+    for (int i = 0; i < n_s; ++i) {
+        const int c = clones[i];
+        if (c < 0 || c >= e->n) return fail(LBM_ERR_ARG, "clone index out of range");
+        LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(e->snaps) + (size_t)i * bytes,
+                                 static_cast<char*>(e->ckpt) + ((size_t)c * e->n_ckpt + k) * bytes, bytes,
+                                 cudaMemcpyDeviceToDevice, e->stream));
+    }
+    if (n_s > 0) {
+        int rc = bank_masses(e, n_s);
+        if (rc) return rc;
     }
     e->n_snaps_set = n_s;
     return LBM_OK;

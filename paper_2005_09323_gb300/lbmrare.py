@@ -18,6 +18,7 @@ from . import build as _build
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_OOM, LBM_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 LBM_FP32, LBM_FP16_SHIFTED, LBM_BF16_SHIFTED = 0, 1, 2
 STORAGE = {"fp32": LBM_FP32, "fp16": LBM_FP16_SHIFTED, "bf16": LBM_BF16_SHIFTED}
+STORAGE_NAMES = tuple(STORAGE)
 
 EXPORTS = [
     "lbm_last_error", "lbm_launch_count", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_step",
@@ -31,7 +32,7 @@ EXPORTS = [
     "cnn_create", "cnn_destroy", "cnn_param_count", "cnn_get_params", "cnn_set_params", "cnn_forward",
     "cnn_gradient", "cnn_get_gradient", "cnn_adam_step", "cnn_train_step", "lbm_ensemble_fields",
     "cnn_shape", "cnn_predict", "cnn_fit", "lbm_ensemble_attach_score", "lbm_ensemble_evaluate_score",
-    "lbm_ensemble_score_history", "lbm_surrogate_dataset",
+    "lbm_ensemble_score_history", "lbm_surrogate_dataset", "lbm_ensemble_set_snapshots_from_checkpoint",
 ]
 
 
@@ -50,12 +51,14 @@ class lbm_config(C.Structure):
 
 class lbm_gktl_params(C.Structure):
     _fields_ = [("period", C.c_int32), ("n_periods", C.c_int32), ("k", C.c_double), ("eps", C.c_double),
-                ("seed", C.c_uint64), ("window", C.c_int32), ("kappa", C.c_double)]
+                ("seed", C.c_uint64), ("window", C.c_int32), ("kappa", C.c_double),
+                ("refresh_snapshots", C.c_int32)]
 
 
 class lbm_ams_params(C.Structure):
     _fields_ = [("t_a", C.c_int32), ("window", C.c_int32), ("max_iter", C.c_int32), ("level", C.c_double),
-                ("eps", C.c_double), ("seed", C.c_uint64), ("score_kind", C.c_int32)]
+                ("eps", C.c_double), ("seed", C.c_uint64), ("score_kind", C.c_int32),
+                ("refresh_snapshots", C.c_int32)]
 
 
 def config(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, storage="fp32", shift_exp=0,
@@ -131,6 +134,7 @@ def lib():
             "lbm_ensemble_evaluate_score": ([p, p], C.c_int),
             "lbm_ensemble_score_history": ([p, p], C.c_int),
             "lbm_surrogate_dataset": ([p, i32, i32, i32, i32, C.c_float, C.c_float, p, p, p, p], C.c_int),
+            "lbm_ensemble_set_snapshots_from_checkpoint": ([p, i32, p, i32], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -232,6 +236,11 @@ def lbm_ensemble_set_snapshots(e, clones):
     _check(lib().lbm_ensemble_set_snapshots(e, len(a), _host(a)))
 
 
+def lbm_ensemble_set_snapshots_from_checkpoint(e, clones, k: int):
+    a = np.ascontiguousarray(clones, dtype=np.int32)
+    _check(lib().lbm_ensemble_set_snapshots_from_checkpoint(e, len(a), _host(a), k))
+
+
 def lbm_ensemble_clone(e, parent_dev, eps: float, seed: int, it: int):
     import torch
     _check(lib().lbm_ensemble_clone(e, _dev(parent_dev, torch.int32), eps, seed, it))
@@ -291,9 +300,10 @@ def lbm_ensemble_kernel_time(e, reset: bool = False):
 
 # ---------------------------------------------------------------- drivers
 def lbm_gktl_run(e, period: int, n_periods: int, k: float, eps: float, seed: int, window: int,
-                 logR_dev, parent_dev, integral_dev=None, maxima_dev=None, kappa: float = 0.0, correction_dev=None):
+                 logR_dev, parent_dev, integral_dev=None, maxima_dev=None, kappa: float = 0.0, correction_dev=None,
+                 refresh_snapshots: bool = False):
     import torch
-    prm = lbm_gktl_params(period, n_periods, k, eps, seed, window, kappa)
+    prm = lbm_gktl_params(period, n_periods, k, eps, seed, window, kappa, int(refresh_snapshots))
     _check(lib().lbm_gktl_run(e, C.byref(prm), _dev(logR_dev, torch.float64), _dev(parent_dev, torch.int32),
                               _dev(integral_dev, torch.float64), _dev(maxima_dev, torch.float64),
                               _dev(correction_dev, torch.float64)))
@@ -310,10 +320,10 @@ def gktl_probability(k: float, logR_dev, integral_dev, maxima_dev, levels_dev, t
 
 
 def lbm_ams_run(e, t_a: int, window: int, max_iter: int, level: float, eps: float, seed: int, Q_dev,
-                with_kills: bool = False, score_kind: int = 0):
+                with_kills: bool = False, score_kind: int = 0, refresh_snapshots: bool = False):
     """returns (iterations, log_weight, levels z_1..z_iterations[, kills per iteration])"""
     import torch
-    prm = lbm_ams_params(t_a, window, max_iter, level, eps, seed, score_kind)
+    prm = lbm_ams_params(t_a, window, max_iter, level, eps, seed, score_kind, int(refresh_snapshots))
     it = C.c_int32()
     lw = C.c_double()
     levels = np.zeros(max(max_iter, 1))

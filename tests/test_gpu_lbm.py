@@ -231,6 +231,27 @@ def test_clone_exact_copy_and_perturbation(L, orc):
         assert np.array_equal(e.pops(3), before[2])  # kept its own slot (a copy of 2 since the first call)
 
 
+def test_snapshot_bank_from_checkpoints(L, orc):
+    """The App. D bank refilled from checkpointed states (the flow at the
+    branching time) perturbs exactly like states taken live at that time."""
+    kw = dict(RAGGED, max_steps=100, ckpt_stride=20, n_snapshots=2)
+    oc = oracle_cfg(orc, kw)
+    with Ens(L, 4, seed=3, **kw) as e:
+        L.lbm_ensemble_step(e.h, 40)
+        at40 = [e.pops(c) for c in range(4)]
+        L.lbm_ensemble_step(e.h, 25)
+        L.lbm_ensemble_set_snapshots_from_checkpoint(e.h, [3, 1], 2)
+        before = e.pops(2)
+        parent = torch.tensor([0, 1, 0, 3], dtype=torch.int32, device="cuda")
+        L.lbm_ensemble_clone(e.h, parent, 0.002, 5, 9)
+        alpha = orc.perturb_alphas(5, 9, 2, 2)
+        ref = orc.perturb(oc, e.pops(0), np.stack([at40[3], at40[1]]), alpha, 0.002)
+        assert rel(e.pops(2), ref) < 1e-6
+        assert not np.array_equal(e.pops(2), before)
+        with pytest.raises(L.LbmError):
+            L.lbm_ensemble_set_snapshots_from_checkpoint(e.h, [0], 99)
+
+
 def test_branch_replays_bitwise(L):
     """AMS branching restores the last checkpoint and replays: with eps = 0 the
     branch is the source trajectory, state and drag, bit for bit."""
