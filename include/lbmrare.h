@@ -171,6 +171,12 @@ int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant);
 int lbm_step_variant_info(int32_t variant, int32_t* storage, int32_t* vec, int32_t* warps);
 int32_t lbm_step_variant_count(void);
 
+/* Failure-detection self test of the bounded device-side waits used by the
+ * row-staged step kernels: one thread polls an mbarrier that nothing arrives
+ * at, `spins` times, then gives up; *status (host) receives LBM_ERR_TIMEOUT.
+ * The context stays usable.  Waits. */
+int lbm_selftest_bounded_wait(int64_t spins, void* stream, int32_t* status);
+
 /* Kernel timing: when enabled, every batch of fused-step launches is bracketed
  * by CUDA events on the ensemble's stream; lbm_ensemble_kernel_time waits and
  * returns the summed milliseconds and launch count since the last reset. */

@@ -362,15 +362,21 @@ struct Ring {
     int ry0, ry1, rs0, rs1, n_slots;
 };
 
+// vec = 0: row-staged kernels, one slot per consumer warp in each ring row
 Ring ring_for(const lbm_config& c, int vec)
 {
     Ring r{0, -1, 0, -1, 0};
     if (c.obs_w <= 0) return r;
-    const int seg_w = 32 * vec;
     r.ry0 = std::max(c.obs_y0 - 1, 0);
     r.ry1 = std::min(c.obs_y0 + c.obs_h, c.ny - 1);
-    r.rs0 = (c.obs_x0 - 1) / seg_w;
-    r.rs1 = (c.obs_x0 + c.obs_w) / seg_w;
+    if (vec > 0) {
+        const int seg_w = 32 * vec;
+        r.rs0 = (c.obs_x0 - 1) / seg_w;
+        r.rs1 = (c.obs_x0 + c.obs_w) / seg_w;
+    } else {
+        r.rs0 = 0;
+        r.rs1 = kRowWarps - 1;
+    }
     r.n_slots = (r.ry1 - r.ry0 + 1) * (r.rs1 - r.rs0 + 1);
     return r;
 }
@@ -384,7 +390,7 @@ int default_variant(int storage)
     return -1;
 }
 
-StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_list, int vec, int step)
+StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_list, int vec, int step, int kind = 0)
 {
     const lbm_config& c = e->cfg;
     StepParams p{};
@@ -399,11 +405,12 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
     p.plane = e->plane;
     p.clone_stride = e->clone_stride;
     p.nseg = (c.nx + 32 * vec - 1) / (32 * vec);
+    p.err_flag = e->flag_dev + 2;
     p.ox0 = c.obs_x0;
     p.ox1 = c.obs_w > 0 ? c.obs_x0 + c.obs_w : c.obs_x0;
     p.oy0 = c.obs_y0;
     p.oy1 = c.obs_w > 0 ? c.obs_y0 + c.obs_h : c.obs_y0;
-    const Ring r = ring_for(c, vec);
+    const Ring r = ring_for(c, kind == 1 ? 0 : vec);
     p.ry0 = r.ry0;
     p.ry1 = r.ry1;
     p.rs0 = r.rs0;
@@ -414,6 +421,7 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
     p.omega = (float)(1.0 / c.tau);
     p.gx = (float)c.gx;
     p.gy = (float)c.gy;
+    p.bgk = bgk_consts(p.omega, p.gx, p.gy);
     p.scale = e->scale;
     p.inv_scale = e->inv_scale;
     p.step_in_batch = step;
@@ -422,10 +430,11 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
 
 int check_sticky(lbm_ensemble* e)
 {
-    int32_t flag = 0;
-    LBM_CUDA(cudaMemcpyAsync(&flag, e->flag_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
+    int32_t flag[3] = {0, 0, 0};
+    LBM_CUDA(cudaMemcpyAsync(flag, e->flag_dev, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, e->stream));
     LBM_CUDA(cudaStreamSynchronize(e->stream));
-    if (flag) return fail(LBM_ERR_NONFINITE, "a drag value of the ensemble is not finite (unstable flow?)");
+    if (flag[2]) return fail(LBM_ERR_TIMEOUT, "a bounded device-side wait of the fused step ran out");
+    if (flag[0]) return fail(LBM_ERR_NONFINITE, "a drag value of the ensemble is not finite (unstable flow?)");
     return LBM_OK;
 }
 
@@ -456,7 +465,7 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
     const auto& vars = step_variants();
     const StepVariant& v = vars[e->variant];
     const int n_list = (int)list.size();
-    const Ring r = ring_for(e->cfg, v.vec);
+    const Ring r = ring_for(e->cfg, v.kind == 1 ? 0 : v.vec);
     int32_t t = e->t_host[list[0]];
     int32_t left = n_steps;
     while (left > 0) {
@@ -472,7 +481,7 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
             LBM_CUDA(cudaEventRecord(ev0, e->stream));
         }
         for (int s = 0; s < chunk; ++s) {
-            StepParams p = make_params(e, list_dev, n_list, v.vec, s);
+            StepParams p = make_params(e, list_dev, n_list, v.vec, s, v.kind);
             cudaError_t err = v.launch(p, e->stream);
             if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
             count_launches(1);
@@ -633,7 +642,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     // partial slots: enough for the narrowest segments of any variant
     int max_slots = 1;
     for (const auto& v : step_variants())
-        if (v.storage == c.storage) max_slots = std::max(max_slots, ring_for(c, v.vec).n_slots);
+        if (v.storage == c.storage) max_slots = std::max(max_slots, ring_for(c, v.kind == 1 ? 0 : v.vec).n_slots);
     e->n_slots = max_slots;
     e->n_ckpt = c.ckpt_stride > 0 ? c.max_steps / c.ckpt_stride + 1 : 0;
     e->parity_host.assign(n_clones, 0);
@@ -658,7 +667,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     ALLOC(e->partials, sizeof(float) * (size_t)n_clones * e->batch_cap * e->n_slots);
     ALLOC(e->drag, sizeof(double) * (size_t)n_clones * c.max_steps);
     ALLOC(e->scores, sizeof(double) * (size_t)n_clones * c.max_steps);
-    ALLOC(e->flag_dev, sizeof(int32_t) * 2);
+    ALLOC(e->flag_dev, sizeof(int32_t) * 4);
     ALLOC(e->red_partials, sizeof(double) * 3 * (size_t)n_clones * e->red_blocks);
     ALLOC(e->mass_dev, sizeof(double) * 3 * n_clones);
     if (c.n_snapshots > 0) {
@@ -674,7 +683,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     if ((rc = chk(cudaMemcpyAsync(e->all_dev, iota.data(), sizeof(int32_t) * n_clones, cudaMemcpyHostToDevice, e->stream), "copy clone index"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->parity_dev, 0, sizeof(int32_t) * n_clones, e->stream), "memset parity"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->t_dev, 0, sizeof(int32_t) * n_clones, e->stream), "memset time"))) return rc;
-    if ((rc = chk(cudaMemsetAsync(e->flag_dev, 0, sizeof(int32_t) * 2, e->stream), "memset flag"))) return rc;
+    if ((rc = chk(cudaMemsetAsync(e->flag_dev, 0, sizeof(int32_t) * 4, e->stream), "memset flag"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->buf[0], 0, state_bytes, e->stream), "memset state"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->buf[1], 0, state_bytes, e->stream), "memset state"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->partials, 0, sizeof(float) * (size_t)n_clones * e->batch_cap * e->n_slots, e->stream), "memset partials"))) return rc;
@@ -1034,7 +1043,8 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
     for (size_t i = 0; i < vars.size(); ++i) {
         const StepVariant& v = vars[i];
         if (v.storage != e->cfg.storage) continue;
-        StepParams p = make_params(e, e->all_dev, e->n, v.vec, 0);
+        StepParams p = make_params(e, e->all_dev, e->n, v.vec, 0, v.kind);
+        if (v.supports && !v.supports(p)) continue;
         const int reps = 5;
         for (int r = 0; r < 2; ++r) LBM_CUDA(v.launch(p, e->stream));
         LBM_CUDA(cudaEventRecord(a, e->stream));

@@ -54,6 +54,41 @@ template <int S, bool SCALED> struct Carry {
     }
 };
 
+// one opposite pair (q, opp q) of the collision, from the shared E and O terms
+__device__ __forceinline__ void bgk_pair(float& gq, float& go, float cu, float A, float B, float wq, float P, float Qc,
+                                         float a0, float omm)
+{
+    const float E = fmaf(cu, fmaf(Qc, cu, A), a0);
+    const float O = fmaf(P, cu, B);
+    gq = fmaf(wq, E + O, omm * gq);
+    go = fmaf(wq, E - O, omm * go);
+}
+
+// BGK collision with Guo forcing of site j, in place on the carried values
+// g = f - w, in the pairwise form of BgkConsts
+template <int V>
+__device__ __forceinline__ void bgk_collide(float (&g)[9][V], int j, const BgkConsts& k)
+{
+    const float s1 = g[1][j] + g[3][j], d1 = g[1][j] - g[3][j];
+    const float s2 = g[2][j] + g[4][j], d2 = g[2][j] - g[4][j];
+    const float s5 = g[5][j] + g[7][j], d5 = g[5][j] - g[7][j];
+    const float s6 = g[6][j] + g[8][j], d6 = g[6][j] - g[8][j];
+    const float drho = (g[0][j] + s1) + (s2 + (s5 + s6));
+    const float jx = d1 + (d5 - d6), jy = d2 + (d5 + d6);
+    const float inv = __fdividef(1.0f, 1.0f + drho);
+    const float ux = (jx + k.hgx) * inv, uy = (jy + k.hgy) * inv;
+    const float P = fmaf(k.om3, drho, k.om3);  // 3 om rho
+    const float Qc = 1.5f * P;                  // 4.5 om rho
+    const float u2 = fmaf(ux, ux, uy * uy);
+    float a0 = fmaf(k.om, drho, -(0.5f * P) * u2);
+    a0 = fmaf(-k.kgx, ux, fmaf(-k.kgy, uy, a0));
+    g[0][j] = fmaf(wf(0), a0, k.omm * g[0][j]);
+    bgk_pair(g[1][j], g[3][j], ux, k.A[0], k.B[0], wf(1), P, Qc, a0, k.omm);
+    bgk_pair(g[2][j], g[4][j], uy, k.A[1], k.B[1], wf(2), P, Qc, a0, k.omm);
+    bgk_pair(g[5][j], g[7][j], ux + uy, k.A[2], k.B[2], wf(5), P, Qc, a0, k.omm);
+    bgk_pair(g[6][j], g[8][j], uy - ux, k.A[3], k.B[3], wf(6), P, Qc, a0, k.omm);
+}
+
 template <int S, int V, bool GENERAL, bool SCALED>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
                                           typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
@@ -148,47 +183,9 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
         }
     }
 
-    // ---- phase 3: BGK collision with Guo forcing.
-    // With drho = rho - 1 = sum g and the carried value g = f - w:
-    //   g*_q = (1 - om) g_q + w_q [a0 + 3k cF_q + cu (3 om rho + 9k cF_q + 4.5 om rho cu)]
-    //   a0 = om drho - 1.5 om rho u.u - 3k u.F,
-    // k = 1 - om/2, cu = c_q.u, cF_q = c_q.F: the equilibrium of App. A plus
-    // the Guo source, expanded.
-    const float om = p.omega, one_m_om = 1.0f - om, kap3 = 3.0f * (1.0f - 0.5f * om);
-    const float gx = p.gx, gy = p.gy;
+    // ---- phase 3: BGK collision with Guo forcing
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        float sum = 0.f, jx = 0.f, jy = 0.f;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            sum += g[q][j];
-            if (cx(q) > 0) jx += g[q][j];
-            if (cx(q) < 0) jx -= g[q][j];
-            if (cy(q) > 0) jy += g[q][j];
-            if (cy(q) < 0) jy -= g[q][j];
-        }
-        const float drho = sum;
-        const float rho = 1.0f + drho;
-        const float inv = __fdividef(1.0f, rho);
-        const float ux = (jx + 0.5f * gx) * inv;
-        const float uy = (jy + 0.5f * gy) * inv;
-        const float omr = om * rho;
-        const float P = 3.0f * omr, Qc = 4.5f * omr;
-        const float a0 = om * drho - 1.5f * omr * (ux * ux + uy * uy) - kap3 * (ux * gx + uy * gy);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float wq = wf(q);
-            if (q == 0) {
-                g[0][j] = fmaf(wq, a0, one_m_om * g[0][j]);
-                continue;
-            }
-            const float cu = (cx(q) == 0 ? 0.f : (float)cx(q) * ux) + (cy(q) == 0 ? 0.f : (float)cy(q) * uy);
-            const float cF = (cx(q) == 0 ? 0.f : (float)cx(q) * gx) + (cy(q) == 0 ? 0.f : (float)cy(q) * gy);
-            const float t = fmaf(Qc, cu, fmaf(3.0f * kap3, cF, P));
-            const float t2 = fmaf(cu, t, fmaf(kap3, cF, a0));
-            g[q][j] = fmaf(wq, t2, one_m_om * g[q][j]);
-        }
-    }
+    for (int j = 0; j < V; ++j) bgk_collide<V>(g, j, p.bgk);
 
     if (GENERAL && ox1 > ox0) {
         if (y >= oy0 && y < oy1) {

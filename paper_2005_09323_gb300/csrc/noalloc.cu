@@ -144,6 +144,7 @@ extern "C" int lbm_step_noalloc(const lbm_config* cfg, int32_t n_clones, const v
     p.omega = (float)(1.0 / c.tau);
     p.gx = (float)c.gx;
     p.gy = (float)c.gy;
+    p.bgk = bgk_consts(p.omega, p.gx, p.gy);
     const int sexp = c.storage == kFP32 ? 0 : c.shift_exp;
     p.scale = (float)std::ldexp(1.0, sexp);
     p.inv_scale = (float)std::ldexp(1.0, -sexp);

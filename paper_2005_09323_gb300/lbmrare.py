@@ -33,6 +33,7 @@ EXPORTS = [
     "cnn_gradient", "cnn_get_gradient", "cnn_adam_step", "cnn_train_step", "lbm_ensemble_fields",
     "cnn_shape", "cnn_predict", "cnn_fit", "lbm_ensemble_attach_score", "lbm_ensemble_evaluate_score",
     "lbm_ensemble_score_history", "lbm_surrogate_dataset", "lbm_ensemble_set_snapshots_from_checkpoint",
+    "lbm_selftest_bounded_wait",
 ]
 
 
@@ -135,6 +136,7 @@ def lib():
             "lbm_ensemble_score_history": ([p, p], C.c_int),
             "lbm_surrogate_dataset": ([p, i32, i32, i32, i32, C.c_float, C.c_float, p, p, p, p], C.c_int),
             "lbm_ensemble_set_snapshots_from_checkpoint": ([p, i32, p, i32], C.c_int),
+            "lbm_selftest_bounded_wait": ([i64, p, p], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -289,6 +291,12 @@ def lbm_step_variant_info(variant: int):
 
 def lbm_ensemble_set_timing(e, enable: bool):
     _check(lib().lbm_ensemble_set_timing(e, int(bool(enable))))
+
+
+def lbm_selftest_bounded_wait(spins: int, stream=None) -> int:
+    st = C.c_int32(0)
+    _check(lib().lbm_selftest_bounded_wait(spins, _stream(stream), C.byref(st)))
+    return st.value
 
 
 def lbm_ensemble_kernel_time(e, reset: bool = False):

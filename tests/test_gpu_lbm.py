@@ -108,6 +108,39 @@ def test_every_variant_on_ragged_grid(L, orc):
     assert tried >= 3
 
 
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_every_16bit_variant_agrees(L, storage):
+    """All compiled variants of one storage format (register-staged row
+    segments, bulk-copy-staged whole rows) compute the same populations bit for
+    bit; the drag differs only by the grouping of its partial sums."""
+    kw = dict(RAGGED, max_steps=50, storage=storage)
+    ref = None
+    n_var = L.lbm_step_variant_count()
+    for v in range(n_var):
+        st, vec, warps = L.lbm_step_variant_info(v)
+        if st != L.STORAGE[storage]:
+            continue
+        with Ens(L, 3, seed=9, **kw) as e:
+            L.lbm_ensemble_set_variant(e.h, v)
+            L.lbm_ensemble_step(e.h, 30)
+            got = ([e.pops(c) for c in range(3)], e.drag(0, 30))
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got[0], ref[0]):
+            assert np.array_equal(a, b), (vec, warps)
+        assert np.abs(got[1] - ref[1]).max() <= 1e-5 * np.abs(ref[1]).max()
+
+
+def test_bounded_wait_runs_out_and_reports(L):
+    """A device-side wait on an mbarrier that nothing completes gives up after
+    its spin limit and reports LBM_ERR_TIMEOUT; the context remains usable."""
+    assert L.lbm_selftest_bounded_wait(20000) == L.LBM_ERR_TIMEOUT
+    with Ens(L, 1, **dict(RAGGED, max_steps=4)) as e:
+        L.lbm_ensemble_step(e.h, 2)
+        assert np.all(np.isfinite(e.drag(0, 2)))
+
+
 def test_one_step_from_arbitrary_state(L, orc):
     """A single step from a non-equilibrium state loaded into the GPU."""
     kw = dict(nx=96, ny=20, obstacle=(30, 7, 5, 6), tau=0.8, gx=1e-4, gy=2e-5, max_steps=10)
