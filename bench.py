@@ -57,17 +57,31 @@ K_SIGMA = 1.0
 SIGMA_DRAG = 1e-3        # drag scale used to set k (k = K_SIGMA / (SIGMA_DRAG * PERIOD))
 BYTES_PER_SITE = 72      # FP32: 9 loads + 9 stores of 4 bytes
 METRIC = "Ensemble D2Q9 GLUPS & HBM-roofline fraction; time-to-return-time vs plain"
-# DRAM traffic of one fused-step launch measured by ncu on this workload, and
-# the kernel source it was measured on (reported only while the source matches)
-NCU_TRAFFIC = {"sha": "12cee4d507c8406e", "bytes_per_site": 68.5474}  # mean of 3 launches, 64 clones
+# DRAM traffic of one fused-step launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of 3 launches of the full workload), per site,
+# with the kernel sources it was measured on: reported only while they match
+NCU_TRAFFIC = {
+    ("gktl", "step_kernel<fp32, vec=4, warps=4>"): {
+        "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp32.cu"),
+        "sha": "d8352fcdf3e131b9", "bytes_per_site": 68.4740},
+    ("precision", "step_rows_kernel<fp16, vec=4, warps=9>"): {
+        "files": ("lbm_step_rows.cuh", "lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp16.cu"),
+        "sha": "b182c50ad811bd2e", "bytes_per_site": 32.5181},
+}
 
 
-def kernel_sha() -> str:
+def kernel_sha(files=NCU_TRAFFIC[("gktl", "step_kernel<fp32, vec=4, warps=4>")]["files"]) -> str:
     h = hashlib.sha256()
-    for f in ("lbm_step.cuh", "lbm_device.cuh", "step_fp32.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2005_09323_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def kernel_label(L, variant: int, storage: str) -> str:
+    _, vec, warps = L.lbm_step_variant_info(variant)
+    name = "step_rows_kernel" if L.lbm_step_variant_kind(variant) == 1 else "step_kernel"
+    return f"{name}<{storage}, vec={vec}, warps={warps}>"
 
 
 def peaks():
@@ -258,7 +272,7 @@ def run_ours(args):
     else:
         variant = int(args.variant)
         L.lbm_ensemble_set_variant(e, variant)
-    vinfo = L.lbm_step_variant_info(variant)
+    label = kernel_label(L, variant, args.storage)
     k = K_SIGMA / (SIGMA_DRAG * PERIOD)
     s = torch.zeros(n_clones, dtype=torch.float64, device="cuda")
     W = torch.zeros_like(s)
@@ -359,9 +373,9 @@ def run_ours(args):
     bytes_per_site = BYTES_PER_SITE if args.storage == "fp32" else BYTES_PER_SITE // 2
     achieved = bytes_per_site * sites / (avg_launch_ms / 1e3) / 1e9
     traffic = None
-    if (NCU_TRAFFIC["sha"] == kernel_sha() and NCU_TRAFFIC["bytes_per_site"] and args.workload == "gktl"
-            and args.storage == "fp32"):
-        traffic = NCU_TRAFFIC["bytes_per_site"] * sites
+    rec = NCU_TRAFFIC.get((args.workload, label))
+    if rec and rec["sha"] == kernel_sha(rec["files"]) and not args.clones:
+        traffic = rec["bytes_per_site"] * sites
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -370,7 +384,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": f"step_kernel<{args.storage}, vec={vinfo[1]}, warps={vinfo[2]}>",
+                         "kernel": label,
                          "peak_kind": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_site": bytes_per_site,
                          "avg_launch_us": avg_launch_ms * 1e3},
             "e2e": {"value": e2e_value, "unit": "GLUPS", "h2d_bytes_per_step": 8 * n_clones,
@@ -651,6 +665,77 @@ def run_cnn(args):
         "gpu_launches": launches}))
 
 
+def run_ams_branch(args):
+    """The AMS branching phase (App. B.1): after a kill, one trajectory is
+    restarted and stepped alone to T_a, in chunks cut by its checkpoints.  One
+    bench step = one branch of 2000 lattice steps of one 512x128 trajectory of
+    the AMS workload with a checkpoint every 250 steps, taken in turn from a
+    pool of 16 trajectories; timed with step-chunk graphs (the default) and
+    with one direct launch per lattice step."""
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = workload(argparse.Namespace(workload="ams", clones=16))
+    n, branch, stride = 16, 2000, 250
+    if 2 * (args.steps + args.warmup) > n * (10000 // branch):
+        raise SystemExit("ams-branch: at most 27 steps + warm-up")
+    stream = torch.cuda.current_stream()
+    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], tau=TAU, gx=GX, storage=L.STORAGE[args.storage],
+                   max_steps=10000, ckpt_stride=stride)
+    e = L.lbm_ensemble_create(cfg, n, 1, stream)
+    if args.variant != "auto":
+        L.lbm_ensemble_set_variant(e, int(args.variant))
+    nxt = [0]
+
+    def one_branch():
+        c = nxt[0] % n
+        nxt[0] += 1
+        L.lbm_ensemble_step_clones(e, branch, [c])
+
+    res = {}
+    launches = 0
+    for graphs in (True, False):
+        L.lbm_ensemble_set_graphs(e, graphs)
+        for _ in range(args.warmup):
+            one_branch()
+        torch.cuda.synchronize()
+        l0 = L.lbm_launch_count()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            one_branch()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        res[graphs] = ms
+        if graphs:
+            launches = L.lbm_launch_count() - l0
+    L.lbm_ensemble_destroy(e)
+    sites = w["nx"] * w["ny"]
+    glups = {g: sites * branch / (ms / 1e3) / 1e9 for g, ms in res.items()}
+    bps = BYTES_PER_SITE if args.storage == "fp32" else BYTES_PER_SITE // 2
+    hbm, peak_kind = peaks()
+    achieved = bps * sites * branch / (res[True] / 1e3) / 1e9
+    print(json.dumps({
+        "metric": "AMS branch-phase stepping rate (one trajectory)", "value": glups[True], "unit": "GLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[True], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"AMS branch: one {w['nx']}x{w['ny']} trajectory ({args.storage}), {branch} lattice "
+                               f"steps per bench step, checkpoint every {stride} steps, pool of {n}",
+                   "storage": args.storage,
+                   "l2": "working set of one trajectory (two buffers) is L2-resident; no flush: this is the "
+                         "branch phase as AMS runs it"},
+        "direct_launches": {"value": glups[False], "unit": "GLUPS", "ms_per_step": res[False],
+                            "us_per_lattice_step": 1e3 * res[False] / branch},
+        "graphs": {"us_per_lattice_step": 1e3 * res[True] / branch, "speedup": res[False] / res[True]},
+        "roofline": {"bound": "latency", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs; algorithmic bytes of an L2-resident "
+                                                   f"working set, so frac may exceed 1"},
+        "gpu_launches": launches}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -662,7 +747,7 @@ def main():
                     help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report"])
+    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     args = ap.parse_args()
     if args.impl == "reference":
@@ -673,6 +758,8 @@ def main():
         run_return_time(args)
     elif args.workload == "precision-report":
         run_precision_report(args)
+    elif args.workload == "ams-branch":
+        run_ams_branch(args)
     else:
         run_ours(args)
 

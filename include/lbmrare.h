@@ -170,12 +170,25 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant);
 int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant);
 int lbm_step_variant_info(int32_t variant, int32_t* storage, int32_t* vec, int32_t* warps);
 int32_t lbm_step_variant_count(void);
+/* Data movement of a variant: 0 = register-staged row segments, one warp per
+ * segment (lbm_step.cuh); 1 = whole rows staged in shared memory by bulk
+ * copies (lbm_step_rows.cuh).  LBM_ERR_ARG for an index out of range. */
+int32_t lbm_step_variant_kind(int32_t variant);
 
 /* Failure-detection self test of the bounded device-side waits used by the
  * row-staged step kernels: one thread polls an mbarrier that nothing arrives
  * at, `spins` times, then gives up; *status (host) receives LBM_ERR_TIMEOUT.
  * The context stays usable.  Waits. */
 int lbm_selftest_bounded_wait(int64_t spins, void* stream, int32_t* status);
+
+/* CUDA graphs (on by default): each chunk of fused-step launches between two
+ * drag finalisations is captured once per (variant, clone list, chunk length)
+ * into a CUDA graph, cached (24 per ensemble, least recently used dropped) and
+ * replayed on the ensemble's stream.  The replay does the same work as the
+ * launches; it removes the per-launch host cost, which bounds the step rate
+ * of small ensembles such as one AMS branch.  enable = 0 launches each step
+ * directly.  Errors: LBM_ERR_ARG for a null ensemble. */
+int lbm_ensemble_set_graphs(lbm_ensemble* e, int32_t enable);
 
 /* Kernel timing: when enabled, every batch of fused-step launches is bracketed
  * by CUDA events on the ensemble's stream; lbm_ensemble_kernel_time waits and

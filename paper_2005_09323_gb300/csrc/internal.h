@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "lbmrare.h"
+#include "step_params.h"
 
 namespace lbm {
 
@@ -21,75 +22,6 @@ int cuda_fail(cudaError_t err, const char* what);
         cudaError_t err_ = (call);                            \
         if (err_ != cudaSuccess) return cuda_fail(err_, #call); \
     } while (0)
-
-// Everything one fused stream-collide launch needs.  Populations of clone c
-// live at buf[p] + c * clone_stride, direction q at + q * plane, row y at
-// + y * pitch; p alternates per clone with its own parity.
-// Constants of the BGK collision with Guo forcing, in the pairwise form the
-// step kernels use (the BGK collision and D2Q9 equilibrium of App. A with
-// Guo's body-force term, expanded).  With the
-// carried value g = f - w, drho = sum g, u = (sum c g + F/2) / rho and
-// kap3 = 3 (1 - om/2), the post-collision value of direction q is
-//   g*_q = (1 - om) g_q + w_q t_q,
-//   t_q  = a0 + kap3 cF + cu (3 om rho + 3 kap3 cF + 4.5 om rho cu),
-//   a0   = om drho - 1.5 om rho u.u - kap3 u.F,   cu = c_q.u,  cF = c_q.F.
-// For the opposite direction cu and cF change sign, so a pair shares
-//   E = a0 + cu (A + 4.5 om rho cu),  O = B + 3 om rho cu,
-//   t_q = E + O,  t_opp = E - O,      A = 3 kap3 cF,  B = kap3 cF,
-// for the pairs (1,3), (2,4), (5,7), (6,8) with cF = F_x, F_y, F_x + F_y,
-// F_y - F_x.  Computed once on the host so that every kernel reads them as
-// launch constants.
-struct BgkConsts {
-    float om, omm, om3;  // omega, 1 - omega, 3 omega
-    float hgx, hgy;      // F/2
-    float kgx, kgy;      // kap3 F
-    float A[4], B[4];    // per direction pair
-};
-
-inline BgkConsts bgk_consts(float om, float gx, float gy)
-{
-    BgkConsts k;
-    const float kap3 = 3.0f * (1.0f - 0.5f * om);
-    k.om = om;
-    k.omm = 1.0f - om;
-    k.om3 = 3.0f * om;
-    k.hgx = 0.5f * gx;
-    k.hgy = 0.5f * gy;
-    k.kgx = kap3 * gx;
-    k.kgy = kap3 * gy;
-    const float cf[4] = {gx, gy, gx + gy, gy - gx};
-    for (int i = 0; i < 4; ++i) {
-        k.B[i] = kap3 * cf[i];
-        k.A[i] = 3.0f * k.B[i];
-    }
-    return k;
-}
-
-struct StepParams {
-    void* buf0;
-    void* buf1;
-    const int32_t* parity;      // [N] current buffer of each clone
-    const int32_t* clone_list;  // clones advanced by this launch
-    int32_t n_list;
-    int32_t nx, ny, pitch;
-    int64_t plane, clone_stride;
-    int32_t nseg;               // row segments of 32*V sites
-    // obstacle: solid cells [ox0, ox1) x [oy0, oy1); ox1 == ox0 for none
-    int32_t ox0, ox1, oy0, oy1;
-    // drag ring: rows [ry0, ry1], segments [rs0, rs1]; one partial per warp
-    int32_t ry0, ry1, rs0, rs1, n_slots, batch_cap;
-    float* partials;            // [N][batch_cap][n_slots]
-    float omega;                // 1/tau
-    float gx, gy;               // body-force density
-    float scale, inv_scale;     // 16-bit shift scale 2^s and its inverse
-    int32_t step_in_batch;
-    int32_t* err_flag;          // set to 1 when a bounded device-side wait runs out (may be null)
-    BgkConsts bgk;              // bgk_consts(omega, gx, gy)
-};
-
-// consumer warps of the row-staged step kernel; each writes its own drag
-// partial for every obstacle-ring row it computes
-constexpr int kRowWarps = 8;
 
 struct StepVariant {
     int storage;
@@ -159,6 +91,19 @@ struct lbm_ensemble {
     double* pot_tmp[2];
     // selected step variant (index into step_variants())
     int variant;
+    // step chunks captured once as CUDA graphs and replayed: one cached
+    // executable per (variant, clone list, list length, chunk length)
+    struct StepGraph {
+        int variant;
+        const int32_t* list;
+        int32_t n_list, chunk;
+        cudaGraphExec_t exec;
+        uint64_t used;
+    };
+    std::vector<StepGraph> graphs;
+    uint64_t graph_clock;
+    bool use_graphs;          // on by default (lbm_ensemble_set_graphs)
+    cudaStream_t cap_stream;  // private stream the chunks are captured on
     // optional timing of the fused step launches
     bool timing;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;

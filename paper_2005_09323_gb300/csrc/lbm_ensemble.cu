@@ -49,6 +49,7 @@ const std::vector<StepVariant>& step_variants()
 }
 
 constexpr int kBatchCap = 512;     // steps per drag-finalisation batch
+constexpr int kGraphCache = 24;    // cached step-chunk graphs per ensemble
 constexpr int kRedBlocks = 152;    // blocks of a per-clone reduction (one wave)
 constexpr int kRedThreads = 256;
 
@@ -458,6 +459,59 @@ int solid_bounds(const lbm_config& c, int& ox0, int& ox1, int& oy0, int& oy1)
     return 0;
 }
 
+// the fused step launches of one chunk: steps 0 .. chunk-1 of a drag batch.
+// With graphs on, the chunk is captured once (on a private stream, so that the
+// caller's stream may be the legacy default stream) and the cached executable
+// is replayed on the ensemble's stream; every kernel argument except the step
+// index is fixed for the life of the ensemble, and the clone list is read
+// through its device pointer at run time, so a replay is the same work as the
+// launches it was captured from.
+int launch_chunk(lbm_ensemble* e, const int32_t* list_dev, int n_list, int chunk)
+{
+    const StepVariant& v = step_variants()[e->variant];
+    if (!e->use_graphs) {
+        for (int s = 0; s < chunk; ++s) {
+            cudaError_t err = v.launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
+            if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
+        }
+        count_launches(chunk);
+        return LBM_OK;
+    }
+    lbm_ensemble::StepGraph* hit = nullptr;
+    for (auto& g : e->graphs)
+        if (g.variant == e->variant && g.list == list_dev && g.n_list == n_list && g.chunk == chunk) hit = &g;
+    if (!hit) {
+        if (!e->cap_stream) LBM_CUDA(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+        LBM_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed));
+        cudaError_t launch_err = cudaSuccess;
+        for (int s = 0; s < chunk && launch_err == cudaSuccess; ++s)
+            launch_err = v.launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t end_err = cudaStreamEndCapture(e->cap_stream, &graph);
+        if (launch_err != cudaSuccess || end_err != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return cuda_fail(launch_err != cudaSuccess ? launch_err : end_err, "capture of the step chunk");
+        }
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t inst_err = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (inst_err != cudaSuccess) return cuda_fail(inst_err, "cudaGraphInstantiate of the step chunk");
+        if (e->graphs.size() >= (size_t)kGraphCache) {  // drop the least recently used
+            auto lru = std::min_element(e->graphs.begin(), e->graphs.end(),
+                                        [](const auto& a, const auto& b) { return a.used < b.used; });
+            cudaGraphExecDestroy(lru->exec);
+            e->graphs.erase(lru);
+        }
+        e->graphs.push_back({e->variant, list_dev, n_list, chunk, exec, 0});
+        hit = &e->graphs.back();
+    }
+    hit->used = ++e->graph_clock;
+    LBM_CUDA(cudaGraphLaunch(hit->exec, e->stream));
+    count_launches(chunk);
+    return LBM_OK;
+}
+
 // run the fused step n times on the listed clones (all at time t), with drag
 // finalisation per batch and checkpoints at multiples of ckpt_stride
 int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_t>& list, int32_t n_steps)
@@ -480,12 +534,7 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
             LBM_CUDA(cudaEventCreate(&ev1));
             LBM_CUDA(cudaEventRecord(ev0, e->stream));
         }
-        for (int s = 0; s < chunk; ++s) {
-            StepParams p = make_params(e, list_dev, n_list, v.vec, s, v.kind);
-            cudaError_t err = v.launch(p, e->stream);
-            if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
-            count_launches(1);
-        }
+        if (int rc = launch_chunk(e, list_dev, n_list, chunk)) return rc;
         if (e->timing) {
             LBM_CUDA(cudaEventRecord(ev1, e->stream));
             e->events.emplace_back(ev0, ev1);
@@ -589,6 +638,13 @@ int64_t lbm_launch_count(void) { return g_launches.load(std::memory_order_relaxe
 
 int32_t lbm_step_variant_count(void) { return (int32_t)step_variants().size(); }
 
+int32_t lbm_step_variant_kind(int32_t variant)
+{
+    const auto& v = step_variants();
+    if (variant < 0 || variant >= (int32_t)v.size()) return fail(LBM_ERR_ARG, "variant index out of range");
+    return v[variant].kind;
+}
+
 int lbm_step_variant_info(int32_t variant, int32_t* storage, int32_t* vec, int32_t* warps)
 {
     const auto& v = step_variants();
@@ -637,6 +693,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     e->scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : c.shift_exp);
     e->inv_scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : -c.shift_exp);
     e->variant = default_variant(c.storage);
+    e->use_graphs = true;
     e->batch_cap = kBatchCap;
     e->red_blocks = kRedBlocks;
     // partial slots: enough for the narrowest segments of any variant
@@ -722,6 +779,8 @@ int lbm_ensemble_destroy(lbm_ensemble* e)
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
+    for (auto& g : e->graphs) cudaGraphExecDestroy(g.exec);
+    if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
     void* ptrs[] = {e->buf[0], e->buf[1], e->parity_dev, e->t_dev, e->list_dev, e->all_dev, e->partials,
                     e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt,
                     e->fields_list_dev, e->cnn_x, e->cnn_pred, e->cnn_score, e->pot[0], e->pot[1], e->pot[2],
@@ -1063,6 +1122,13 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
     cudaEventDestroy(b);
     e->variant = best;
     if (variant) *variant = best;
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_graphs(lbm_ensemble* e, int32_t enable)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    e->use_graphs = enable != 0;
     return LBM_OK;
 }
 

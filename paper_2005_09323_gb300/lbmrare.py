@@ -27,6 +27,7 @@ EXPORTS = [
     "lbm_ensemble_branch", "lbm_ensemble_moments", "lbm_ensemble_get_populations",
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
+    "lbm_ensemble_set_graphs", "lbm_step_variant_kind",
     "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
     "lbm_gktl_run", "gktl_probability", "lbm_ams_run", "ams_probability",
     "cnn_create", "cnn_destroy", "cnn_param_count", "cnn_get_params", "cnn_set_params", "cnn_forward",
@@ -107,7 +108,9 @@ def lib():
             "lbm_ensemble_set_variant": ([p, i32], C.c_int),
             "lbm_step_variant_info": ([i32, p, p, p], C.c_int),
             "lbm_step_variant_count": ([], i32),
+            "lbm_step_variant_kind": ([i32], i32),
             "lbm_ensemble_set_timing": ([p, i32], C.c_int),
+            "lbm_ensemble_set_graphs": ([p, i32], C.c_int),
             "lbm_ensemble_kernel_time": ([p, p, p, i32], C.c_int),
             "gktl_weights": ([i32, p, p, p, p], C.c_int),
             "gktl_select": ([i32, p, u64, u64, p, p, p], C.c_int),
@@ -283,6 +286,13 @@ def lbm_step_variant_count() -> int:
     return lib().lbm_step_variant_count()
 
 
+def lbm_step_variant_kind(variant: int) -> int:
+    k = lib().lbm_step_variant_kind(variant)
+    if k < 0:
+        _check(k)
+    return k
+
+
 def lbm_step_variant_info(variant: int):
     s, v, w = C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib().lbm_step_variant_info(variant, C.byref(s), C.byref(v), C.byref(w)))
@@ -291,6 +301,10 @@ def lbm_step_variant_info(variant: int):
 
 def lbm_ensemble_set_timing(e, enable: bool):
     _check(lib().lbm_ensemble_set_timing(e, int(bool(enable))))
+
+
+def lbm_ensemble_set_graphs(e, enable: bool):
+    _check(lib().lbm_ensemble_set_graphs(e, int(bool(enable))))
 
 
 def lbm_selftest_bounded_wait(spins: int, stream=None) -> int:

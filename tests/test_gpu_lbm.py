@@ -235,6 +235,27 @@ def test_subset_step_equals_full_step(L):
         assert list(L.lbm_ensemble_time(b.h, 4)) == [30, 0, 30, 0]
 
 
+def test_graph_replay_equals_direct_launches(L):
+    """Replayed step-chunk graphs do the same work as direct launches: the
+    same populations and drag bit for bit, for whole-ensemble chunks, chunks
+    cut by checkpoints, and subset steps whose clone list changes between
+    replays of one cached graph."""
+    kw = dict(RAGGED, max_steps=200, ckpt_stride=25)
+    out = []
+    for graphs in (False, True):
+        with Ens(L, 4, seed=12, **kw) as e:
+            L.lbm_ensemble_set_graphs(e.h, graphs)
+            L.lbm_ensemble_step(e.h, 60)       # chunks 25, 25, 10
+            L.lbm_ensemble_step(e.h, 15)       # 15
+            for c in [3, 1, 0, 2]:             # one cached graph, four different lists
+                L.lbm_ensemble_step_clones(e.h, 15, [c])
+            L.lbm_ensemble_step(e.h, 50)
+            out.append(([e.pops(c) for c in range(4)], e.drag(0, 140)))
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_clone_exact_copy_and_perturbation(L, orc):
     kw = dict(RAGGED, max_steps=100, n_snapshots=3)
     oc = oracle_cfg(orc, kw)
