@@ -301,6 +301,20 @@ int cnn_train_step(cnn_model* m, const void* x_dev, const float* y_dev, int32_t 
                    void* stream);
 
 int cnn_shape(const cnn_model* m, int32_t* height, int32_t* width, int32_t* max_batch);
+/* Kernels of the three hidden 32 -> 32 layers (forward and data gradient).
+ * path 0 (default): fifth-generation tensor cores (tcgen05.mma with the
+ * accumulator in tensor memory, operands staged by TMA) wherever the shape
+ * allows: width a multiple of 128 or a divisor of 128 (>= 8) and height a
+ * multiple of 256 / min(width, 128); other shapes use path 1.  path 1: the
+ * warp-level mma.sync kernels.  Both compute the same layer (FP32 accumulation
+ * of BF16 products; the summation order differs).  The input layer and the
+ * weight gradients use mma.sync.  LBM_ERR_ARG for another path. */
+int cnn_set_conv_path(cnn_model* m, int32_t path);
+/* Waits for the stream, then LBM_ERR_TIMEOUT if a bounded device-side wait of
+ * a tensor-core convolution ran out since the model was created (the kernel
+ * records it and returns; the context stays usable), else LBM_OK.  cnn_fit
+ * checks the same flag after every minibatch. */
+int cnn_status(cnn_model* m, void* stream);
 /* predictions for n inputs (any n; evaluated in batches of max_batch) */
 int cnn_predict(cnn_model* m, const void* x_dev, int64_t n, float* pred_dev, void* stream);
 /* epochs of minibatch Adam over a data set x_dev [n][H][W][8], y_dev[n] (FP32):

@@ -528,6 +528,8 @@ struct cnn_model {
     float* lossb;   // [1]
     int32_t* idx;   // [max_batch] sample indices of the minibatch
     int64_t adam_t;
+    int32_t conv_path;  // 0: tensor-core (tcgen05) hidden layers where the shape allows; 1: mma.sync everywhere
+    int32_t* err;       // device flag: a bounded device-side wait ran out
 };
 
 namespace {
@@ -547,16 +549,39 @@ int export_weights(cnn_model* m, cudaStream_t s)
     return LBM_OK;
 }
 
+bool use_tc(const cnn_model* m, int batch)
+{
+    return m->conv_path == 0 && conv3x3_tc_supported(batch, m->H, m->W);
+}
+
+// one hidden 32 -> 32 layer: forward (ReLU(conv + bias)) or data gradient
+// (conv with W' masked by the layer below)
+int conv32(cnn_model* m, const bf16* x, const bf16* w, const bf16* mask, bf16* out, int batch, bool bwd,
+           cudaStream_t s)
+{
+    if (use_tc(m, batch)) return conv3x3_tc(x, w, mask, out, batch, m->H, m->W, bwd, m->err, s);
+    const dim3 grid(m->W / kTW, m->H / kTH, batch);
+    if (bwd)
+        conv3x3_kernel<kC, true><<<grid, 128, 0, s>>>(x, w, mask, out, m->H, m->W);
+    else
+        conv3x3_kernel<kC, false><<<grid, 128, 0, s>>>(x, w, nullptr, out, m->H, m->W);
+    LBM_CUDA(cudaGetLastError());
+    count_launches(1);
+    return LBM_OK;
+}
+
 int forward(cnn_model* m, const bf16* x, int batch, cudaStream_t s)
 {
     const dim3 grid(m->W / kTW, m->H / kTH, batch);
     conv3x3_kernel<kCin0, false><<<grid, 128, 0, s>>>(x, m->w[0], nullptr, m->act[0], m->H, m->W);
+    LBM_CUDA(cudaGetLastError());
+    count_launches(1);
     for (int l = 1; l < kLayers; ++l)
-        conv3x3_kernel<kC, false><<<grid, 128, 0, s>>>(m->act[l - 1], m->w[l], nullptr, m->act[l], m->H, m->W);
+        if (int rc = conv32(m, m->act[l - 1], m->w[l], nullptr, m->act[l], batch, false, s)) return rc;
     head_forward_kernel<<<batch, 256, 0, s>>>(m->act[kLayers - 1], m->H * m->W, m->master + m->off[kLayers],
                                              m->pooled, m->pred);
     LBM_CUDA(cudaGetLastError());
-    count_launches(kLayers + 1);
+    count_launches(1);
     return LBM_OK;
 }
 
@@ -588,15 +613,11 @@ int gradient(cnn_model* m, const bf16* x, const float* y, int batch, float* loss
     LBM_CUDA(cudaGetLastError());
     count_launches(2);
     int cur = 0;
-    const dim3 grid(m->W / kTW, m->H / kTH, batch);
     for (int l = kLayers - 1; l >= 0; --l) {
         const bf16* in = l == 0 ? x : m->act[l - 1];
         if ((rc = wgrad(m, l, in, m->dy[cur], batch, s))) return rc;
         if (l > 0) {
-            conv3x3_kernel<kC, true><<<grid, 128, 0, s>>>(m->dy[cur], m->wt[l], m->act[l - 1], m->dy[cur ^ 1], m->H,
-                                                          m->W);
-            LBM_CUDA(cudaGetLastError());
-            count_launches(1);
+            if ((rc = conv32(m, m->dy[cur], m->wt[l], m->act[l - 1], m->dy[cur ^ 1], batch, true, s))) return rc;
             cur ^= 1;
         }
     }
@@ -675,9 +696,11 @@ int cnn_create(int32_t height, int32_t width, int32_t max_batch, uint64_t seed, 
     ALLOC(m->yb, sizeof(float) * max_batch);
     ALLOC(m->lossb, sizeof(float));
     ALLOC(m->idx, sizeof(int32_t) * max_batch);
+    ALLOC(m->err, sizeof(int32_t));
 #undef ALLOC
     if ((err = cudaMemcpy(m->master, host.data(), sizeof(float) * o, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cleanup(cuda_fail(err, "cnn_create upload"));
+    cudaMemset(m->err, 0, sizeof(int32_t));
     cudaMemset(m->grad, 0, sizeof(float) * o);
     cudaMemset(m->adam_m, 0, sizeof(float) * o);
     cudaMemset(m->adam_v, 0, sizeof(float) * o);
@@ -696,7 +719,7 @@ int cnn_destroy(cnn_model* m)
     if (!m) return LBM_OK;
     cudaDeviceSynchronize();
     void* ptrs[] = {m->master, m->grad, m->adam_m, m->adam_v, m->off_dev, m->w_dev, m->wt_dev, m->dy[0], m->dy[1],
-                    m->pooled, m->pred, m->seed, m->wpart, m->xb, m->yb, m->lossb, m->idx};
+                    m->pooled, m->pred, m->seed, m->wpart, m->xb, m->yb, m->lossb, m->idx, m->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int l = 0; l < kLayers; ++l) {
@@ -780,6 +803,25 @@ int cnn_train_step(cnn_model* m, const void* x_dev, const float* y_dev, int32_t 
     return cnn_adam_step(m, lr, 0.9f, 0.999f, 1e-8f, stream);
 }
 
+int cnn_set_conv_path(cnn_model* m, int32_t path)
+{
+    if (!m) return fail(LBM_ERR_ARG, "cnn_set_conv_path: null model");
+    if (path != 0 && path != 1) return fail(LBM_ERR_ARG, "cnn_set_conv_path: path must be 0 or 1");
+    m->conv_path = path;
+    return LBM_OK;
+}
+
+int cnn_status(cnn_model* m, void* stream)
+{
+    if (!m) return fail(LBM_ERR_ARG, "cnn_status: null model");
+    int32_t err = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LBM_CUDA(cudaMemcpyAsync(&err, m->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LBM_CUDA(cudaStreamSynchronize(s));
+    if (err) return fail(LBM_ERR_TIMEOUT, "cnn: a bounded device-side wait of the convolution ran out");
+    return LBM_OK;
+}
+
 int cnn_shape(const cnn_model* m, int32_t* height, int32_t* width, int32_t* max_batch)
 {
     if (!m) return fail(LBM_ERR_ARG, "cnn_shape: null model");
@@ -834,8 +876,11 @@ int cnn_fit(cnn_model* m, const void* x_dev, const float* y_dev, int64_t n, int3
             rc = cnn_adam_step(m, lr, 0.9f, 0.999f, 1e-8f, s);
             if (rc) return rc;
             float l = 0.f;
+            int32_t err = 0;
             LBM_CUDA(cudaMemcpyAsync(&l, m->lossb, sizeof(float), cudaMemcpyDeviceToHost, s));
+            LBM_CUDA(cudaMemcpyAsync(&err, m->err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             LBM_CUDA(cudaStreamSynchronize(s));  // also keeps perm alive for the index copy
+            if (err) return fail(LBM_ERR_TIMEOUT, "cnn_fit: a bounded device-side wait of the convolution ran out");
             if (!std::isfinite(l)) return fail(LBM_ERR_NONFINITE, "cnn_fit: loss not finite");
             total += l;
             ++nb;

@@ -35,6 +35,15 @@ struct StepVariant {
 // all compiled variants of the fused step (lbm_step.cu)
 const std::vector<StepVariant>& step_variants();
 
+// tensor-core (tcgen05) 3x3 convolution 32 -> 32 channels over NHWC BF16
+// activations (conv_tc.cu): bwd = false: ReLU(conv(x, w) + bias); bwd = true:
+// conv(x, w) masked by mask > 0.  err (device int) is set on a device-side
+// timeout.  Supported shapes: W a multiple of 128 or a divisor of 128 (>= 8),
+// H a multiple of 2 * 128 / min(W, 128).
+bool conv3x3_tc_supported(int B, int H, int W);
+int conv3x3_tc(const void* x, const void* w, const void* mask, void* out, int B, int H, int W, bool bwd,
+               int32_t* err, cudaStream_t s);
+
 // network input of clones listed on the device (cnn.cu); no synchronisation
 int fields_launch(lbm_ensemble* e, const int32_t* list_dev, int32_t n, int32_t factor, float rho_scale, float u_scale,
                   void* dst_dev);

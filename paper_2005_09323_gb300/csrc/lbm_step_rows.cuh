@@ -18,6 +18,7 @@
 #pragma once
 #include "internal.h"
 #include "lbm_device.cuh"
+#include "async_copy.cuh"
 
 namespace lbm {
 
@@ -25,50 +26,6 @@ constexpr int kRowConsumers = 32 * kRowWarps;
 constexpr int kRowThreads = kRowConsumers + 32;   // + 1 producer warp
 constexpr int kRowMaxStages = 8;
 constexpr int kRowSmemBudget = 110 * 1024;        // two blocks per SM
-constexpr long long kWaitSpins = 1ll << 26;       // ~ seconds of polling before giving up
-
-__device__ inline uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
-
-__device__ inline void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
-}
-
-__device__ inline void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ inline void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
-}
-
-__device__ inline bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ inline void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// bounded wait; false on timeout
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (long long i = 0; i < kWaitSpins; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
 
 // what the consumers of a stage need to know about its work item
 struct StageInfo {

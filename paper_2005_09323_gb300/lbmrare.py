@@ -27,7 +27,7 @@ EXPORTS = [
     "lbm_ensemble_branch", "lbm_ensemble_moments", "lbm_ensemble_get_populations",
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
-    "lbm_ensemble_set_graphs", "lbm_step_variant_kind",
+    "lbm_ensemble_set_graphs", "lbm_step_variant_kind", "cnn_set_conv_path", "cnn_status",
     "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
     "lbm_gktl_run", "gktl_probability", "lbm_ams_run", "ams_probability",
     "cnn_create", "cnn_destroy", "cnn_param_count", "cnn_get_params", "cnn_set_params", "cnn_forward",
@@ -132,6 +132,8 @@ def lib():
             "cnn_train_step": ([p, p, p, i32, C.c_float, p, p], C.c_int),
             "lbm_ensemble_fields": ([p, p, i32, i32, C.c_float, C.c_float, p], C.c_int),
             "cnn_shape": ([p, p, p, p], C.c_int),
+            "cnn_set_conv_path": ([p, i32], C.c_int),
+            "cnn_status": ([p, p], C.c_int),
             "cnn_predict": ([p, p, i64, p, p], C.c_int),
             "cnn_fit": ([p, p, p, i64, i32, i32, C.c_float, u64, p, p], C.c_int),
             "lbm_ensemble_attach_score": ([p, p, i32, C.c_float, C.c_float], C.c_int),
@@ -469,6 +471,14 @@ def cnn_shape(m):
     h, w, b = C.c_int32(), C.c_int32(), C.c_int32()
     _check(lib().cnn_shape(m, C.byref(h), C.byref(w), C.byref(b)))
     return h.value, w.value, b.value
+
+
+def cnn_set_conv_path(m, path: int):
+    _check(lib().cnn_set_conv_path(m, int(path)))
+
+
+def cnn_status(m, stream=None):
+    _check(lib().cnn_status(m, _stream(stream)))
 
 
 def cnn_predict(m, x_dev, pred_dev, stream=None):

@@ -41,11 +41,67 @@ def inputs(B, H, W, seed):
     return xt, xt.float().cpu().numpy().astype(np.float64)
 
 
-@pytest.fixture()
-def model(L):
+@pytest.fixture(params=[0, 1], ids=["tcgen05", "mma_sync"])
+def model(L, request):
+    """16 x 32 inputs: the hidden layers run on the tensor-core (tcgen05) path
+    (128-pixel blocks of 4 rows x 32) or on the mma.sync path"""
     m = L.cnn_create(16, 32, 8, 42)
+    L.cnn_set_conv_path(m, request.param)
     yield m
+    L.cnn_status(m)
     L.cnn_destroy(m)
+
+
+@pytest.mark.parametrize("H,W,B", [(8, 32, 3), (16, 64, 2), (8, 256, 2), (32, 16, 1), (8, 128, 3), (64, 256, 2),
+                                   (24, 32, 2), (8, 48, 2), (8, 16, 2)])
+def test_tensor_core_path_matches_mma_sync(L, H, W, B):
+    """The tcgen05 hidden layers against the mma.sync ones on the same model and
+    inputs, for every block geometry (128-pixel blocks of 128/W rows, or of one
+    row of 128 pixels, several per row) and two shapes it does not support
+    (width 48; 8 x 16, whose 128-pixel blocks of 8 rows do not tile the height
+    twice): both runs then take the mma.sync path.  Both accumulate the same BF16 products
+    in FP32 in different orders and round the activations to BF16, so values
+    agree to a few BF16 units in the last place."""
+    xt, _ = inputs(B, H, W, 7)
+    y = torch.tensor(np.linspace(-1, 1, B), dtype=torch.float32, device="cuda")
+    m = L.cnn_create(H, W, B, 3)
+    try:
+        out = []
+        for path in (1, 0):
+            L.cnn_set_conv_path(m, path)
+            pred = torch.zeros(B, dtype=torch.float32, device="cuda")
+            L.cnn_forward(m, xt, pred)
+            loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+            L.cnn_gradient(m, xt, y, loss)
+            L.cnn_status(m)
+            out.append((pred.cpu().numpy().astype(np.float64), L.cnn_get_gradient(m).astype(np.float64)))
+        (p1, g1), (p0, g0) = out
+        assert np.abs(p0 - p1).max() <= 1e-2 * (np.abs(p1).max() + 1e-3), (p0, p1)
+        from oracle import cnn
+        off, _ = cnn.offsets()
+        for l in range(4):
+            sl = slice(off[l], off[l + 1])
+            assert np.linalg.norm(g0[sl] - g1[sl]) <= 2e-2 * np.linalg.norm(g1[sl]), l
+    finally:
+        L.cnn_destroy(m)
+
+
+def test_tensor_core_forward_at_full_size_matches_oracle(L, orc):
+    """64 x 256 inputs (the 4x-downsampled 1024 x 256 channel), the shape the
+    throughput bench runs: one row of 128 pixels per block, two blocks per row."""
+    from oracle import cnn
+    m = L.cnn_create(64, 256, 2, 5)
+    try:
+        xt, x = inputs(2, 64, 256, 9)
+        pred = torch.zeros(2, dtype=torch.float32, device="cuda")
+        L.cnn_forward(m, xt, pred)
+        L.cnn_status(m)
+        p = conv_layers_bf16(L.cnn_get_params(m))
+        ref, _ = cnn.forward(p, x, store=bf16_round)
+        got = pred.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-2 * (np.abs(ref).max() + 1e-3), (got, ref)
+    finally:
+        L.cnn_destroy(m)
 
 
 def test_forward_matches_oracle(L, orc, model):
@@ -151,6 +207,8 @@ def test_cnn_argument_errors(L, model):
     with pytest.raises(TypeError):  # wrong image size is caught before any launch
         L.cnn_forward(model, torch.zeros((2, 8, 32, 8), dtype=torch.bfloat16, device="cuda"),
                       torch.zeros(2, device="cuda"))
+    with pytest.raises(L.LbmError):
+        L.cnn_set_conv_path(model, 2)
     bad = L.cnn_get_params(model)
     bad[5] = np.nan
     with pytest.raises(L.LbmError):
