@@ -58,15 +58,16 @@ SIGMA_DRAG = 1e-3        # drag scale used to set k (k = K_SIGMA / (SIGMA_DRAG *
 BYTES_PER_SITE = 72      # FP32: 9 loads + 9 stores of 4 bytes
 METRIC = "Ensemble D2Q9 GLUPS & HBM-roofline fraction; time-to-return-time vs plain"
 # DRAM traffic of one fused-step launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of 3 launches of the full workload), per site,
+# dram__bytes_write.sum of launches of the full workload), per site,
 # with the kernel sources it was measured on: reported only while they match
 NCU_TRAFFIC = {
     ("gktl", "step_kernel<fp32, vec=4, warps=4>"): {
         "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp32.cu"),
         "sha": "d8352fcdf3e131b9", "bytes_per_site": 68.4740},
     ("precision", "step_rows_kernel<fp16, vec=4, warps=9>"): {
-        "files": ("lbm_step_rows.cuh", "lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp16.cu"),
-        "sha": "b182c50ad811bd2e", "bytes_per_site": 32.5181},
+        "files": ("lbm_step_rows.cuh", "async_copy.cuh", "lbm_step.cuh", "lbm_device.cuh", "step_params.h",
+                  "step_fp16.cu"),
+        "sha": "a812d592ef16a159", "bytes_per_site": 32.6753},
 }
 
 
