@@ -85,6 +85,28 @@ def kernel_label(L, variant: int, storage: str) -> str:
     return f"{name}<{storage}, vec={vec}, warps={warps}>"
 
 
+def max_over_ranks(dist, values, device="cpu"):
+    """Each rank's timings -> their maxima over all ranks (the slowest rank
+    sets the job's time).  dist = None: a single process."""
+    import torch
+    if dist is None:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_glups(sites_per_rank: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the lattice-site updates of all ranks over the
+    job's time (replicas: every rank advances its own ensemble)."""
+    return sites_per_rank * steps * world / seconds / 1e9
+
+
+def replica_seed(rank: int) -> int:
+    """Each rank's ensemble is an independent replica with its own seed."""
+    return 1000 + rank
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -267,7 +289,7 @@ def run_ours(args):
     cfg = L.config(nx, ny, obstacle=w["obst"], tau=TAU, gx=GX, max_steps=PERIOD * total_periods,
                    n_snapshots=N_SNAP, init_amp=0.01, storage=args.storage)
     n_clones = w["clones"]
-    e = L.lbm_ensemble_create(cfg, n_clones, 1000 + rank, stream)
+    e = L.lbm_ensemble_create(cfg, n_clones, replica_seed(rank), stream)
     if args.variant == "auto":
         variant = L.lbm_ensemble_autotune(e)
     else:
@@ -361,14 +383,10 @@ def run_ours(args):
 
     L.lbm_ensemble_destroy(e)
 
-    if dist is not None:
-        tt = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, e2e_s = tt.tolist()
+    ms, e2e_s = max_over_ranks(dist, [ms, e2e_s], device="cuda")
     sites = n_clones * nx * ny
-    updates = sites * PERIOD * args.steps * world
-    value = updates / (ms / 1e3) / 1e9
-    e2e_value = sites * PERIOD * e2e_steps * world / e2e_s / 1e9
+    value = job_glups(sites, PERIOD * args.steps, world, ms / 1e3)
+    e2e_value = job_glups(sites, PERIOD * e2e_steps, world, e2e_s)
     hbm, peak_kind = peaks()
     avg_launch_ms = st_ms / max(st_launches, 1)
     bytes_per_site = BYTES_PER_SITE if args.storage == "fp32" else BYTES_PER_SITE // 2
