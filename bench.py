@@ -755,6 +755,74 @@ def run_ams_branch(args):
         "gpu_launches": launches}))
 
 
+def run_ams_run(args):
+    """A whole AMS run (App. B.1) on the AMS workload: N trajectories of
+    512x128 stepped to T_a, then kill-and-branch iterations (each restores the
+    survivor's checkpoint, replays to the branching time, perturbs with the
+    App. D bank refilled from that checkpoint and steps the copy to T_a).  The
+    score is the instantaneous drag (--ams-window 1, the paper's Sec. 4.1
+    workload) or its trailing mean.  One bench step = one run on a fresh
+    ensemble; reported: milliseconds per run, with the initial ensemble timed
+    on its own."""
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = workload(argparse.Namespace(workload="ams", clones=args.clones))
+    n, t_a, J, stride = w["clones"], 2000, 40, 250
+    window = args.ams_window
+    stream = torch.cuda.current_stream()
+    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], tau=TAU, gx=GX, storage=L.STORAGE[args.storage],
+                   max_steps=t_a, ckpt_stride=stride, n_snapshots=N_SNAP)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    runs, inits, iters, launches = [], [], [], 0
+    for step in range(args.warmup + args.steps):
+        e = L.lbm_ensemble_create(cfg, n, 2000 + step, stream)
+        try:
+            L.lbm_ensemble_set_snapshots(e, [i * n // N_SNAP for i in range(N_SNAP)])
+            Q = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            l0 = L.lbm_launch_count()
+            ev[0].record(stream)
+            it, lw, levels = L.lbm_ams_run(e, t_a, window, J, float("inf"), EPS, 7 + step, Q,
+                                           refresh_snapshots=True)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            l1 = L.lbm_launch_count()
+        finally:
+            L.lbm_ensemble_destroy(e)
+        e = L.lbm_ensemble_create(cfg, n, 2000 + step, stream)  # the initial ensemble alone
+        try:
+            torch.cuda.synchronize()
+            ev[2].record(stream)
+            L.lbm_ensemble_step(e, t_a)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+        finally:
+            L.lbm_ensemble_destroy(e)
+        if step >= args.warmup:
+            runs.append(ev[0].elapsed_time(ev[1]))
+            inits.append(ev[2].elapsed_time(ev[3]))
+            iters.append(it)
+            launches += l1 - l0
+    ms = statistics.median(runs)
+    init_ms = statistics.median(inits)
+    it_med = statistics.median(iters)
+    score = "instantaneous drag" if window == 1 else f"{window}-step time-averaged drag"
+    print(json.dumps({
+        "metric": "AMS run time (initial ensemble + kill/branch iterations)", "value": ms, "unit": "ms per run",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"AMS: N={n} trajectories of {w['nx']}x{w['ny']} ({args.storage}), T_a={t_a}, "
+                               f"up to {J} iterations, score = {score}, checkpoints every {stride} steps, "
+                               f"App. D bank of {N_SNAP} refilled at each branch",
+                   "storage": args.storage, "score_window": window},
+        "initial_ensemble": {"ms": init_ms, "glups": n * w["nx"] * w["ny"] * t_a / (init_ms / 1e3) / 1e9},
+        "branch_phase": {"iterations": it_med, "ms_per_iteration": (ms - init_ms) / max(it_med, 1)},
+        "gpu_launches": launches // max(len(runs), 1)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -766,8 +834,10 @@ def main():
                     help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch"])
+    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--ams-window", type=int, default=1,
+                    help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -779,6 +849,8 @@ def main():
         run_precision_report(args)
     elif args.workload == "ams-branch":
         run_ams_branch(args)
+    elif args.workload == "ams-run":
+        run_ams_run(args)
     else:
         run_ours(args)
 

@@ -166,7 +166,11 @@ int lbm_ensemble_set_populations(lbm_ensemble* e, int32_t clone, const double* h
  * per block) for this ensemble by timing each on its own state; the state and
  * the drag history are left unchanged.  *variant (may be NULL) gets the index. */
 int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant);
-/* Force a variant by index (-1 restores the default); describe any index. */
+/* Force a variant by index for every step call (-1 restores the defaults);
+ * describe any index.  Without a forced variant, step calls over at most 2^18
+ * sites (clones x nx x ny, e.g. one AMS branch) use a separate small-list
+ * variant (default: the narrowest register-staged variant with 8 warps, which
+ * puts the most threads on a small grid); lbm_ensemble_autotune picks both. */
 int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant);
 int lbm_step_variant_info(int32_t variant, int32_t* storage, int32_t* vec, int32_t* warps);
 int32_t lbm_step_variant_count(void);

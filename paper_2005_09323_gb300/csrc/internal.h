@@ -98,8 +98,10 @@ struct lbm_ensemble {
     double* cnn_score;        // [N][n_ckpt] score at every checkpoint (NaN until evaluated)
     double* pot[3];           // GKTL potential: now, previous, start (per slot)
     double* pot_tmp[2];
-    // selected step variant (index into step_variants())
+    // selected step variants (indices into step_variants()): one for step
+    // calls over many sites, one for calls below kSmallSites (an AMS branch)
     int variant;
+    int variant_small;
     // step chunks captured once as CUDA graphs and replayed: one cached
     // executable per (variant, clone list, list length, chunk length)
     struct StepGraph {

@@ -50,6 +50,9 @@ const std::vector<StepVariant>& step_variants()
 
 constexpr int kBatchCap = 512;     // steps per drag-finalisation batch
 constexpr int kGraphCache = 24;    // cached step-chunk graphs per ensemble
+// step calls over at most this many sites (n clones x nx x ny) use the
+// small-list variant: one wave of the wide variants would leave most SMs idle
+constexpr int64_t kSmallSites = int64_t(1) << 18;
 constexpr int kRedBlocks = 152;    // blocks of a per-clone reduction (one wave)
 constexpr int kRedThreads = 256;
 
@@ -391,6 +394,23 @@ int default_variant(int storage)
     return -1;
 }
 
+// narrowest register-staged variant with 8 warps per block: the most threads
+// for a small step call (measured fastest for one 512 x 128 clone)
+int default_variant_small(int storage)
+{
+    const auto& v = step_variants();
+    int best = -1;
+    for (size_t i = 0; i < v.size(); ++i)
+        if (v[i].storage == storage && v[i].kind == 0 && v[i].warps == 8 && (best < 0 || v[i].vec < v[best].vec))
+            best = (int)i;
+    return best >= 0 ? best : default_variant(storage);
+}
+
+int variant_for(const lbm_ensemble* e, int n_list)
+{
+    return (int64_t)n_list * e->cfg.nx * e->cfg.ny <= kSmallSites ? e->variant_small : e->variant;
+}
+
 StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_list, int vec, int step, int kind = 0)
 {
     const lbm_config& c = e->cfg;
@@ -466,9 +486,9 @@ int solid_bounds(const lbm_config& c, int& ox0, int& ox1, int& oy0, int& oy1)
 // index is fixed for the life of the ensemble, and the clone list is read
 // through its device pointer at run time, so a replay is the same work as the
 // launches it was captured from.
-int launch_chunk(lbm_ensemble* e, const int32_t* list_dev, int n_list, int chunk)
+int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, int chunk)
 {
-    const StepVariant& v = step_variants()[e->variant];
+    const StepVariant& v = step_variants()[vi];
     if (!e->use_graphs) {
         for (int s = 0; s < chunk; ++s) {
             cudaError_t err = v.launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
@@ -479,7 +499,7 @@ int launch_chunk(lbm_ensemble* e, const int32_t* list_dev, int n_list, int chunk
     }
     lbm_ensemble::StepGraph* hit = nullptr;
     for (auto& g : e->graphs)
-        if (g.variant == e->variant && g.list == list_dev && g.n_list == n_list && g.chunk == chunk) hit = &g;
+        if (g.variant == vi && g.list == list_dev && g.n_list == n_list && g.chunk == chunk) hit = &g;
     if (!hit) {
         if (!e->cap_stream) LBM_CUDA(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
         LBM_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed));
@@ -503,7 +523,7 @@ int launch_chunk(lbm_ensemble* e, const int32_t* list_dev, int n_list, int chunk
             cudaGraphExecDestroy(lru->exec);
             e->graphs.erase(lru);
         }
-        e->graphs.push_back({e->variant, list_dev, n_list, chunk, exec, 0});
+        e->graphs.push_back({vi, list_dev, n_list, chunk, exec, 0});
         hit = &e->graphs.back();
     }
     hit->used = ++e->graph_clock;
@@ -517,8 +537,9 @@ int launch_chunk(lbm_ensemble* e, const int32_t* list_dev, int n_list, int chunk
 int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_t>& list, int32_t n_steps)
 {
     const auto& vars = step_variants();
-    const StepVariant& v = vars[e->variant];
     const int n_list = (int)list.size();
+    const int vi = variant_for(e, n_list);
+    const StepVariant& v = vars[vi];
     const Ring r = ring_for(e->cfg, v.kind == 1 ? 0 : v.vec);
     int32_t t = e->t_host[list[0]];
     int32_t left = n_steps;
@@ -534,7 +555,7 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
             LBM_CUDA(cudaEventCreate(&ev1));
             LBM_CUDA(cudaEventRecord(ev0, e->stream));
         }
-        if (int rc = launch_chunk(e, list_dev, n_list, chunk)) return rc;
+        if (int rc = launch_chunk(e, vi, list_dev, n_list, chunk)) return rc;
         if (e->timing) {
             LBM_CUDA(cudaEventRecord(ev1, e->stream));
             e->events.emplace_back(ev0, ev1);
@@ -693,6 +714,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     e->scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : c.shift_exp);
     e->inv_scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : -c.shift_exp);
     e->variant = default_variant(c.storage);
+    e->variant_small = default_variant_small(c.storage);
     e->use_graphs = true;
     e->batch_cap = kBatchCap;
     e->red_blocks = kRedBlocks;
@@ -978,9 +1000,6 @@ int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, 
                                  bytes, cudaMemcpyDeviceToDevice, e->stream));
     LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(e->buf[e->parity_host[dst]]) + (size_t)dst * bytes,
                              ck + ((size_t)src * e->n_ckpt + kc) * bytes, bytes, cudaMemcpyDeviceToDevice, e->stream));
-    if (t_b > 0)
-        LBM_CUDA(cudaMemcpyAsync(e->drag + (size_t)dst * e->cfg.max_steps, e->drag + (size_t)src * e->cfg.max_steps,
-                                 sizeof(double) * t_b, cudaMemcpyDeviceToDevice, e->stream));
     if (e->cnn_score)  // the learned score of the shared checkpoints
         LBM_CUDA(cudaMemcpyAsync(e->cnn_score + (size_t)dst * e->n_ckpt, e->cnn_score + (size_t)src * e->n_ckpt,
                                  sizeof(double) * (kc + 1), cudaMemcpyDeviceToDevice, e->stream));
@@ -992,6 +1011,12 @@ int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, 
         int rc = lbm_ensemble_step_clones(e, t_b - tc, &dst, 1);
         if (rc) return rc;
     }
+    // the drag history up to t_b is the source's own, copied after the replay:
+    // the replay may run another step variant, whose per-warp drag partials
+    // are summed in another grouping (the populations are identical bit for bit)
+    if (t_b > 0)
+        LBM_CUDA(cudaMemcpyAsync(e->drag + (size_t)dst * e->cfg.max_steps, e->drag + (size_t)src * e->cfg.max_steps,
+                                 sizeof(double) * t_b, cudaMemcpyDeviceToDevice, e->stream));
     if (eps != 0.0) {
         LBM_CUDA(cudaMemcpyAsync(e->list_dev, &dst, sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
         int rc = compute_masses(e, e->list_dev, 1);
@@ -1078,12 +1103,14 @@ int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant)
     if (!e) return fail(LBM_ERR_ARG, "null ensemble");
     if (variant == -1) {
         e->variant = default_variant(e->cfg.storage);
+        e->variant_small = default_variant_small(e->cfg.storage);
         return LBM_OK;
     }
     const auto& v = step_variants();
     if (variant < 0 || variant >= (int32_t)v.size()) return fail(LBM_ERR_ARG, "variant index out of range");
     if (v[variant].storage != e->cfg.storage) return fail(LBM_ERR_ARG, "variant is for another storage format");
-    e->variant = variant;
+    e->variant = variant;  // a forced variant runs every step call
+    e->variant_small = variant;
     return LBM_OK;
 }
 
@@ -1091,37 +1118,45 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
 {
     if (!e) return fail(LBM_ERR_ARG, "null ensemble");
     const auto& vars = step_variants();
-    std::vector<int32_t> all(e->n);
     cudaEvent_t a, b;
     LBM_CUDA(cudaEventCreate(&a));
     LBM_CUDA(cudaEventCreate(&b));
-    float best_ms = std::numeric_limits<float>::infinity();
-    int best = e->variant;
     // Every trial launch reads the current buffer and rewrites the other one
     // at step_in_batch 0: the state does not advance and no drag is recorded.
-    for (size_t i = 0; i < vars.size(); ++i) {
-        const StepVariant& v = vars[i];
-        if (v.storage != e->cfg.storage) continue;
-        StepParams p = make_params(e, e->all_dev, e->n, v.vec, 0, v.kind);
-        if (v.supports && !v.supports(p)) continue;
-        const int reps = 5;
-        for (int r = 0; r < 2; ++r) LBM_CUDA(v.launch(p, e->stream));
-        LBM_CUDA(cudaEventRecord(a, e->stream));
-        for (int r = 0; r < reps; ++r) LBM_CUDA(v.launch(p, e->stream));
-        count_launches(2 + reps);
-        LBM_CUDA(cudaEventRecord(b, e->stream));
-        LBM_CUDA(cudaEventSynchronize(b));
-        float ms = 0.f;
-        LBM_CUDA(cudaEventElapsedTime(&ms, a, b));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = (int)i;
+    auto tune = [&](int n_list, int reps, int best) -> int {
+        float best_ms = std::numeric_limits<float>::infinity();
+        for (size_t i = 0; i < vars.size(); ++i) {
+            const StepVariant& v = vars[i];
+            if (v.storage != e->cfg.storage) continue;
+            StepParams p = make_params(e, e->all_dev, n_list, v.vec, 0, v.kind);
+            if (v.supports && !v.supports(p)) continue;
+            for (int r = 0; r < 2; ++r)
+                if (v.launch(p, e->stream) != cudaSuccess) return -1;
+            cudaEventRecord(a, e->stream);
+            for (int r = 0; r < reps; ++r)
+                if (v.launch(p, e->stream) != cudaSuccess) return -1;
+            count_launches(2 + reps);
+            cudaEventRecord(b, e->stream);
+            if (cudaEventSynchronize(b) != cudaSuccess) return -1;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = (int)i;
+            }
         }
-    }
+        return best;
+    };
+    // the wide variant on the whole ensemble; the small-list one on a single
+    // clone (one AMS branch), with more launches since each is short
+    const int wide = tune(e->n, 5, e->variant);
+    const int small = wide < 0 ? -1 : tune(1, 40, e->variant_small);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    e->variant = best;
-    if (variant) *variant = best;
+    if (wide < 0 || small < 0) return cuda_fail(cudaGetLastError(), "lbm_ensemble_autotune trial launch");
+    e->variant = wide;
+    e->variant_small = small;
+    if (variant) *variant = wide;
     return LBM_OK;
 }
 

@@ -108,11 +108,14 @@ def test_every_variant_on_ragged_grid(L, orc):
     assert tried >= 3
 
 
-@pytest.mark.parametrize("storage", ["fp16", "bf16"])
-def test_every_16bit_variant_agrees(L, storage):
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_every_variant_agrees_bitwise(L, storage):
     """All compiled variants of one storage format (register-staged row
-    segments, bulk-copy-staged whole rows) compute the same populations bit for
-    bit; the drag differs only by the grouping of its partial sums."""
+    segments of every width, bulk-copy-staged whole rows) compute the same
+    populations bit for bit (one collision routine, the same loads); the drag
+    differs only by the grouping of its partial sums.  Small step calls (an AMS
+    branch) may run another variant than the ensemble, so this is what makes a
+    branch replay the source's path exactly."""
     kw = dict(RAGGED, max_steps=50, storage=storage)
     ref = None
     n_var = L.lbm_step_variant_count()
@@ -326,6 +329,24 @@ def test_branch_replays_bitwise(L):
         d = e.drag(0, 120)
         assert np.array_equal(d[1, :50], d[2, :50])
         assert not np.array_equal(d[1, 50:], d[2, 50:])
+
+
+def test_branch_replays_across_step_variants(L):
+    """An ensemble large enough to step with the wide variant, a branch that
+    replays one clone (a small step call, another variant): the replayed
+    state is the source's bit for bit, the drag history up to the branch time
+    is the source's exactly, and later drag values agree to FP32 rounding
+    (their per-warp FP32 partials are grouped differently)."""
+    kw = dict(nx=1024, ny=128, obstacle=(250, 56, 16, 16), tau=0.6, gx=2e-5, max_steps=120, ckpt_stride=25)
+    with Ens(L, 3, seed=9, **kw) as e:
+        L.lbm_ensemble_step(e.h, 80)
+        L.lbm_ensemble_branch(e.h, 1, 2, 63, 0.0, 3, 1)
+        L.lbm_ensemble_step_clones(e.h, 17, [1])
+        assert np.array_equal(e.pops(1), e.pops(2))
+        d = e.drag(0, 80)
+        assert np.array_equal(d[1, :63], d[2, :63])
+        # FP32 per-warp partials summed in another grouping: FP32 rounding
+        assert np.abs(d[1, 63:] - d[2, 63:]).max() <= 1e-5 * np.abs(d[2]).max()
 
 
 def test_nonfinite_state_is_reported(L):

@@ -135,6 +135,35 @@ def test_ams_run_invariants(L, orc):
         L.lbm_ensemble_destroy(e)
 
 
+def test_ams_on_the_instantaneous_drag(L, orc):
+    """AMS with the instantaneous drag as the score (window = 1: the trailing
+    mean of one step is D(t) itself), the second AMS workload of the paper
+    (Sec. 4.1): the levels rise, every final maximum is the maximum of the
+    trajectory's drag series, the estimator weight is the product of the
+    survival fractions, and the branched histories replay bitwise."""
+    n, t_a, J = 8, 200, 10
+    runs = []
+    for _ in range(2):
+        e, cfg = make(L, n, 31, max_steps=t_a, ckpt_stride=25, n_snapshots=2)
+        try:
+            L.lbm_ensemble_set_snapshots(e, [0, 1])
+            Q = zeros(n)
+            it, lw, levels, kills = L.lbm_ams_run(e, t_a, 1, J, float("inf"), 0.002, 17, Q, with_kills=True)
+            d = np.zeros((n, t_a))
+            L.lbm_ensemble_drag(e, 0, t_a, d)
+            runs.append((it, lw, levels, kills, Q.cpu().numpy(), d))
+        finally:
+            L.lbm_ensemble_destroy(e)
+    it, lw, levels, kills, q, d = runs[0]
+    assert 1 <= it <= J and np.all(np.diff(levels) > 0)
+    assert np.array_equal(q, d.max(axis=1))  # window 1: the score is D(t)
+    assert np.array_equal(q, orc.trailing_mean_max(d, 1, t_a))
+    assert np.all(q > levels[-1]) or np.all(q == q[0])
+    assert abs(lw - sum(np.log1p(-k / n) for k in kills)) < 1e-13
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
 def test_ams_run_is_deterministic_and_stops_at_level(L):
     n, t_a, window = 6, 120, 20
     runs = []
