@@ -58,6 +58,7 @@ def lib():
         L.orc_moments.argtypes = [p, p, p, p, p]
         L.orc_macro.argtypes = [p, p, p, p, p]
         L.orc_is_solid.argtypes = [p, C.c_int, C.c_int]; L.orc_is_solid.restype = C.c_int
+        L.orc_cm_collide.argtypes = [p, d, d, p, p, p, p]
         L.orc_perturb_alphas.argtypes = [u64, u64, i32, i32, p]
         L.orc_perturb.argtypes = [p, p, i32, p, p, d, p]
         L.orc_gktl_weights.argtypes = [i32, p, p, p]; L.orc_gktl_weights.restype = C.c_int
@@ -79,12 +80,16 @@ class Cfg(C.Structure):
     """Mirror of ``orc_cfg``: channel nx x ny, solid cells [ox0,ox0+ow) x [oy0,oy0+oh)."""
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ox0", C.c_int32), ("oy0", C.c_int32),
                 ("ow", C.c_int32), ("oh", C.c_int32), ("tau", C.c_double), ("gx", C.c_double),
-                ("gy", C.c_double)]
+                ("gy", C.c_double), ("collision", C.c_int32), ("omega_bulk", C.c_double),
+                ("omega_3", C.c_double), ("omega_4", C.c_double)]
 
 
-def cfg(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0) -> Cfg:
+def cfg(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, collision=0, omega_bulk=1.0, omega_3=1.0,
+        omega_4=1.0) -> Cfg:
+    """collision 0: BGK; 1: central-moment MRT (shear at 1/tau, the other
+    rates as given)"""
     ox0, oy0, ow, oh = obstacle
-    return Cfg(nx, ny, ox0, oy0, ow, oh, tau, gx, gy)
+    return Cfg(nx, ny, ox0, oy0, ow, oh, tau, gx, gy, collision, omega_bulk, omega_3, omega_4)
 
 
 # ---------------------------------------------------------------- rng
@@ -114,6 +119,17 @@ def feq(rho, ux, uy):
 def guo(ux, uy, gx, gy):
     o = np.zeros(9)
     lib().orc_guo(ux, uy, gx, gy, _ptr(o))
+    return o
+
+
+def cm_collide(f, ux, uy, feq9, S9, rates):
+    """central-moment collision of one node (orc_cm_collide)"""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    a = np.ascontiguousarray(feq9, dtype=np.float64)
+    b = np.ascontiguousarray(S9, dtype=np.float64)
+    r = np.ascontiguousarray(rates, dtype=np.float64)
+    o = np.zeros(9)
+    lib().orc_cm_collide(_ptr(f), ux, uy, _ptr(a), _ptr(b), _ptr(r), _ptr(o))
     return o
 
 

@@ -125,6 +125,94 @@ static void link_forces(const orc_cfg* c, const double* f, double* fo, double* f
     if (fw) { fw[0] = wx; fw[1] = wy; }
 }
 
+/* Central-moment collision with multiple relaxation times.  The paper's
+ * production runs replace the BGK collision by a multi-relaxation-time
+ * collision on central moments (App. A, after De Rosis 2016).  Written here
+ * as the generalisation of the BGK collision above:
+ *   central moments       k_pq = sum_i (c_ix - u_x)^p (c_iy - u_y)^q f_i,
+ *                         i.e. k = T f for the nine D2Q9 moments
+ *                         pq = 00 10 01 20 02 11 21 12 22;
+ *   discrete equilibrium  k^eq = T f^eq (the same second-order f^eq);
+ *   forcing               the Guo term S enters as in BGK, with (I - Omega/2)
+ *                         on its moments;
+ *   collision             f* = f - T^{-1} Omega T (f - f^eq) + T^{-1} (I - Omega/2) T S
+ *                            = f + S - T^{-1} Omega T (f - f^eq + S/2).
+ * Omega relaxes the shear moments (k20 - k02 and k11) at 1/tau, the bulk
+ * moment k20 + k02, the third-order k21, k12 and the fourth-order k22 at
+ * their own rates; Omega = omega I is the BGK collision with Guo forcing.  T
+ * is built and inverted numerically (Gauss-Jordan) at every node.            */
+static const int MP[9] = {0, 1, 0, 2, 0, 1, 2, 1, 2};
+static const int MQ[9] = {0, 0, 1, 0, 2, 1, 1, 2, 2};
+
+static double ipow(double b, int e)
+{
+    double r = 1.0;
+    for (int k = 0; k < e; ++k) r *= b;
+    return r;
+}
+
+/* inverse of a 9 x 9 matrix by Gauss-Jordan elimination with partial pivoting */
+static void invert9(const double a_in[9][9], double inv[9][9])
+{
+    double a[9][18];
+    for (int r = 0; r < 9; ++r)
+        for (int j = 0; j < 18; ++j) a[r][j] = j < 9 ? a_in[r][j] : (j - 9 == r ? 1.0 : 0.0);
+    for (int col = 0; col < 9; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 9; ++r)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (piv != col)
+            for (int j = 0; j < 18; ++j) {
+                double t = a[col][j];
+                a[col][j] = a[piv][j];
+                a[piv][j] = t;
+            }
+        double d = a[col][col];
+        for (int j = 0; j < 18; ++j) a[col][j] /= d;
+        for (int r = 0; r < 9; ++r) {
+            if (r == col) continue;
+            double m = a[r][col];
+            if (m != 0.0)
+                for (int j = 0; j < 18; ++j) a[r][j] -= m * a[col][j];
+        }
+    }
+    for (int r = 0; r < 9; ++r)
+        for (int j = 0; j < 9; ++j) inv[r][j] = a[r][j + 9];
+}
+
+void orc_cm_collide(const double f[9], double ux, double uy, const double feq[9], const double S[9],
+                    const double rates[4], double out[9])
+{
+    double T[9][9], Ti[9][9], Om[9][9];
+    for (int r = 0; r < 9; ++r)
+        for (int i = 0; i < 9; ++i) T[r][i] = ipow(CX[i] - ux, MP[r]) * ipow(CY[i] - uy, MQ[r]);
+    invert9(T, Ti);
+    for (int r = 0; r < 9; ++r)
+        for (int j = 0; j < 9; ++j) Om[r][j] = 0.0;
+    const double ws = rates[0], wb = rates[1], w3 = rates[2], w4 = rates[3];
+    Om[0][0] = Om[1][1] = Om[2][2] = 1.0;  /* conserved: their moments of d are zero */
+    Om[3][3] = Om[4][4] = 0.5 * (wb + ws);  /* k20, k02: bulk sum at wb, difference at ws */
+    Om[3][4] = Om[4][3] = 0.5 * (wb - ws);
+    Om[5][5] = ws;                          /* k11 */
+    Om[6][6] = Om[7][7] = w3;               /* k21, k12 */
+    Om[8][8] = w4;                          /* k22 */
+    double d[9], k[9], rk[9];
+    for (int i = 0; i < 9; ++i) d[i] = f[i] - feq[i] + 0.5 * S[i];
+    for (int r = 0; r < 9; ++r) {
+        k[r] = 0.0;
+        for (int i = 0; i < 9; ++i) k[r] += T[r][i] * d[i];
+    }
+    for (int r = 0; r < 9; ++r) {
+        rk[r] = 0.0;
+        for (int j = 0; j < 9; ++j) rk[r] += Om[r][j] * k[j];
+    }
+    for (int i = 0; i < 9; ++i) {
+        double x = 0.0;
+        for (int r = 0; r < 9; ++r) x += Ti[i][r] * rk[r];
+        out[i] = f[i] + S[i] - x;
+    }
+}
+
 void orc_step(const orc_cfg* c, const double* fin, double* fout, double* force_obs, double* force_wall)
 {
     const int nx = c->nx, ny = c->ny;
@@ -162,8 +250,15 @@ void orc_step(const orc_cfg* c, const double* fin, double* fout, double* force_o
             double feq[9], S[9];
             orc_feq(rho, ux, uy, feq);
             orc_guo(ux, uy, c->gx, c->gy, S);
-            for (int i = 0; i < 9; ++i)
-                fout[IDX(c, i, x, y)] = f[i] - (f[i] - feq[i]) / c->tau + (1.0 - 1.0 / (2.0 * c->tau)) * S[i];
+            if (c->collision == 1) {
+                const double rates[4] = {1.0 / c->tau, c->omega_bulk, c->omega_3, c->omega_4};
+                double out[9];
+                orc_cm_collide(f, ux, uy, feq, S, rates, out);
+                for (int i = 0; i < 9; ++i) fout[IDX(c, i, x, y)] = out[i];
+            } else {
+                for (int i = 0; i < 9; ++i)
+                    fout[IDX(c, i, x, y)] = f[i] - (f[i] - feq[i]) / c->tau + (1.0 - 1.0 / (2.0 * c->tau)) * S[i];
+            }
         }
     /* 3. momentum exchanged with the obstacle and the walls by the links that
      *    the next streaming step bounces back */

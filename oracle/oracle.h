@@ -16,6 +16,9 @@
  *   orc_feq / orc_guo       closed-form moments (App. A)
  *   orc_lbm_step            rest-state invariance, mass conservation,
  *                           momentum balance (pins the drag), Poiseuille
+ *   orc_cm_collide          equal rates = BGK; every central moment relaxes
+ *                           at its own rate (numpy sums); mass and momentum
+ *                           balance; shear-wave decay at nu = (tau - 1/2)/3
  *   orc_perturb             exact mass preservation; eps = 0 gives a copy
  *   orc_gktl_weights/select sum of weights = N, k = 0 identity, brute-force
  *                           mean copy counts; OU closed-form SCGF (App. C)
@@ -45,6 +48,10 @@ typedef struct {
     int32_t ox0, oy0, ow, oh;       /* solid cells [ox0,ox0+ow) x [oy0,oy0+oh); ow=0: no obstacle */
     double tau;                     /* BGK relaxation time, nu = (tau - 1/2)/3 */
     double gx, gy;                  /* constant body-force density on fluid nodes */
+    int32_t collision;              /* 0: BGK; 1: central-moment multiple relaxation times */
+    double omega_bulk, omega_3, omega_4;  /* collision 1: rates of the bulk (k20 + k02), third-
+                                       order (k21, k12) and fourth-order (k22) central moments;
+                                       shear (k20 - k02, k11) relaxes at 1/tau */
 } orc_cfg;
 
 int orc_is_solid(const orc_cfg* c, int x, int y);
@@ -52,6 +59,14 @@ int orc_is_solid(const orc_cfg* c, int x, int y);
 void orc_feq(double rho, double ux, double uy, double feq[9]);
 /* Guo forcing term S_q for velocity u and force density (gx, gy) */
 void orc_guo(double ux, double uy, double gx, double gy, double S[9]);
+/* central-moment collision of one node (App. A's production collision):
+ *   out = f + S - T^{-1} Omega T (f - feq + S/2),
+ * T_{pq,i} = (c_ix - ux)^p (c_iy - uy)^q, pq = 00 10 01 20 02 11 21 12 22;
+ * Omega relaxes k20 - k02 and k11 at rates[0], k20 + k02 at rates[1], k21 and
+ * k12 at rates[2], k22 at rates[3] (the conserved moments are unaffected).
+ * rates all equal to omega give the BGK collision with Guo forcing.            */
+void orc_cm_collide(const double f[9], double ux, double uy, const double feq[9], const double S[9],
+                    const double rates[4], double out[9]);
 /* equilibrium start with rho = 1 and a seeded uniform velocity perturbation of
  * amplitude amp on fluid nodes; solid nodes hold the rest weights w_q. */
 void orc_init(const orc_cfg* c, uint64_t seed, int32_t clone, double amp, double* f);
