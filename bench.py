@@ -51,6 +51,7 @@ def workload(args):
     w["clones"] = args.clones or w["clones"]
     nx, ny, side = w["nx"], w["ny"], w["side"]
     w["obst"] = (nx // 4 - side // 2, ny // 2 - side // 2, side, side)
+    w["collision"] = getattr(args, "collision", "bgk")
     return w
 EPS, N_SNAP = 0.002, 10
 K_SIGMA = 1.0
@@ -170,10 +171,10 @@ class Clocks:
 
 # ---------------------------------------------------------------- CPU oracle
 def _oracle_worker(args):
-    steps, seed, barrier, nx, ny, obst = args
+    steps, seed, barrier, nx, ny, obst, collision = args
     sys.path.insert(0, ROOT)
     import oracle
-    c = oracle.cfg(nx, ny, obstacle=obst, tau=TAU, gx=GX)
+    c = oracle.cfg(nx, ny, obstacle=obst, tau=TAU, gx=GX, collision=1 if collision == "cm" else 0)
     f = oracle.init(c, seed, 0, 0.01)
     if barrier is not None:
         barrier.wait()
@@ -188,7 +189,7 @@ def oracle_rate(steps_per_proc: int, procs: int, w):
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
-    geo = (w["nx"], w["ny"], w["obst"])
+    geo = (w["nx"], w["ny"], w["obst"], w.get("collision", "bgk"))
     if procs == 1:
         dt = _oracle_worker((steps_per_proc, 0, None) + geo)
         times = [dt]
@@ -247,6 +248,9 @@ def workload_config(args):
            "parallelism": f"replicas x{args.gpus}"}
     if w["cloning"]:
         cfg.update({"k_sigma": K_SIGMA, "eps": EPS, "n_snapshots": N_SNAP})
+    if args.collision == "cm":
+        cfg["workload"] += ", central-moment collision (shear 1/tau, bulk/3rd/4th-order rates 1)"
+        cfg["collision"] = "central moments"
     return cfg
 
 
@@ -287,7 +291,7 @@ def run_ours(args):
     total_periods = args.warmup + args.steps + 2 * (args.warmup + args.steps) + 2
     nx, ny = w["nx"], w["ny"]
     cfg = L.config(nx, ny, obstacle=w["obst"], tau=TAU, gx=GX, max_steps=PERIOD * total_periods,
-                   n_snapshots=N_SNAP, init_amp=0.01, storage=args.storage)
+                   n_snapshots=N_SNAP, init_amp=0.01, storage=args.storage, collision=args.collision)
     n_clones = w["clones"]
     e = L.lbm_ensemble_create(cfg, n_clones, replica_seed(rank), stream)
     if args.variant == "auto":
@@ -836,6 +840,8 @@ def main():
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
     ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--collision", default="bgk", choices=["bgk", "cm"],
+                    help="gktl/precision/ams workloads: BGK or the central-moment collision")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()

@@ -59,6 +59,16 @@ typedef struct {
     int32_t ckpt_stride;       /* AMS: keep the state every ckpt_stride steps; 0 = none */
     int32_t n_snapshots;       /* capacity of the App. D snapshot bank (N_s) */
     double init_amp;           /* initial velocity perturbation amplitude */
+    /* collision (App. A): 0 = BGK with Guo forcing; 1 = central moments with
+     * multiple relaxation times, the production collision the paper names:
+     *   f* = f + S - T^{-1} Omega T (f - f^eq + S/2),
+     * T(u) the D2Q9 central-moment transform, f^eq the same discrete
+     * equilibrium, S the Guo term; Omega relaxes k20 - k02 and k11 at 1/tau
+     * (the viscosity), k20 + k02 at omega_bulk, k21 and k12 at omega_3, k22 at
+     * omega_4 (each in (0, 2)); all rates 1/tau is BGK.  Zero-initialised
+     * configurations are BGK. */
+    int32_t collision;
+    double omega_bulk, omega_3, omega_4;
 } lbm_config;
 
 typedef struct lbm_ensemble lbm_ensemble;

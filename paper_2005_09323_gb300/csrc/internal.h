@@ -32,6 +32,9 @@ struct StepVariant {
     bool (*supports)(const StepParams&);  // null: every shape
 };
 
+// LBM_ERR_ARG unless the collision fields of c are valid (lbm_ensemble.cu)
+int check_collision(const lbm_config& c);
+
 // all compiled variants of the fused step (lbm_step.cu)
 const std::vector<StepVariant>& step_variants();
 

@@ -366,6 +366,21 @@ struct Ring {
     int ry0, ry1, rs0, rs1, n_slots;
 };
 
+}  // namespace
+
+int lbm::check_collision(const lbm_config& c)
+{
+    if (c.collision != 0 && c.collision != 1) return fail(LBM_ERR_ARG, "collision must be 0 (BGK) or 1 (central moments)");
+    if (c.collision == 1) {
+        const double r[3] = {c.omega_bulk, c.omega_3, c.omega_4};
+        for (double w : r)
+            if (!(w > 0.0 && w < 2.0)) return fail(LBM_ERR_ARG, "central-moment rates must lie in (0, 2)");
+    }
+    return LBM_OK;
+}
+
+namespace {
+
 // vec = 0: row-staged kernels, one slot per consumer warp in each ring row
 Ring ring_for(const lbm_config& c, int vec)
 {
@@ -443,6 +458,8 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
     p.gx = (float)c.gx;
     p.gy = (float)c.gy;
     p.bgk = bgk_consts(p.omega, p.gx, p.gy);
+    p.coll = c.collision;
+    p.cm = cm_consts(p.omega, (float)c.omega_bulk, (float)c.omega_3, (float)c.omega_4, p.gx, p.gy);
     p.scale = e->scale;
     p.inv_scale = e->inv_scale;
     p.step_in_batch = step;
@@ -699,6 +716,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
             return fail(LBM_ERR_ARG, "obstacle must leave a fluid column on both sides in x");
         if (c.obs_y0 < 0 || c.obs_y0 + c.obs_h > c.ny) return fail(LBM_ERR_ARG, "obstacle outside the channel");
     }
+    if (int rc = check_collision(c)) return rc;
     int dev = 0;
     LBM_CUDA(cudaGetDevice(&dev));
     auto* e = new lbm_ensemble();

@@ -28,6 +28,7 @@
 // any boundary test; the few warps on the walls and around the obstacle take
 // the general path, which also produces the drag partial of the warp.
 #pragma once
+#include <type_traits>
 #include "internal.h"
 #include "lbm_device.cuh"
 
@@ -89,7 +90,72 @@ __device__ __forceinline__ void bgk_collide(float (&g)[9][V], int j, const BgkCo
     bgk_pair(g[6][j], g[8][j], uy - ux, k.A[3], k.B[3], wf(6), P, Qc, a0, k.omm);
 }
 
-template <int S, int V, bool GENERAL, bool SCALED>
+// central-moment collision of site j, in place on the carried values g = f - w
+// (CmConsts): raw moments of g from the pair sums, the moments of
+// f - f^eq + S/2 from the closed-form moments of the discrete equilibrium and
+// of the Guo term, binomial shift to central moments, relaxation, shift back,
+// and the D2Q9 inverse of the raw-moment transform
+template <int V>
+__device__ __forceinline__ void cm_collide(float (&g)[9][V], int j, const BgkConsts& k, const CmConsts& m)
+{
+    const float s1 = g[1][j] + g[3][j], d1 = g[1][j] - g[3][j];
+    const float s2 = g[2][j] + g[4][j], d2 = g[2][j] - g[4][j];
+    const float s5 = g[5][j] + g[7][j], d5 = g[5][j] - g[7][j];
+    const float s6 = g[6][j] + g[8][j], d6 = g[6][j] - g[8][j];
+    const float drho = (g[0][j] + s1) + (s2 + (s5 + s6));
+    const float jx = d1 + (d5 - d6), jy = d2 + (d5 + d6);
+    const float rho = 1.0f + drho;
+    const float inv = __fdividef(1.0f, rho);
+    const float ux = (jx + k.hgx) * inv, uy = (jy + k.hgy) * inv;
+    const float fx = m.fx, fy = m.fy;
+    // raw moments of g
+    const float m22 = s5 + s6, m20 = s1 + m22, m02 = s2 + m22, m11 = s5 - s6, m21 = d5 + d6, m12 = d5 - d6;
+    // moments of f - f^eq + S/2 (those of order 0 and 1 vanish)
+    const float rux = rho * ux, ruy = rho * uy, uF = ux * fx + uy * fy;
+    const float M20 = m20 - drho * (1.0f / 3.0f) - rux * ux + ux * fx;
+    const float M02 = m02 - drho * (1.0f / 3.0f) - ruy * uy + uy * fy;
+    const float M11 = m11 - rux * uy + 0.5f * (ux * fy + uy * fx);
+    const float M21 = m21 - ruy * (1.0f / 3.0f) + fy * (1.0f / 6.0f);
+    const float M12 = m12 - rux * (1.0f / 3.0f) + fx * (1.0f / 6.0f);
+    const float M22 = m22 - drho * (1.0f / 9.0f) - (rux * ux + ruy * uy) * (1.0f / 3.0f) + uF * (1.0f / 3.0f);
+    // central moments, relaxed
+    const float k21 = M21 - 2.0f * ux * M11 - uy * M20;
+    const float k12 = M12 - 2.0f * uy * M11 - ux * M02;
+    const float k22 = M22 - 2.0f * ux * M12 - 2.0f * uy * M21 + ux * ux * M02 + uy * uy * M20 + 4.0f * ux * uy * M11;
+    const float r20 = m.a * M20 + m.b * M02, r02 = m.b * M20 + m.a * M02, r11 = m.ws * M11;
+    const float r21 = m.w3 * k21, r12 = m.w3 * k12, r22 = m.w4 * k22;
+    // back to raw moments
+    const float R21 = r21 + 2.0f * ux * r11 + uy * r20;
+    const float R12 = r12 + 2.0f * uy * r11 + ux * r02;
+    const float R22 = r22 + 2.0f * ux * r12 + 2.0f * uy * r21 + ux * ux * r02 + uy * uy * r20 + 4.0f * ux * uy * r11;
+    // Guo term S_q = w_q (3 c.F - 3 u.F + 9 (c.u)(c.F)) and the update g + S - x
+    const float t0 = -3.0f * uF;
+    g[0][j] = g[0][j] + wf(0) * t0 - (R22 - r20 - r02);
+    const float cu1 = ux, cF1 = fx, cu2 = uy, cF2 = fy;
+    const float cu5 = ux + uy, cF5 = fx + fy, cu6 = uy - ux, cF6 = fy - fx;
+    const float e1 = t0 + 9.0f * cu1 * cF1, e2 = t0 + 9.0f * cu2 * cF2;
+    const float e5 = t0 + 9.0f * cu5 * cF5, e6 = t0 + 9.0f * cu6 * cF6;
+    g[1][j] = g[1][j] + wf(1) * (e1 + 3.0f * cF1) - 0.5f * (r20 - R12 - R22);
+    g[3][j] = g[3][j] + wf(3) * (e1 - 3.0f * cF1) - 0.5f * (r20 + R12 - R22);
+    g[2][j] = g[2][j] + wf(2) * (e2 + 3.0f * cF2) - 0.5f * (r02 - R21 - R22);
+    g[4][j] = g[4][j] + wf(4) * (e2 - 3.0f * cF2) - 0.5f * (r02 + R21 - R22);
+    g[5][j] = g[5][j] + wf(5) * (e5 + 3.0f * cF5) - 0.25f * (r11 + R21 + R12 + R22);
+    g[7][j] = g[7][j] + wf(7) * (e5 - 3.0f * cF5) - 0.25f * (r11 - R21 - R12 + R22);
+    g[6][j] = g[6][j] + wf(6) * (e6 + 3.0f * cF6) - 0.25f * (-r11 + R21 - R12 + R22);
+    g[8][j] = g[8][j] + wf(8) * (e6 - 3.0f * cF6) - 0.25f * (-r11 - R21 + R12 + R22);
+}
+
+// the collision selected at compile time: 0 BGK, 1 central moments
+template <int COLL, int V>
+__device__ __forceinline__ void collide(float (&g)[9][V], int j, const StepParams& p)
+{
+    if constexpr (COLL == 0)
+        bgk_collide<V>(g, j, p.bgk);
+    else
+        cm_collide<V>(g, j, p.bgk, p.cm);
+}
+
+template <int S, int V, bool GENERAL, bool SCALED, int COLL>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
                                           typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
 {
@@ -185,7 +251,7 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
 
     // ---- phase 3: BGK collision with Guo forcing
 #pragma unroll
-    for (int j = 0; j < V; ++j) bgk_collide<V>(g, j, p.bgk);
+    for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
 
     if (GENERAL && ox1 > ox0) {
         if (y >= oy0 && y < oy1) {
@@ -242,7 +308,7 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
     }
 }
 
-template <int S, int V, int WARPS, bool SCALED>
+template <int S, int V, int WARPS, bool SCALED, int COLL>
 __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
 {
     using T = typename Codec<S>::T;
@@ -257,9 +323,9 @@ __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
     const bool wall_row = y == 0 || y == p.ny - 1;
     const bool ring = p.ox1 > p.ox0 && y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1;
     if (wall_row || ring)
-        step_warp<S, V, true, SCALED>(p, src, dst, c, y, seg, lane);
+        step_warp<S, V, true, SCALED, COLL>(p, src, dst, c, y, seg, lane);
     else
-        step_warp<S, V, false, SCALED>(p, src, dst, c, y, seg, lane);
+        step_warp<S, V, false, SCALED, COLL>(p, src, dst, c, y, seg, lane);
 }
 
 template <int S, int V, int WARPS>
@@ -267,14 +333,21 @@ cudaError_t launch_step(const StepParams& p, cudaStream_t s)
 {
     const dim3 block(32, WARPS);
     const dim3 grid(p.nseg, (p.ny + WARPS - 1) / WARPS, p.n_list);
-    if constexpr (S == kFP32) {
-        step_kernel<S, V, WARPS, false><<<grid, block, 0, s>>>(p);
-    } else {
-        if (p.scale == 1.0f)
-            step_kernel<S, V, WARPS, false><<<grid, block, 0, s>>>(p);
-        else
-            step_kernel<S, V, WARPS, true><<<grid, block, 0, s>>>(p);
-    }
+    auto go = [&](auto coll) {
+        constexpr int C = decltype(coll)::value;
+        if constexpr (S == kFP32) {
+            step_kernel<S, V, WARPS, false, C><<<grid, block, 0, s>>>(p);
+        } else {
+            if (p.scale == 1.0f)
+                step_kernel<S, V, WARPS, false, C><<<grid, block, 0, s>>>(p);
+            else
+                step_kernel<S, V, WARPS, true, C><<<grid, block, 0, s>>>(p);
+        }
+    };
+    if (p.coll == 1)
+        go(std::integral_constant<int, 1>{});
+    else
+        go(std::integral_constant<int, 0>{});
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ struct StageInfo {
 // V sites x0 .. x0+V-1 of row y from the staged rows st; returns this
 // thread's share of the momentum exchange with the obstacle (GENERAL rows only:
 // the walls, and the ring of rows around the obstacle)
-template <int S, int V, bool SCALED, bool GENERAL>
+template <int S, int V, bool SCALED, bool GENERAL, int COLL>
 __device__ __forceinline__ float rows_sites(const StepParams& p, const typename Codec<S>::T* st,
                                             const typename Codec<S>::T* gsrc, typename Codec<S>::T* dst, int y,
                                             int x0, bool ring)
@@ -91,7 +91,7 @@ __device__ __forceinline__ float rows_sites(const StepParams& p, const typename 
         }
     }
 #pragma unroll
-    for (int j = 0; j < V; ++j) bgk_collide<V>(g, j, p.bgk);
+    for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
     float acc = 0.f;
     if (GENERAL && ring) {
         const bool row_solid = y >= p.oy0 && y < p.oy1;
@@ -127,7 +127,7 @@ __device__ __forceinline__ float rows_sites(const StepParams& p, const typename 
     return acc;
 }
 
-template <int S, int V, bool SCALED>
+template <int S, int V, bool SCALED, int COLL>
 __global__ void __launch_bounds__(kRowThreads, 2) step_rows_kernel(const StepParams p, int stages)
 {
     using T = typename Codec<S>::T;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) step_rows_kernel(const StepPar
         if (ring || y == 0 || y == p.ny - 1) {
             float acc = 0.f;
             for (int x0 = tid * V; x0 < nx; x0 += kRowConsumers * V)
-                acc += rows_sites<S, V, SCALED, true>(p, st, gsrc, dst, y, x0, ring);
+                acc += rows_sites<S, V, SCALED, true, COLL>(p, st, gsrc, dst, y, x0, ring);
             if (ring) {  // one drag partial per consumer warp and ring row
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) step_rows_kernel(const StepPar
             }
         } else {
             for (int x0 = tid * V; x0 < nx; x0 += kRowConsumers * V)
-                rows_sites<S, V, SCALED, false>(p, st, gsrc, dst, y, x0, false);
+                rows_sites<S, V, SCALED, false, COLL>(p, st, gsrc, dst, y, x0, false);
         }
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(smem_addr(&empty[s]));  // this warp is done with the stage
@@ -231,6 +231,22 @@ bool rows_supported(const StepParams& p)
     using T = typename Codec<S>::T;
     const int64_t stage = 9 * (int64_t)p.nx * sizeof(T);
     return p.nx % V == 0 && (p.nx * (int64_t)sizeof(T)) % 16 == 0 && 2 * stage <= kRowSmemBudget;
+}
+
+// one launch of one instantiation; the opt-in to more than 48 KB of dynamic
+// shared memory is made once per instantiation (its own static flag)
+template <int S, int V, bool SCALED, int COLL>
+cudaError_t launch_rows_kernel(const StepParams& p, cudaStream_t s, int grid, int stages, size_t smem)
+{
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(step_rows_kernel<S, V, SCALED, COLL>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kRowSmemBudget);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    step_rows_kernel<S, V, SCALED, COLL><<<grid, kRowThreads, smem, s>>>(p, stages);
+    return cudaGetLastError();
 }
 
 template <int S, int V>
@@ -247,21 +263,12 @@ cudaError_t launch_rows(const StepParams& p, cudaStream_t s)
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = items < 2 * sms ? items : 2 * sms;
-    auto go = [&](auto kernel) {
-        static bool attr = false;  // one per instantiation
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kRowSmemBudget);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        kernel<<<grid, kRowThreads, smem, s>>>(p, stages);
-        return cudaGetLastError();
-    };
-    if constexpr (S == kFP32) {
-        return go(step_rows_kernel<S, V, false>);
-    } else {
-        return p.scale == 1.0f ? go(step_rows_kernel<S, V, false>) : go(step_rows_kernel<S, V, true>);
-    }
+    const bool scaled = S != kFP32 && p.scale != 1.0f;
+    if (p.coll == 1)
+        return scaled ? launch_rows_kernel<S, V, S != kFP32, 1>(p, s, grid, stages, smem)
+                      : launch_rows_kernel<S, V, false, 1>(p, s, grid, stages, smem);
+    return scaled ? launch_rows_kernel<S, V, S != kFP32, 0>(p, s, grid, stages, smem)
+                  : launch_rows_kernel<S, V, false, 0>(p, s, grid, stages, smem);
 }
 
 }  // namespace lbm

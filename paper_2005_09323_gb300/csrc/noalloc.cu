@@ -64,6 +64,7 @@ extern "C" int lbm_step_noalloc(const lbm_config* cfg, int32_t n_clones, const v
     if (c.obs_w > 0 && (c.obs_x0 < 1 || c.obs_x0 + c.obs_w > c.nx - 1 || c.obs_y0 < 0 || c.obs_y0 + c.obs_h > c.ny))
         return fail(LBM_ERR_ARG, "lbm_step_noalloc: obstacle outside the allowed region");
     if (f_in_dev == f_out_dev) return fail(LBM_ERR_ARG, "lbm_step_noalloc: input and output must differ");
+    if (int rc = check_collision(c)) return rc;
     const int32_t pitch = ((c.nx + 255) / 256) * 256;
     if ((int64_t)9 * pitch * c.ny >= ((int64_t)1 << 31))
         return fail(LBM_ERR_ARG, "lbm_step_noalloc: one clone must hold fewer than 2^31 population values");
@@ -145,6 +146,8 @@ extern "C" int lbm_step_noalloc(const lbm_config* cfg, int32_t n_clones, const v
     p.gx = (float)c.gx;
     p.gy = (float)c.gy;
     p.bgk = bgk_consts(p.omega, p.gx, p.gy);
+    p.coll = c.collision;
+    p.cm = cm_consts(p.omega, (float)c.omega_bulk, (float)c.omega_3, (float)c.omega_4, p.gx, p.gy);
     const int sexp = c.storage == kFP32 ? 0 : c.shift_exp;
     p.scale = (float)std::ldexp(1.0, sexp);
     p.inv_scale = (float)std::ldexp(1.0, -sexp);

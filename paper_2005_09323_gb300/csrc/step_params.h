@@ -46,6 +46,34 @@ inline BgkConsts bgk_consts(float om, float gx, float gy)
     return k;
 }
 
+// Constants of the central-moment collision (the multiple-relaxation-time
+// collision on central moments of App. A's production runs), the
+// generalisation of the BGK collision above:
+//   g* = g + S - T^{-1} Omega T (f - f^eq + S/2),
+// T(u) the D2Q9 central-moment transform (moments 00 10 01 20 02 11 21 12 22),
+// f^eq the same discrete equilibrium, S the Guo term.  Omega relaxes k20 - k02
+// and k11 at ws = 1/tau, k20 + k02 at wb, k21 and k12 at w3, k22 at w4; equal
+// rates give the BGK collision exactly.
+struct CmConsts {
+    float ws, wb, w3, w4;
+    float a, b;    // (wb + ws)/2 and (wb - ws)/2: the k20, k02 block of Omega
+    float fx, fy;  // F
+};
+
+inline CmConsts cm_consts(float ws, float wb, float w3, float w4, float gx, float gy)
+{
+    CmConsts m;
+    m.ws = ws;
+    m.wb = wb;
+    m.w3 = w3;
+    m.w4 = w4;
+    m.a = 0.5f * (wb + ws);
+    m.b = 0.5f * (wb - ws);
+    m.fx = gx;
+    m.fy = gy;
+    return m;
+}
+
 // Everything one fused stream-collide launch needs.  Populations of clone c
 // live at buf[p] + c * clone_stride, direction q at + q * plane, row y at
 // + y * pitch; p alternates per clone with its own parity.
@@ -69,6 +97,8 @@ struct StepParams {
     int32_t step_in_batch;
     int32_t* err_flag;          // set to 1 when a bounded device-side wait runs out (may be null)
     BgkConsts bgk;              // bgk_consts(omega, gx, gy)
+    int32_t coll;               // 0: BGK; 1: central-moment collision with cm
+    CmConsts cm;
 };
 
 // consumer warps of the row-staged step kernel; each writes its own drag

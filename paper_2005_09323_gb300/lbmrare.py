@@ -48,7 +48,9 @@ class lbm_config(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("obs_x0", C.c_int32), ("obs_y0", C.c_int32),
                 ("obs_w", C.c_int32), ("obs_h", C.c_int32), ("tau", C.c_double), ("gx", C.c_double),
                 ("gy", C.c_double), ("storage", C.c_int32), ("shift_exp", C.c_int32), ("max_steps", C.c_int32),
-                ("ckpt_stride", C.c_int32), ("n_snapshots", C.c_int32), ("init_amp", C.c_double)]
+                ("ckpt_stride", C.c_int32), ("n_snapshots", C.c_int32), ("init_amp", C.c_double),
+                ("collision", C.c_int32), ("omega_bulk", C.c_double), ("omega_3", C.c_double),
+                ("omega_4", C.c_double)]
 
 
 class lbm_gktl_params(C.Structure):
@@ -63,12 +65,19 @@ class lbm_ams_params(C.Structure):
                 ("refresh_snapshots", C.c_int32)]
 
 
+COLLISION = {"bgk": 0, "cm": 1}
+
+
 def config(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, storage="fp32", shift_exp=0,
-           max_steps=1000, ckpt_stride=0, n_snapshots=0, init_amp=0.01) -> lbm_config:
+           max_steps=1000, ckpt_stride=0, n_snapshots=0, init_amp=0.01, collision="bgk", omega_bulk=1.0,
+           omega_3=1.0, omega_4=1.0) -> lbm_config:
+    """collision "bgk" or "cm" (central moments: shear at 1/tau, the bulk,
+    third- and fourth-order central moments at omega_bulk, omega_3, omega_4)"""
     ox0, oy0, ow, oh = obstacle
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    co = COLLISION[collision] if isinstance(collision, str) else int(collision)
     return lbm_config(nx, ny, ox0, oy0, ow, oh, tau, gx, gy, st, shift_exp, max_steps, ckpt_stride,
-                      n_snapshots, init_amp)
+                      n_snapshots, init_amp, co, omega_bulk, omega_3, omega_4)
 
 
 _lib = None

@@ -1,0 +1,150 @@
+"""GPU central-moment collision (collision = 1, App. A's production collision)
+against the FP64 oracle: the 256 x 64 channel over 200 steps, every FP32
+variant on the ragged grid with unequal rates, 16-bit storage, bitwise
+agreement of the variants, the BGK limit, the allocation-free step, and
+argument checks.  Tolerances as for BGK: populations 1e-5 and drag 1e-4
+relative (FP32 arithmetic against FP64)."""
+import numpy as np
+import pytest
+import torch
+
+from tests import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+POP_TOL, DRAG_TOL = 1e-5, 1e-4
+RATES = dict(omega_bulk=1.3, omega_3=0.9, omega_4=1.7)
+CFG1 = dict(nx=256, ny=64, obstacle=si.channel(256, 64, 8, 64), tau=0.52, gx=1e-6, max_steps=2000)
+RAGGED = dict(nx=200, ny=37, obstacle=(50, 14, 9, 7), tau=0.6, gx=2e-5, gy=-5e-6, max_steps=400)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2005_09323_gb300 import build, lbmrare
+    build.build()
+    lbmrare.lib()
+    return lbmrare
+
+
+class Ens:
+    def __init__(self, L, n, seed=0, **kw):
+        self.L, self.n = L, n
+        self.cfg = L.config(**kw)
+        self.h = L.lbm_ensemble_create(self.cfg, n, seed, torch.cuda.current_stream())
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.L.lbm_ensemble_destroy(self.h)
+
+    def pops(self, c):
+        return self.L.lbm_ensemble_get_populations(self.h, c, self.cfg.nx, self.cfg.ny)
+
+    def drag(self, t0, t1):
+        d = np.zeros((self.n, t1 - t0))
+        self.L.lbm_ensemble_drag(self.h, t0, t1, d)
+        return d
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def ocfg(orc, kw, rates):
+    return orc.cfg(kw["nx"], kw["ny"], obstacle=kw.get("obstacle", (0, 0, 0, 0)), tau=kw["tau"],
+                   gx=kw.get("gx", 0.0), gy=kw.get("gy", 0.0), collision=1, **rates)
+
+
+@pytest.mark.parametrize("rates", [dict(), RATES], ids=["unit_rates", "mixed_rates"])
+def test_cm_cfg1_200_steps_match_oracle(L, orc, rates):
+    with Ens(L, 1, seed=0, collision="cm", **rates, **CFG1) as e:
+        L.lbm_ensemble_step(e.h, 200)
+        oc = ocfg(orc, CFG1, rates)
+        f_ref, d_ref = orc.run(oc, orc.init(oc, 0, 0, 0.01), 200)
+        assert rel(e.pops(0), f_ref) < POP_TOL
+        assert rel(e.drag(0, 200)[0], d_ref) < DRAG_TOL
+
+
+def test_cm_every_fp32_variant_on_ragged_grid(L, orc):
+    oc = ocfg(orc, RAGGED, RATES)
+    refs = [orc.run(oc, orc.init(oc, 9, c, 0.01), 60) for c in range(3)]
+    tried = 0
+    for v in range(L.lbm_step_variant_count()):
+        st, vec, warps = L.lbm_step_variant_info(v)
+        if st != 0:
+            continue
+        with Ens(L, 3, seed=9, collision="cm", **RATES, **RAGGED) as e:
+            L.lbm_ensemble_set_variant(e.h, v)
+            L.lbm_ensemble_step(e.h, 60)
+            d = e.drag(0, 60)
+            for c in range(3):
+                assert rel(e.pops(c), refs[c][0]) < POP_TOL, (vec, warps, c)
+                assert rel(d[c], refs[c][1]) < DRAG_TOL, (vec, warps, c)
+        tried += 1
+    assert tried >= 3
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_cm_every_variant_agrees_bitwise(L, storage):
+    ref = None
+    for v in range(L.lbm_step_variant_count()):
+        st, vec, warps = L.lbm_step_variant_info(v)
+        if st != L.STORAGE[storage]:
+            continue
+        with Ens(L, 3, seed=9, storage=storage, collision="cm", **RATES, **dict(RAGGED, max_steps=50)) as e:
+            L.lbm_ensemble_set_variant(e.h, v)
+            L.lbm_ensemble_step(e.h, 30)
+            got = [e.pops(c) for c in range(3)]
+        if ref is None:
+            ref = got
+            continue
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), (vec, warps)
+
+
+def test_cm_fp16_storage(L, orc):
+    with Ens(L, 1, seed=0, storage="fp16", collision="cm", **CFG1) as e:
+        L.lbm_ensemble_step(e.h, 200)
+        oc = ocfg(orc, CFG1, {})
+        f_ref, _ = orc.run(oc, orc.init(oc, 0, 0, 0.01), 200)
+        g_ref = f_ref - orc.feq(1.0, 0.0, 0.0)[:, None, None]
+        assert np.abs(e.pops(0) - f_ref).max() / np.abs(g_ref).max() < 3e-3
+        assert np.all(np.isfinite(e.drag(0, 200)))
+
+
+def test_cm_with_equal_rates_is_bgk(L):
+    tau = RAGGED["tau"]
+    eq = dict(omega_bulk=1 / tau, omega_3=1 / tau, omega_4=1 / tau)
+    with Ens(L, 2, seed=3, **RAGGED) as a, Ens(L, 2, seed=3, collision="cm", **eq, **RAGGED) as b:
+        L.lbm_ensemble_step(a.h, 80)
+        L.lbm_ensemble_step(b.h, 80)
+        for c in range(2):
+            assert rel(b.pops(c), a.pops(c)) < 1e-6
+        assert rel(b.drag(0, 80), a.drag(0, 80)) < 1e-5
+
+
+def test_cm_noalloc_step_matches_ensemble(L):
+    kw = dict(RAGGED, max_steps=4, collision="cm", **RATES)
+    n = 2
+    with Ens(L, n, seed=5, **kw) as e:
+        f0 = [e.pops(c) for c in range(n)]
+        L.lbm_ensemble_step(e.h, 1)
+        ref = [e.pops(c) for c in range(n)]
+    nx, ny = kw["nx"], kw["ny"]
+    pitch = L.noalloc_pitch(nx)
+    a = torch.zeros((n, 9, ny, pitch), dtype=torch.float32, device="cuda")
+    for c in range(n):
+        a[c, :, :, :nx] = torch.tensor(f0[c], dtype=torch.float32)
+    b = torch.zeros_like(a)
+    d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    L.lbm_step_noalloc(e.cfg, n, a, b, d, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    for c in range(n):
+        assert rel(b[c, :, :, :nx].double().cpu().numpy(), ref[c]) < POP_TOL
+
+
+def test_cm_argument_errors(L):
+    for bad in (dict(collision=2), dict(collision="cm", omega_bulk=2.5), dict(collision="cm", omega_4=0.0)):
+        with pytest.raises(L.LbmError):
+            L.lbm_ensemble_create(L.config(**dict(RAGGED, **bad)), 1, 0, torch.cuda.current_stream())
