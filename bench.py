@@ -64,11 +64,11 @@ METRIC = "Ensemble D2Q9 GLUPS & HBM-roofline fraction; time-to-return-time vs pl
 NCU_TRAFFIC = {
     ("gktl", "step_kernel<fp32, vec=4, warps=4>"): {
         "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp32.cu"),
-        "sha": "d8352fcdf3e131b9", "bytes_per_site": 68.4740},
+        "sha": "b014b575bcce569b", "bytes_per_site": 68.4726},
     ("precision", "step_rows_kernel<fp16, vec=4, warps=9>"): {
         "files": ("lbm_step_rows.cuh", "async_copy.cuh", "lbm_step.cuh", "lbm_device.cuh", "step_params.h",
                   "step_fp16.cu"),
-        "sha": "a812d592ef16a159", "bytes_per_site": 32.6753},
+        "sha": "67c4d5757ae86952", "bytes_per_site": 32.5216},
 }
 
 
