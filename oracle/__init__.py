@@ -299,3 +299,46 @@ def ams_probability(log_weight: float, maxima: np.ndarray, level: float) -> floa
     final ensemble whose maximum reaches the level."""
     maxima = np.asarray(maxima, dtype=np.float64)
     return float(np.exp(log_weight) * np.mean(maxima >= level))
+
+
+# ---------------------------------------------------------------- direct sampling (Sec. 3)
+def autocorrelation(drag: np.ndarray, max_lag: int):
+    """C(tau) = mean f~(t + tau) f~(t) / mean f~^2 of the drag fluctuations
+    f~ = f - mean (caption of Fig. pdf_drag), pooled over the rows of drag
+    [clones][steps] (independent trajectories; each lag averages the products
+    available inside each row).  Returns (C[0..max_lag], tau_c) with tau_c the
+    first lag where C <= 0 (C(tau_c) = 0 in the paper), -1 if none."""
+    d = np.asarray(drag, dtype=np.float64)
+    d = d.reshape(1, -1) if d.ndim == 1 else d
+    n, length = d.shape
+    mu = d.mean()
+    x = d - mu
+    var = np.mean(x * x)
+    c = np.zeros(max_lag + 1)
+    for tau in range(max_lag + 1):
+        c[tau] = np.mean(x[:, tau:] * x[:, :length - tau]) / var
+    below = np.nonzero(c <= 0.0)[0]
+    return c, int(below[0]) if below.size else -1
+
+
+def return_times(drag: np.ndarray, levels, gap: int):
+    """Waiting-time return times of Sec. 3 from drag [clones][steps]: an
+    event of level a starts where the series crosses from below a to >= a,
+    unless it was >= a within the last `gap` steps (the same fluctuation);
+    r(a) = observed steps / number of events, i.e. the mean waiting time
+    between events.  Returns (events[len(levels)], r[len(levels)]), r = inf
+    without events."""
+    d = np.asarray(drag, dtype=np.float64)
+    d = d.reshape(1, -1) if d.ndim == 1 else d
+    n, length = d.shape
+    events = np.zeros(len(levels), dtype=np.int64)
+    for j, a in enumerate(levels):
+        for row in d:
+            last_above = None
+            for t in range(length):
+                if row[t] >= a:
+                    if t > 0 and row[t - 1] < a and (last_above is None or t - last_above > gap):
+                        events[j] += 1
+                    last_above = t
+    r = np.where(events > 0, n * length / np.maximum(events, 1), np.inf)
+    return events, r
