@@ -210,6 +210,30 @@ int lbm_ensemble_set_graphs(lbm_ensemble* e, int32_t enable);
 int lbm_ensemble_set_timing(lbm_ensemble* e, int32_t enable);
 int lbm_ensemble_kernel_time(lbm_ensemble* e, double* ms, int64_t* launches, int32_t reset);
 
+/* ---------------------------------------------------------------- direct sampling (Sec. 3) */
+
+/* Drag statistics of direct sampling.  The clones are independent
+ * trajectories; their drag series over the steps [t0, t1) are pooled (every
+ * clone must have reached t1).  FP64, every sum in a fixed order.
+ *
+ * lbm_drag_autocorrelation: c_dev[tau] (device, max_lag + 1 doubles) =
+ *   mean_{clones, t} f~(t + tau) f~(t) / mean f~^2,   f~ = f_d - mean f_d,
+ * the autocorrelation of the caption of Fig. pdf_drag; each lag averages the
+ * n (t1 - t0 - tau) products inside the series.  *tau_c (host, may be NULL)
+ * receives the correlation time, the first lag with C <= 0 (C(tau_c) = 0 in
+ * the paper), or -1 if C stays positive up to max_lag (then waits).
+ * 0 <= max_lag < t1 - t0.
+ *
+ * lbm_drag_return_times: the waiting-time return time of Sec. 3 for each of
+ * n_levels levels (levels_dev, device doubles).  An event of level a starts
+ * where a series crosses from below a to >= a, unless it was >= a within the
+ * last gap steps (then it is the same fluctuation; gap = tau_c declusters).
+ * events[j] (host) = events over all clones; r[j] (host) = n (t1 - t0) /
+ * events[j], the mean waiting time in steps, +inf without events.  Waits. */
+int lbm_drag_autocorrelation(lbm_ensemble* e, int32_t t0, int32_t t1, int32_t max_lag, double* c_dev, int32_t* tau_c);
+int lbm_drag_return_times(lbm_ensemble* e, int32_t t0, int32_t t1, int32_t n_levels, const double* levels_dev,
+                          int32_t gap, int64_t* events, double* r);
+
 /* ---------------------------------------------------------------- drivers */
 
 /* GKTL run (App. C.1), from the ensemble's current time t0 (all clones equal):

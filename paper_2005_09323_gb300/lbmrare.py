@@ -28,6 +28,7 @@ EXPORTS = [
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
     "lbm_ensemble_set_graphs", "lbm_step_variant_kind", "cnn_set_conv_path", "cnn_status",
+    "lbm_drag_autocorrelation", "lbm_drag_return_times",
     "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
     "lbm_gktl_run", "gktl_probability", "lbm_ams_run", "ams_probability",
     "cnn_create", "cnn_destroy", "cnn_param_count", "cnn_get_params", "cnn_set_params", "cnn_forward",
@@ -142,6 +143,8 @@ def lib():
             "lbm_ensemble_fields": ([p, p, i32, i32, C.c_float, C.c_float, p], C.c_int),
             "cnn_shape": ([p, p, p, p], C.c_int),
             "cnn_set_conv_path": ([p, i32], C.c_int),
+            "lbm_drag_autocorrelation": ([p, i32, i32, i32, p, p], C.c_int),
+            "lbm_drag_return_times": ([p, i32, i32, i32, p, i32, p, p], C.c_int),
             "cnn_status": ([p, p], C.c_int),
             "cnn_predict": ([p, p, i64, p, p], C.c_int),
             "cnn_fit": ([p, p, p, i64, i32, i32, C.c_float, u64, p, p], C.c_int),
@@ -365,6 +368,24 @@ def lbm_ams_run(e, t_a: int, window: int, max_iter: int, level: float, eps: floa
                              _host(kills)))
     out = (it.value, lw.value, levels[:it.value].copy())
     return out + (kills[:it.value].copy(),) if with_kills else out
+
+
+def lbm_drag_autocorrelation(e, t0: int, t1: int, max_lag: int, c_dev):
+    """C(tau) into c_dev (float64 CUDA tensor, max_lag + 1); returns tau_c"""
+    import torch
+    tc = C.c_int32()
+    _check(lib().lbm_drag_autocorrelation(e, t0, t1, max_lag, _dev(c_dev, torch.float64), C.byref(tc)))
+    return tc.value
+
+
+def lbm_drag_return_times(e, t0: int, t1: int, levels_dev, gap: int):
+    """returns (events[n_levels] int64, r[n_levels] float64) for the levels of levels_dev"""
+    import torch
+    n = levels_dev.numel()
+    ev = np.zeros(n, dtype=np.int64)
+    r = np.zeros(n)
+    _check(lib().lbm_drag_return_times(e, t0, t1, n, _dev(levels_dev, torch.float64), gap, _host(ev), _host(r)))
+    return ev, r
 
 
 def ams_probability(log_weight: float, Q_dev, levels_dev, p_dev, stream=None):
