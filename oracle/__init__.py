@@ -59,6 +59,8 @@ def lib():
         L.orc_macro.argtypes = [p, p, p, p, p]
         L.orc_is_solid.argtypes = [p, C.c_int, C.c_int]; L.orc_is_solid.restype = C.c_int
         L.orc_cm_collide.argtypes = [p, d, d, p, p, p, p]
+        L.orc_tau_at.argtypes = [p, C.c_int]; L.orc_tau_at.restype = d
+        L.orc_inlet_u.argtypes = [p, C.c_int]; L.orc_inlet_u.restype = d
         L.orc_perturb_alphas.argtypes = [u64, u64, i32, i32, p]
         L.orc_perturb.argtypes = [p, p, i32, p, p, d, p]
         L.orc_gktl_weights.argtypes = [i32, p, p, p]; L.orc_gktl_weights.restype = C.c_int
@@ -81,15 +83,20 @@ class Cfg(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ox0", C.c_int32), ("oy0", C.c_int32),
                 ("ow", C.c_int32), ("oh", C.c_int32), ("tau", C.c_double), ("gx", C.c_double),
                 ("gy", C.c_double), ("collision", C.c_int32), ("omega_bulk", C.c_double),
-                ("omega_3", C.c_double), ("omega_4", C.c_double)]
+                ("omega_3", C.c_double), ("omega_4", C.c_double), ("open_x", C.c_int32), ("u_in", C.c_double),
+                ("grid_x0", C.c_int32), ("grid_w", C.c_int32), ("grid_bar", C.c_int32), ("grid_gap", C.c_int32),
+                ("sponge_len", C.c_int32), ("sponge_tau", C.c_double)]
 
 
 def cfg(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, collision=0, omega_bulk=1.0, omega_3=1.0,
-        omega_4=1.0) -> Cfg:
+        omega_4=1.0, open_x=0, u_in=0.0, grid=(0, 0, 0, 0), sponge_len=0, sponge_tau=1.0) -> Cfg:
     """collision 0: BGK; 1: central-moment MRT (shear at 1/tau, the other
-    rates as given)"""
+    rates as given).  open_x = 1: inlet/outlet channel with centreline inlet
+    velocity u_in, entrance grid (x0, width, bar, gap) and sponge."""
     ox0, oy0, ow, oh = obstacle
-    return Cfg(nx, ny, ox0, oy0, ow, oh, tau, gx, gy, collision, omega_bulk, omega_3, omega_4)
+    gx0, gw, gbar, ggap = grid
+    return Cfg(nx, ny, ox0, oy0, ow, oh, tau, gx, gy, collision, omega_bulk, omega_3, omega_4, open_x, u_in,
+               gx0, gw, gbar, ggap, sponge_len, sponge_tau)
 
 
 # ---------------------------------------------------------------- rng
@@ -173,9 +180,11 @@ def macro(c: Cfg, f: np.ndarray):
 
 
 def solid_mask(c: Cfg) -> np.ndarray:
+    """solid cells: the square and, in an open channel, the entrance grid"""
     m = np.zeros((c.ny, c.nx), dtype=bool)
-    if c.ow > 0:
-        m[c.oy0:c.oy0 + c.oh, c.ox0:c.ox0 + c.ow] = True
+    for y in range(c.ny):
+        for x in range(c.nx):
+            m[y, x] = bool(lib().orc_is_solid(C.byref(c), x, y))
     return m
 
 

@@ -36,9 +36,39 @@ static const double CS2 = 1.0 / 3.0;
 
 #define IDX(c, q, x, y) ((((size_t)(q)) * (c)->ny + (size_t)(y)) * (c)->nx + (size_t)(x))
 
-int orc_is_solid(const orc_cfg* c, int x, int y)
+/* the square whose drag is measured */
+static int in_obstacle(const orc_cfg* c, int x, int y)
 {
     return c->ow > 0 && x >= c->ox0 && x < c->ox0 + c->ow && y >= c->oy0 && y < c->oy0 + c->oh;
+}
+
+/* Open channel of Sec. 2: a grid of bars at the entrance generates the
+ * turbulence; bars of height grid_bar separated by grid_gap fluid rows,
+ * starting with a gap at the bottom wall, grid_w columns thick. */
+static int in_grid(const orc_cfg* c, int x, int y)
+{
+    return c->grid_w > 0 && x >= c->grid_x0 && x < c->grid_x0 + c->grid_w &&
+           (y % (c->grid_bar + c->grid_gap)) >= c->grid_gap;
+}
+
+int orc_is_solid(const orc_cfg* c, int x, int y) { return in_obstacle(c, x, y) || in_grid(c, x, y); }
+
+/* sponge zone (Sec. 2, "viscosity artificially enhanced" near the end of the
+ * channel): tau rises quadratically from tau to sponge_tau over the last
+ * sponge_len columns, reaching sponge_tau at x = nx - 1 */
+double orc_tau_at(const orc_cfg* c, int x)
+{
+    if (!c->open_x || c->sponge_len <= 0 || x < c->nx - c->sponge_len) return c->tau;
+    double s = (double)(x - (c->nx - c->sponge_len) + 1) / c->sponge_len;
+    return c->tau + (c->sponge_tau - c->tau) * s * s;
+}
+
+/* parabolic inlet profile vanishing on the halfway walls y = -1/2 and
+ * y = ny - 1/2, u_in on the centreline */
+double orc_inlet_u(const orc_cfg* c, int y)
+{
+    double h = c->ny, yy = y + 0.5;
+    return c->u_in * 4.0 * yy * (h - yy) / (h * h);
 }
 
 void orc_feq(double rho, double ux, double uy, double feq[9])
@@ -76,6 +106,7 @@ void orc_init(const orc_cfg* c, uint64_t seed, int32_t clone, double amp, double
                 orc_philox4x64(ctr, key, o);
                 double ux = amp * (2.0 * orc_u01(o[0]) - 1.0);
                 double uy = amp * (2.0 * orc_u01(o[1]) - 1.0);
+                if (c->open_x) ux += orc_inlet_u(c, y);  /* open channel: the inlet profile everywhere */
                 orc_feq(1.0, ux, uy, feq);
             }
             for (int i = 0; i < 9; ++i) f[IDX(c, i, x, y)] = feq[i];
@@ -115,7 +146,7 @@ static void link_forces(const orc_cfg* c, const double* f, double* fo, double* f
                 if (yn < 0 || yn >= c->ny) {
                     wx += 2.0 * CX[i] * v;
                     wy += 2.0 * CY[i] * v;
-                } else if (orc_is_solid(c, xn, yn)) {
+                } else if (in_obstacle(c, xn, yn)) {  /* the drag: links into the square only */
                     ox += 2.0 * CX[i] * v;
                     oy += 2.0 * CY[i] * v;
                 }
@@ -213,6 +244,79 @@ void orc_cm_collide(const double f[9], double ux, double uy, const double feq[9]
     }
 }
 
+/* Boundary columns of the open channel (Sec. 2), applied to post-collision
+ * populations:
+ *   inlet  x = 0:      f = f^eq(rho = 1, u = (u_in(y), 0))  ("constant
+ *                      parabolic velocity profile and constant mass density");
+ *   outlet x = nx-1:   u extrapolated to second order from the two columns
+ *                      upstream, u(nx-1) = 2 u(nx-2) - u(nx-3), rho = 1, and
+ *                      the populations regularized (Latt et al. 2008):
+ *                      f = f^eq(rho, u) + w_i / (2 cs2^2) Q_i : Pi,
+ *                      Q_i = c_i c_i - cs2 I,  Pi = -2 rho cs2 (tau_out - 1) S,
+ *                      S the strain rate from finite differences (one-sided
+ *                      second order in x, central in y, one-sided at the walls);
+ *                      tau_out - 1, not tau_out: the post-collision
+ *                      non-equilibrium is (1 - 1/tau) times the pre-collision one.
+ * The outlet density is the reference density rather than extrapolated: with
+ * the inlet holding rho = 1, an extrapolated outlet density leaves the mean
+ * pressure drop free, and that neutral mode drifts (the channel either
+ * accelerates or fills up and stalls within a few thousand steps).
+ * The macroscopic fields of a post-collision state are rho = sum f,
+ * rho u = sum c f (an open channel has no body force).                       */
+static void open_boundaries(const orc_cfg* c, double* f)
+{
+    const int nx = c->nx, ny = c->ny;
+    for (int y = 0; y < ny; ++y) {
+        if (orc_is_solid(c, 0, y)) continue;
+        double feq[9];
+        orc_feq(1.0, orc_inlet_u(c, y), 0.0, feq);
+        for (int i = 0; i < 9; ++i) f[IDX(c, i, 0, y)] = feq[i];
+    }
+    double* ux = malloc(sizeof(double) * ny);
+    double* uy = malloc(sizeof(double) * ny);
+    double* u2x = malloc(sizeof(double) * ny);  /* u at nx-2 minus u at nx-3: the x derivative */
+    double* u2y = malloc(sizeof(double) * ny);
+    for (int y = 0; y < ny; ++y) {
+        double vx[2], vy[2];
+        for (int k = 0; k < 2; ++k) {
+            const int x = nx - 2 - k;
+            double m = 0, jx = 0, jy = 0;
+            for (int i = 0; i < 9; ++i) {
+                double v = f[IDX(c, i, x, y)];
+                m += v;
+                jx += v * CX[i];
+                jy += v * CY[i];
+            }
+            vx[k] = jx / m;
+            vy[k] = jy / m;
+        }
+        ux[y] = 2.0 * vx[0] - vx[1];
+        uy[y] = 2.0 * vy[0] - vy[1];
+        u2x[y] = vx[0] - vx[1];  /* (3 u(nx-1) - 4 u(nx-2) + u(nx-3)) / 2 */
+        u2y[y] = vy[0] - vy[1];
+    }
+    const double tau_out = orc_tau_at(c, nx - 1);
+    for (int y = 0; y < ny; ++y) {
+        const int ym = y > 0 ? y - 1 : y, yp = y < ny - 1 ? y + 1 : y;
+        const double dy = (double)(yp - ym);
+        const double dxux = u2x[y], dxuy = u2y[y];
+        const double dyux = (ux[yp] - ux[ym]) / dy, dyuy = (uy[yp] - uy[ym]) / dy;
+        const double sxx = dxux, syy = dyuy, sxy = 0.5 * (dyux + dxuy);
+        const double pre = -2.0 * CS2 * (tau_out - 1.0);  /* rho = 1 */
+        const double pxx = pre * sxx, pyy = pre * syy, pxy = pre * sxy;
+        double feq[9];
+        orc_feq(1.0, ux[y], uy[y], feq);
+        for (int i = 0; i < 9; ++i) {
+            const double q = (CX[i] * CX[i] - CS2) * pxx + 2.0 * CX[i] * CY[i] * pxy + (CY[i] * CY[i] - CS2) * pyy;
+            f[IDX(c, i, nx - 1, y)] = feq[i] + W[i] / (2.0 * CS2 * CS2) * q;
+        }
+    }
+    free(ux);
+    free(uy);
+    free(u2x);
+    free(u2y);
+}
+
 void orc_step(const orc_cfg* c, const double* fin, double* fout, double* force_obs, double* force_wall)
 {
     const int nx = c->nx, ny = c->ny;
@@ -225,6 +329,10 @@ void orc_step(const orc_cfg* c, const double* fin, double* fout, double* force_o
                 int xn = ((x + CX[i]) % nx + nx) % nx;
                 int yn = y + CY[i];
                 double v = fin[IDX(c, i, x, y)];
+                /* open channel: a population leaving through the inlet or the
+                 * outlet column is gone (those columns are set by their
+                 * boundary conditions after the collision) */
+                if (c->open_x && (x + CX[i] < 0 || x + CX[i] >= nx) && yn >= 0 && yn < ny) continue;
                 if (yn < 0 || yn >= ny || orc_is_solid(c, xn, yn))
                     fout[IDX(c, OPP[i], x, y)] = v;
                 else
@@ -250,17 +358,20 @@ void orc_step(const orc_cfg* c, const double* fin, double* fout, double* force_o
             double feq[9], S[9];
             orc_feq(rho, ux, uy, feq);
             orc_guo(ux, uy, c->gx, c->gy, S);
+            const double tau = orc_tau_at(c, x);
             if (c->collision == 1) {
-                const double rates[4] = {1.0 / c->tau, c->omega_bulk, c->omega_3, c->omega_4};
+                const double rates[4] = {1.0 / tau, c->omega_bulk, c->omega_3, c->omega_4};
                 double out[9];
                 orc_cm_collide(f, ux, uy, feq, S, rates, out);
                 for (int i = 0; i < 9; ++i) fout[IDX(c, i, x, y)] = out[i];
             } else {
                 for (int i = 0; i < 9; ++i)
-                    fout[IDX(c, i, x, y)] = f[i] - (f[i] - feq[i]) / c->tau + (1.0 - 1.0 / (2.0 * c->tau)) * S[i];
+                    fout[IDX(c, i, x, y)] = f[i] - (f[i] - feq[i]) / tau + (1.0 - 1.0 / (2.0 * tau)) * S[i];
             }
         }
-    /* 3. momentum exchanged with the obstacle and the walls by the links that
+    /* 3. open channel: the boundary columns (Sec. 2) */
+    if (c->open_x) open_boundaries(c, fout);
+    /* 4. momentum exchanged with the obstacle and the walls by the links that
      *    the next streaming step bounces back */
     if (force_obs || force_wall) link_forces(c, fout, force_obs, force_wall);
 }

@@ -23,6 +23,12 @@
  *   orc_gktl_weights/select sum of weights = N, k = 0 identity, brute-force
  *                           mean copy counts; OU closed-form SCGF (App. C)
  *   orc_ams_select          OU brute-force exceedance probability (App. B)
+ *   open channel (Sec. 2)   rest state kept; per-step mass balance through
+ *                           the boundary columns; developed flow: one mass
+ *                           flux through every cut, parabolic profile,
+ *                           cs2 drho/dx = nu(x) rho u'' in bulk and sponge;
+ *                           inlet equilibrium; outlet moments (numpy);
+ *                           grid geometry; drag over the square's links only
  */
 #ifndef LBMRARE_ORACLE_H
 #define LBMRARE_ORACLE_H
@@ -52,9 +58,23 @@ typedef struct {
     double omega_bulk, omega_3, omega_4;  /* collision 1: rates of the bulk (k20 + k02), third-
                                        order (k21, k12) and fourth-order (k22) central moments;
                                        shear (k20 - k02, k11) relaxes at 1/tau */
+    /* open channel (Sec. 2): x not periodic; inlet column x = 0 held at the
+     * equilibrium of rho = 1 and the parabolic profile of centreline u_in;
+     * outlet column x = nx-1: rho = 1, u extrapolated (second order), the
+     * populations regularized with the finite-difference strain rate.        */
+    int32_t open_x;
+    double u_in;
+    int32_t grid_x0, grid_w, grid_bar, grid_gap;  /* entrance grid: cells x in [grid_x0, grid_x0+grid_w)
+                                       with y mod (bar + gap) >= gap are solid; grid_w = 0: none */
+    int32_t sponge_len;             /* tau rises to sponge_tau over the last sponge_len columns */
+    double sponge_tau;
 } orc_cfg;
 
-int orc_is_solid(const orc_cfg* c, int x, int y);
+int orc_is_solid(const orc_cfg* c, int x, int y);   /* obstacle or entrance grid */
+/* relaxation time of column x (tau, or the sponge profile of an open channel) */
+double orc_tau_at(const orc_cfg* c, int x);
+/* inlet velocity of row y of an open channel */
+double orc_inlet_u(const orc_cfg* c, int y);
 /* equilibrium populations for density rho and velocity (ux, uy) */
 void orc_feq(double rho, double ux, double uy, double feq[9]);
 /* Guo forcing term S_q for velocity u and force density (gx, gy) */
