@@ -49,8 +49,9 @@ typedef enum {
  * halfway bounce-back on its surface, and a constant body-force density
  * (gx, gy) on fluid nodes (Guo forcing). */
 typedef struct {
-    int32_t nx, ny;            /* nx a multiple of 8, nx >= 8, ny >= 2 */
-    int32_t obs_x0, obs_y0, obs_w, obs_h;  /* obs_w = 0: no obstacle; else 1 <= obs_x0, obs_x0+obs_w <= nx-1 */
+    int32_t nx, ny;            /* nx a multiple of 8 (any nx >= 8 for an open channel), nx >= 8, ny >= 2 */
+    int32_t obs_x0, obs_y0, obs_w, obs_h;  /* obs_w = 0: no obstacle; else 1 <= obs_x0, obs_x0+obs_w <= nx-1
+                                              (<= nx-3 in an open channel) */
     double tau;                /* BGK relaxation time (> 1/2); nu = (tau - 1/2)/3 */
     double gx, gy;             /* force density per fluid node */
     int32_t storage;           /* lbm_storage */
@@ -69,6 +70,32 @@ typedef struct {
      * configurations are BGK. */
     int32_t collision;
     double omega_bulk, omega_3, omega_4;
+    /* open channel (Sec. 2); open_x = 0 (zero-initialised) is the periodic,
+     * body-forced channel.  open_x = 1:
+     *   inlet   column x = 0 holds the equilibrium of rho = 1 and u = (u_in(y), 0),
+     *           u_in(y) = 4 u_in (y + 1/2)(ny - y - 1/2) / ny^2, the parabola that
+     *           vanishes on the halfway walls with centreline value u_in;
+     *   outlet  column x = nx-1 takes rho = 1 and the velocity extrapolated to
+     *           second order from columns nx-2 and nx-3, its populations
+     *           regularized with the finite-difference strain rate (Latt et al.
+     *           2008); the paper extrapolates the density too, which leaves the
+     *           mean pressure drop free (a drifting neutral mode);
+     *   grid    bars of grid_bar rows separated by grid_gap fluid rows (a gap at
+     *           the bottom wall) over columns [grid_x0, grid_x0 + grid_w);
+     *           grid_w = 0: none.  The drag counts the square's links only;
+     *   sponge  tau(x) = tau + (sponge_tau - tau) s^2 over the last sponge_len
+     *           columns, s = (x - nx + sponge_len + 1) / sponge_len;
+     * each step the boundary columns are overwritten after the collision.
+     * Requires gx = gy = 0, 8 <= nx (any nx, not only multiples of 8), ny >= 3,
+     * the square and the grid inside columns [1, nx-3), tau at the outlet
+     * (sponge_tau, or tau without a sponge) at most 1 (larger values made the
+     * outlet unstable), |u_in| < 0.3.  Open channels run on register-staged
+     * step variants only and not through lbm_step_noalloc. */
+    int32_t open_x;
+    double u_in;
+    int32_t grid_x0, grid_w, grid_bar, grid_gap;
+    int32_t sponge_len;
+    double sponge_tau;
 } lbm_config;
 
 typedef struct lbm_ensemble lbm_ensemble;

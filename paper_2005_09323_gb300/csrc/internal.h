@@ -24,16 +24,22 @@ int cuda_fail(cudaError_t err, const char* what);
     } while (0)
 
 struct StepVariant {
+    using Launch = cudaError_t (*)(const StepParams&, cudaStream_t);
     int storage;
     int vec;    // sites per thread
     int warps;  // warps per block
     cudaError_t (*launch)(const StepParams&, cudaStream_t);
     int kind;   // 0: register-staged row segments per warp; 1: whole rows staged by bulk copies
     bool (*supports)(const StepParams&);  // null: every shape
+    // the open channel's step (fused step + boundary columns); null: this
+    // variant has no open-channel instantiation
+    Launch launch_open = nullptr;
 };
 
 // LBM_ERR_ARG unless the collision fields of c are valid (lbm_ensemble.cu)
 int check_collision(const lbm_config& c);
+// LBM_ERR_ARG unless the open-channel fields of c are valid (lbm_ensemble.cu)
+int check_open(const lbm_config& c);
 
 // all compiled variants of the fused step (lbm_step.cu)
 const std::vector<StepVariant>& step_variants();
@@ -89,6 +95,8 @@ struct lbm_ensemble {
     double* red_partials;     // [N][red_blocks] (or larger)
     int32_t red_blocks;
     double* mass_dev;         // [N]
+    float* om_col;            // open channel: [nx] relaxation rate of each column
+    float* inlet_g;           // open channel: [9][ny] inlet populations minus w_q
     double* scores;           // [N][max_steps] trailing means
     int32_t score_window, score_t_begin, score_t_end;  // arguments of the last lbm_ensemble_scores
     int32_t* fields_list_dev; // clone list of field extractions

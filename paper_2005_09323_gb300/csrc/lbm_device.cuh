@@ -22,6 +22,18 @@ static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "axis op
 static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "diagonal opposites");
 static_assert(cx(opp(5)) == -cx(5) && cy(opp(6)) == -cy(6), "opposite velocity");
 
+// Solid cells (Sec. 2): the square [ox0, ox1) x [oy0, oy1) whose drag is
+// measured (ox1 == ox0 for none) and, in an open channel, the entrance grid of
+// bars: cells x in [gx0, gx1) with y mod period >= gap (gx1 == gx0 for none;
+// bars of period - gap rows separated by gap fluid rows, a gap at the bottom).
+struct Solids {
+    int32_t ox0, ox1, oy0, oy1;
+    int32_t gx0, gx1, gap, period;
+    __host__ __device__ bool square(int x, int y) const { return x >= ox0 && x < ox1 && y >= oy0 && y < oy1; }
+    __host__ __device__ bool grid(int x, int y) const { return x >= gx0 && x < gx1 && y % period >= gap; }
+    __host__ __device__ bool at(int x, int y) const { return square(x, y) || grid(x, y); }
+};
+
 // ---------------------------------------------------------------- random numbers
 // Philox4x64-10 of Salmon, Moraes, Dror & Shaw (SC'11): ten rounds of two
 // 64x64 -> 128-bit products whose halves are mixed with the other counter

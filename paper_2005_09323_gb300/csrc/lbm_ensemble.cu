@@ -35,6 +35,9 @@ int cuda_fail(cudaError_t err, const char* what)
 void register_step_fp32(std::vector<StepVariant>&);
 void register_step_fp16(std::vector<StepVariant>&);
 void register_step_bf16(std::vector<StepVariant>&);
+void register_open_fp32(std::vector<StepVariant>&);
+void register_open_fp16(std::vector<StepVariant>&);
+void register_open_bf16(std::vector<StepVariant>&);
 
 const std::vector<StepVariant>& step_variants()
 {
@@ -43,6 +46,9 @@ const std::vector<StepVariant>& step_variants()
         register_step_fp32(v);
         register_step_fp16(v);
         register_step_bf16(v);
+        register_open_fp32(v);
+        register_open_fp16(v);
+        register_open_bf16(v);
         return v;
     }();
     return table;
@@ -61,8 +67,7 @@ static int elem_size(int storage) { return storage == kFP32 ? 4 : 2; }
 // ---------------------------------------------------------------- kernels
 template <int S>
 __global__ void init_kernel(void* buf, int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx,
-                            int32_t ny, int32_t n, int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1,
-                            uint64_t seed, double amp, float scale)
+                            int32_t ny, int32_t n, Solids sol, uint64_t seed, double amp, double u_in, float scale)
 {
     using T = typename Codec<S>::T;
     T* base = static_cast<T*>(buf);
@@ -72,11 +77,14 @@ __global__ void init_kernel(void* buf, int64_t clone_stride, int64_t plane, int3
         const int64_t site = i - (int64_t)c * sites;
         const int y = (int)(site / nx), x = (int)(site - (int64_t)y * nx);
         double ux = 0.0, uy = 0.0;
-        const bool solid = x >= ox0 && x < ox1 && y >= oy0 && y < oy1;
-        if (!solid) {
+        if (!sol.at(x, y)) {
             const u64x4 r = philox(kStreamInit, (uint64_t)c, (uint64_t)site, 0u, seed, 0u);
             ux = amp * (2.0 * unit_double(r.v[0]) - 1.0);
             uy = amp * (2.0 * unit_double(r.v[1]) - 1.0);
+            if (u_in != 0.0) {  // open channel: the inlet profile everywhere
+                const double h = ny, yy = y + 0.5;
+                ux += u_in * 4.0 * yy * (h - yy) / (h * h);
+            }
         }
         const double usq = ux * ux + uy * uy;
         T* cell = base + (int64_t)c * clone_stride + (int64_t)y * pitch + x;
@@ -210,8 +218,7 @@ __global__ void first_crossing_kernel(const double* F, int32_t t_lo, int32_t t_h
 template <int S>
 __global__ void moments_partial_kernel(const void* buf0, const void* buf1, const int32_t* parity, const int32_t* list,
                                        int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny,
-                                       int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1, float inv_scale,
-                                       double* partial)
+                                       Solids sol, float inv_scale, double* partial)
 {
     using T = typename Codec<S>::T;
     __shared__ double sh[kRedThreads];
@@ -222,7 +229,7 @@ __global__ void moments_partial_kernel(const void* buf0, const void* buf1, const
     double m = 0.0, px = 0.0, py = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < sites; i += (int64_t)gridDim.x * kRedThreads) {
         const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
-        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1) continue;
+        if (sol.at(x, y)) continue;
         const T* cell = base + (int64_t)y * pitch + x;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -259,8 +266,7 @@ __global__ void moments_final_kernel(const double* partial, int32_t nblocks, con
 // fluid mass of every state in the snapshot bank (fixed-order FP64 partials)
 template <int S>
 __global__ void bank_mass_partial_kernel(const void* snaps, int64_t clone_stride, int64_t plane, int32_t pitch,
-                                         int32_t nx, int32_t ny, int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1,
-                                         float inv_scale, double* partial)
+                                         int32_t nx, int32_t ny, Solids sol, float inv_scale, double* partial)
 {
     using T = typename Codec<S>::T;
     __shared__ double sh[kRedThreads];
@@ -270,7 +276,7 @@ __global__ void bank_mass_partial_kernel(const void* snaps, int64_t clone_stride
     double m = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)kRedThreads + threadIdx.x; i < sites; i += (int64_t)gridDim.x * kRedThreads) {
         const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
-        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1) continue;
+        if (sol.at(x, y)) continue;
         const T* cell = base + (int64_t)y * pitch + x;
 #pragma unroll
         for (int q = 0; q < 9; ++q) m += (double)wf(q) + (double)Codec<S>::dec(cell[q * plane], wf(q), inv_scale);
@@ -294,7 +300,7 @@ template <int S>
 __global__ void perturb_kernel(void* buf0, void* buf1, const int32_t* parity, const int32_t* parent, int32_t n_clones,
                                int32_t* flag, int32_t inplace,
                                int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny,
-                               int32_t ox0, int32_t ox1, int32_t oy0, int32_t oy1, const void* snaps, int32_t n_s,
+                               Solids sol, const void* snaps, int32_t n_s,
                                const double* snap_mass, const double* mass, double eps, uint64_t seed, uint64_t iter,
                                float scale, float inv_scale)
 {
@@ -329,7 +335,7 @@ __global__ void perturb_kernel(void* buf0, void* buf1, const int32_t* parity, co
     const int64_t sites = (int64_t)nx * ny;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sites; i += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(i / nx), x = (int)(i - (int64_t)y * nx);
-        if (x >= ox0 && x < ox1 && y >= oy0 && y < oy1) continue;  // solid: stays at rest
+        if (sol.at(x, y)) continue;  // solid: stays at rest
         const int64_t off = (int64_t)y * pitch + x;
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -379,7 +385,63 @@ int lbm::check_collision(const lbm_config& c)
     return LBM_OK;
 }
 
+int lbm::check_open(const lbm_config& c)
+{
+    if (c.open_x == 0) {
+        if (c.grid_w != 0 || c.sponge_len != 0)
+            return fail(LBM_ERR_ARG, "the entrance grid and the sponge belong to an open channel (open_x = 1)");
+        return LBM_OK;
+    }
+    if (c.open_x != 1) return fail(LBM_ERR_ARG, "open_x must be 0 or 1");
+    if (c.gx != 0.0 || c.gy != 0.0) return fail(LBM_ERR_ARG, "an open channel has no body force (gx = gy = 0)");
+    if (c.ny < 3) return fail(LBM_ERR_ARG, "an open channel needs ny >= 3");
+    if (!(std::fabs(c.u_in) < 0.3)) return fail(LBM_ERR_ARG, "u_in must satisfy |u_in| < 0.3");
+    if (c.obs_w > 0 && c.obs_x0 + c.obs_w > c.nx - 3)
+        return fail(LBM_ERR_ARG, "an open channel's obstacle must end before column nx-3");
+    if (c.grid_w < 0) return fail(LBM_ERR_ARG, "grid_w must be >= 0");
+    if (c.grid_w > 0 && (c.grid_x0 < 1 || c.grid_x0 + c.grid_w > c.nx - 3 || c.grid_bar < 1 || c.grid_gap < 1))
+        return fail(LBM_ERR_ARG, "grid: need 1 <= grid_x0, grid_x0 + grid_w <= nx - 3, grid_bar >= 1, grid_gap >= 1");
+    if (c.sponge_len < 0 || c.sponge_len > c.nx) return fail(LBM_ERR_ARG, "sponge_len must be in [0, nx]");
+    if (c.sponge_len > 0 && !(c.sponge_tau > 0.5)) return fail(LBM_ERR_ARG, "sponge_tau must exceed 1/2");
+    const double tau_out = c.sponge_len > 0 ? c.sponge_tau : c.tau;
+    if (!(tau_out <= 1.0)) return fail(LBM_ERR_ARG, "the relaxation time at the outlet must be at most 1");
+    return LBM_OK;
+}
+
 namespace {
+
+// relaxation time of column x of an open channel (the sponge profile)
+double open_tau(const lbm_config& c, int x)
+{
+    if (c.sponge_len <= 0 || x < c.nx - c.sponge_len) return c.tau;
+    const double s = (double)(x - (c.nx - c.sponge_len) + 1) / c.sponge_len;
+    return c.tau + (c.sponge_tau - c.tau) * s * s;
+}
+
+Solids solids_of(const lbm_config& c)
+{
+    Solids s{};
+    s.ox0 = c.obs_x0;
+    s.oy0 = c.obs_y0;
+    s.ox1 = c.obs_w > 0 ? c.obs_x0 + c.obs_w : c.obs_x0;
+    s.oy1 = c.obs_w > 0 ? c.obs_y0 + c.obs_h : c.obs_y0;
+    if (c.open_x && c.grid_w > 0) {
+        s.gx0 = c.grid_x0;
+        s.gx1 = c.grid_x0 + c.grid_w;
+        s.gap = c.grid_gap;
+        s.period = c.grid_bar + c.grid_gap;
+    } else {
+        s.gx0 = s.gx1 = 0;
+        s.gap = s.period = 1;
+    }
+    return s;
+}
+
+// the launcher of variant v for this ensemble's channel
+StepVariant::Launch launcher(const lbm_ensemble* e, const StepVariant& v)
+{
+    return e->cfg.open_x ? v.launch_open : v.launch;
+}
 
 // vec = 0: row-staged kernels, one slot per consumer warp in each ring row
 Ring ring_for(const lbm_config& c, int vec)
@@ -405,7 +467,7 @@ int default_variant(int storage)
     const auto& v = step_variants();
     const int want_vec = storage == kFP32 ? 4 : 8;
     for (size_t i = 0; i < v.size(); ++i)
-        if (v[i].storage == storage && v[i].vec == want_vec && v[i].warps == 4) return (int)i;
+        if (v[i].storage == storage && v[i].kind == 0 && v[i].vec == want_vec && v[i].warps == 4) return (int)i;
     return -1;
 }
 
@@ -463,6 +525,25 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
     p.scale = e->scale;
     p.inv_scale = e->inv_scale;
     p.step_in_batch = step;
+    const Solids sol = solids_of(c);
+    p.open = c.open_x;
+    p.gx0 = sol.gx0;
+    p.gx1 = sol.gx1;
+    p.ggap = sol.gap;
+    p.gperiod = sol.period;
+    p.gs0 = 1;
+    p.gs1 = 0;
+    p.sx0 = c.nx;
+    if (c.open_x) {
+        if (c.grid_w > 0 && vec > 0) {
+            p.gs0 = (c.grid_x0 - 1) / (32 * vec);
+            p.gs1 = (c.grid_x0 + c.grid_w) / (32 * vec);
+        }
+        if (c.sponge_len > 0) p.sx0 = c.nx - c.sponge_len;
+        p.om_col = e->om_col;
+        p.inlet_g = e->inlet_g;
+        p.bc_pre = (float)(-2.0 / 3.0 * (open_tau(c, c.nx - 1) - 1.0));
+    }
     return p;
 }
 
@@ -487,15 +568,6 @@ int dispatch_storage(int storage, F&& f)
     return fail(LBM_ERR_ARG, "unknown storage");
 }
 
-int solid_bounds(const lbm_config& c, int& ox0, int& ox1, int& oy0, int& oy1)
-{
-    ox0 = c.obs_x0;
-    oy0 = c.obs_y0;
-    ox1 = c.obs_w > 0 ? c.obs_x0 + c.obs_w : c.obs_x0;
-    oy1 = c.obs_w > 0 ? c.obs_y0 + c.obs_h : c.obs_y0;
-    return 0;
-}
-
 // the fused step launches of one chunk: steps 0 .. chunk-1 of a drag batch.
 // With graphs on, the chunk is captured once (on a private stream, so that the
 // caller's stream may be the legacy default stream) and the cached executable
@@ -506,12 +578,15 @@ int solid_bounds(const lbm_config& c, int& ox0, int& ox1, int& oy0, int& oy1)
 int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, int chunk)
 {
     const StepVariant& v = step_variants()[vi];
+    const StepVariant::Launch launch = launcher(e, v);
+    if (!launch) return fail(LBM_ERR_ARG, "the step variant has no open-channel instantiation");
+    const int per_step = e->cfg.open_x ? 2 : 1;  // an open channel adds the boundary-column kernel
     if (!e->use_graphs) {
         for (int s = 0; s < chunk; ++s) {
-            cudaError_t err = v.launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
+            cudaError_t err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
             if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
         }
-        count_launches(chunk);
+        count_launches(chunk * per_step);
         return LBM_OK;
     }
     lbm_ensemble::StepGraph* hit = nullptr;
@@ -522,7 +597,7 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
         LBM_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed));
         cudaError_t launch_err = cudaSuccess;
         for (int s = 0; s < chunk && launch_err == cudaSuccess; ++s)
-            launch_err = v.launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->cap_stream);
+            launch_err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->cap_stream);
         cudaGraph_t graph = nullptr;
         const cudaError_t end_err = cudaStreamEndCapture(e->cap_stream, &graph);
         if (launch_err != cudaSuccess || end_err != cudaSuccess) {
@@ -545,7 +620,7 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
     }
     hit->used = ++e->graph_clock;
     LBM_CUDA(cudaGraphLaunch(hit->exec, e->stream));
-    count_launches(chunk);
+    count_launches(chunk * per_step);
     return LBM_OK;
 }
 
@@ -610,14 +685,13 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
 
 int compute_masses(lbm_ensemble* e, const int32_t* list_dev, int n_list)
 {
-    int ox0, ox1, oy0, oy1;
-    solid_bounds(e->cfg, ox0, ox1, oy0, oy1);
+    const Solids sol = solids_of(e->cfg);
     return dispatch_storage(e->cfg.storage, [&](auto tag) -> int {
         constexpr int S = decltype(tag)::value;
         dim3 grid(e->red_blocks, n_list);
         moments_partial_kernel<S><<<grid, kRedThreads, 0, e->stream>>>(
             e->buf[0], e->buf[1], e->parity_dev, list_dev, e->clone_stride, e->plane, e->pitch, e->cfg.nx, e->cfg.ny,
-            ox0, ox1, oy0, oy1, e->inv_scale, e->red_partials);
+            sol, e->inv_scale, e->red_partials);
         count_launches(1);
         LBM_CUDA(cudaGetLastError());
         moments_final_kernel<<<n_list, 32, 0, e->stream>>>(e->red_partials, e->red_blocks, list_dev, e->mass_dev,
@@ -630,12 +704,11 @@ int compute_masses(lbm_ensemble* e, const int32_t* list_dev, int n_list)
 
 int bank_masses(lbm_ensemble* e, int n_s)
 {
-    int ox0, ox1, oy0, oy1;
-    solid_bounds(e->cfg, ox0, ox1, oy0, oy1);
+    const Solids sol = solids_of(e->cfg);
     return dispatch_storage(e->cfg.storage, [&](auto tag) -> int {
         constexpr int S = decltype(tag)::value;
         bank_mass_partial_kernel<S><<<dim3(e->red_blocks, n_s), kRedThreads, 0, e->stream>>>(
-            e->snaps, e->clone_stride, e->plane, e->pitch, e->cfg.nx, e->cfg.ny, ox0, ox1, oy0, oy1, e->inv_scale,
+            e->snaps, e->clone_stride, e->plane, e->pitch, e->cfg.nx, e->cfg.ny, sol, e->inv_scale,
             e->red_partials);
         LBM_CUDA(cudaGetLastError());
         bank_mass_final_kernel<<<n_s, 32, 0, e->stream>>>(e->red_partials, e->red_blocks, e->snap_mass);
@@ -647,8 +720,7 @@ int bank_masses(lbm_ensemble* e, int n_s)
 
 int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, double eps, uint64_t seed, uint64_t iter)
 {
-    int ox0, ox1, oy0, oy1;
-    solid_bounds(e->cfg, ox0, ox1, oy0, oy1);
+    const Solids sol = solids_of(e->cfg);
     const int n_s = eps != 0.0 ? e->n_snaps_set : 0;
     return dispatch_storage(e->cfg.storage, [&](auto tag) -> int {
         constexpr int S = decltype(tag)::value;
@@ -657,7 +729,7 @@ int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, dou
         dim3 grid(bx, e->n);
         perturb_kernel<S><<<grid, 256, 0, e->stream>>>(
             e->buf[0], e->buf[1], e->parity_dev, parent_dev, e->n, e->flag_dev, inplace, e->clone_stride, e->plane, e->pitch, e->cfg.nx,
-            e->cfg.ny, ox0, ox1, oy0, oy1, e->snaps, n_s, e->snap_mass, e->mass_dev, eps, seed, iter, e->scale,
+            e->cfg.ny, sol, e->snaps, n_s, e->snap_mass, e->mass_dev, eps, seed, iter, e->scale,
             e->inv_scale);
         count_launches(1);
         LBM_CUDA(cudaGetLastError());
@@ -698,7 +770,8 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     if (!cfg || !out) return fail(LBM_ERR_ARG, "null config or output pointer");
     *out = nullptr;
     const lbm_config c = *cfg;
-    if (c.nx < 8 || c.nx % 8 != 0) return fail(LBM_ERR_ARG, "nx must be a positive multiple of 8");
+    if (c.nx < 8 || (c.open_x == 0 && c.nx % 8 != 0))
+        return fail(LBM_ERR_ARG, "nx must be a positive multiple of 8 (any nx >= 8 in an open channel)");
     if (c.ny < 2) return fail(LBM_ERR_ARG, "ny must be at least 2");
     if (n_clones < 1 || n_clones > 65535) return fail(LBM_ERR_ARG, "clone count must be in [1, 65535]");
     if ((int64_t)9 * (((c.nx + 255) / 256) * 256) * c.ny >= ((int64_t)1 << 31))
@@ -717,6 +790,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
         if (c.obs_y0 < 0 || c.obs_y0 + c.obs_h > c.ny) return fail(LBM_ERR_ARG, "obstacle outside the channel");
     }
     if (int rc = check_collision(c)) return rc;
+    if (int rc = check_open(c)) return rc;
     int dev = 0;
     LBM_CUDA(cudaGetDevice(&dev));
     auto* e = new lbm_ensemble();
@@ -772,6 +846,10 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
         ALLOC(e->snap_mass, sizeof(double) * c.n_snapshots);
     }
     if (e->n_ckpt > 0) { ALLOC(e->ckpt, (size_t)e->clone_stride * e->elem_bytes * n_clones * e->n_ckpt); }
+    if (c.open_x) {
+        ALLOC(e->om_col, sizeof(float) * c.nx);
+        ALLOC(e->inlet_g, sizeof(float) * 9 * c.ny);
+    }
 #undef ALLOC
     std::vector<int32_t> iota(n_clones);
     for (int i = 0; i < n_clones; ++i) iota[i] = i;
@@ -785,14 +863,29 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     if ((rc = chk(cudaMemsetAsync(e->buf[1], 0, state_bytes, e->stream), "memset state"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->partials, 0, sizeof(float) * (size_t)n_clones * e->batch_cap * e->n_slots, e->stream), "memset partials"))) return rc;
     if ((rc = chk(cudaMemsetAsync(e->drag, 0, sizeof(double) * (size_t)n_clones * c.max_steps, e->stream), "memset drag"))) return rc;
-    int ox0, ox1, oy0, oy1;
-    solid_bounds(c, ox0, ox1, oy0, oy1);
+    if (c.open_x) {
+        // per-column relaxation rate and the inlet populations (FP64, then FP32)
+        std::vector<float> om(c.nx), inlet(9 * (size_t)c.ny);
+        for (int x = 0; x < c.nx; ++x) om[x] = (float)(1.0 / open_tau(c, x));
+        for (int y = 0; y < c.ny; ++y) {
+            const double h = c.ny, yy = y + 0.5, u = c.u_in * 4.0 * yy * (h - yy) / (h * h);
+            for (int q = 0; q < 9; ++q) {
+                const double cu = cx(q) * u;
+                inlet[(size_t)q * c.ny + y] = (float)(wd(q) * (3.0 * cu + 4.5 * cu * cu - 1.5 * u * u));
+            }
+        }
+        if ((rc = chk(cudaMemcpyAsync(e->om_col, om.data(), sizeof(float) * c.nx, cudaMemcpyHostToDevice, e->stream), "copy sponge rates"))) return rc;
+        if ((rc = chk(cudaMemcpyAsync(e->inlet_g, inlet.data(), sizeof(float) * inlet.size(), cudaMemcpyHostToDevice, e->stream), "copy inlet"))) return rc;
+        // the copies read pageable host memory: wait before the vectors go
+        if ((rc = chk(cudaStreamSynchronize(e->stream), "open-channel tables"))) return rc;
+    }
+    const Solids sol = solids_of(c);
     rc = dispatch_storage(c.storage, [&](auto tag) -> int {
         constexpr int S = decltype(tag)::value;
         const int64_t total = (int64_t)c.nx * c.ny * n_clones;
         const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
         init_kernel<S><<<grid, 256, 0, e->stream>>>(e->buf[0], e->clone_stride, e->plane, e->pitch, c.nx, c.ny,
-                                                    n_clones, ox0, ox1, oy0, oy1, seed, c.init_amp, e->scale);
+                                                    n_clones, sol, seed, c.init_amp, c.open_x ? c.u_in : 0.0, e->scale);
         count_launches(1);
         return chk(cudaGetLastError(), "init kernel");
     });
@@ -824,7 +917,7 @@ int lbm_ensemble_destroy(lbm_ensemble* e)
     void* ptrs[] = {e->buf[0], e->buf[1], e->parity_dev, e->t_dev, e->list_dev, e->all_dev, e->partials,
                     e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt,
                     e->fields_list_dev, e->cnn_x, e->cnn_pred, e->cnn_score, e->pot[0], e->pot[1], e->pot[2],
-                    e->pot_tmp[0], e->pot_tmp[1]};
+                    e->pot_tmp[0], e->pot_tmp[1], e->om_col, e->inlet_g};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete e;
@@ -1127,6 +1220,7 @@ int lbm_ensemble_set_variant(lbm_ensemble* e, int32_t variant)
     const auto& v = step_variants();
     if (variant < 0 || variant >= (int32_t)v.size()) return fail(LBM_ERR_ARG, "variant index out of range");
     if (v[variant].storage != e->cfg.storage) return fail(LBM_ERR_ARG, "variant is for another storage format");
+    if (!launcher(e, v[variant])) return fail(LBM_ERR_ARG, "the variant has no open-channel instantiation");
     e->variant = variant;  // a forced variant runs every step call
     e->variant_small = variant;
     return LBM_OK;
@@ -1146,14 +1240,16 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
         for (size_t i = 0; i < vars.size(); ++i) {
             const StepVariant& v = vars[i];
             if (v.storage != e->cfg.storage) continue;
+            const StepVariant::Launch launch = launcher(e, v);
+            if (!launch) continue;
             StepParams p = make_params(e, e->all_dev, n_list, v.vec, 0, v.kind);
             if (v.supports && !v.supports(p)) continue;
             for (int r = 0; r < 2; ++r)
-                if (v.launch(p, e->stream) != cudaSuccess) return -1;
+                if (launch(p, e->stream) != cudaSuccess) return -1;
             cudaEventRecord(a, e->stream);
             for (int r = 0; r < reps; ++r)
-                if (v.launch(p, e->stream) != cudaSuccess) return -1;
-            count_launches(2 + reps);
+                if (launch(p, e->stream) != cudaSuccess) return -1;
+            count_launches((2 + reps) * (e->cfg.open_x ? 2 : 1));
             cudaEventRecord(b, e->stream);
             if (cudaEventSynchronize(b) != cudaSuccess) return -1;
             float ms = 0.f;

@@ -155,7 +155,28 @@ __device__ __forceinline__ void collide(float (&g)[9][V], int j, const StepParam
         cm_collide<V>(g, j, p.bgk, p.cm);
 }
 
-template <int S, int V, bool GENERAL, bool SCALED, int COLL>
+// the same collision at the relaxation rate om of a sponge column (open
+// channel, Sec. 2: no body force, so only the rate-dependent constants change;
+// the central-moment collision relaxes the shear moments at om)
+template <int COLL, int V>
+__device__ __forceinline__ void collide_at(float (&g)[9][V], int j, const StepParams& p, float om)
+{
+    BgkConsts k = p.bgk;
+    k.om = om;
+    k.omm = 1.0f - om;
+    k.om3 = 3.0f * om;
+    if constexpr (COLL == 0) {
+        bgk_collide<V>(g, j, k);
+    } else {
+        CmConsts m = p.cm;
+        m.ws = om;
+        m.a = 0.5f * (m.wb + om);
+        m.b = 0.5f * (m.wb - om);
+        cm_collide<V>(g, j, k, m);
+    }
+}
+
+template <int S, int V, bool GENERAL, bool SCALED, int COLL, bool OPEN>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
                                           typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
 {
@@ -226,7 +247,33 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
             g[q][V - 1] = e;
         }
     }
-    if (GENERAL && ox1 > ox0) {
+    if constexpr (OPEN) {
+        if (GENERAL) {
+            // links whose upstream node is solid (the square, or a bar of the
+            // open channel's grid) bounce back at this node
+#pragma unroll
+            for (int q = 1; q < 9; ++q) {
+                const int ex = cx(q), ys = y - cy(q);
+                const bool sq_row = ys >= oy0 && ys < oy1;
+                const bool grid_row = ys >= 0 && ys < p.ny && ys % p.gperiod >= p.ggap;
+                if (!sq_row && !grid_row) continue;
+                bool hit[V];
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < V; ++j) {
+                    const int xs = x0 + j - ex;
+                    hit[j] = (sq_row && xs >= ox0 && xs < ox1) || (grid_row && xs >= p.gx0 && xs < p.gx1);
+                    any |= hit[j];
+                }
+                if (any) {
+                    const Vec<T, V> o = ld_stream<T, V>(src + opp(q) * plane + row + x0);
+#pragma unroll
+                    for (int j = 0; j < V; ++j)
+                        if (hit[j]) g[q][j] = K::in(o.e[j], wf(q), p.inv_scale);
+                }
+            }
+        }
+    } else if (GENERAL && ox1 > ox0) {
         // links whose upstream node is solid bounce back at this node
 #pragma unroll
         for (int q = 1; q < 9; ++q) {
@@ -250,8 +297,47 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
     }
 
     // ---- phase 3: BGK collision with Guo forcing
+    if constexpr (OPEN) {
+        if (x0 + V > p.sx0) {
+            // a segment reaching into the sponge: the rate of each column
 #pragma unroll
-    for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
+            for (int j = 0; j < V; ++j) {
+                const int x = x0 + j;
+                if (x >= p.sx0 && x < p.nx)
+                    collide_at<COLL, V>(g, j, p, __ldg(p.om_col + x));
+                else
+                    collide<COLL, V>(g, j, p);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
+    }
+    if constexpr (OPEN) {
+        if (GENERAL && y % p.gperiod >= p.ggap) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int x = x0 + j;
+                if (x >= p.gx0 && x < p.gx1) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) g[q][j] = 0.f;  // a bar of the grid: rest state
+                }
+            }
+        }
+        // an open channel's nx need not be a multiple of V: sites past the
+        // last column (row padding) are kept at rest
+        if (x0 + V > p.nx) {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if (x0 + j >= p.nx) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) g[q][j] = 0.f;
+                }
+        }
+    }
 
     if (GENERAL && ox1 > ox0) {
         if (y >= oy0 && y < oy1) {
@@ -308,7 +394,7 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
     }
 }
 
-template <int S, int V, int WARPS, bool SCALED, int COLL>
+template <int S, int V, int WARPS, bool SCALED, int COLL, bool OPEN = false>
 __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
 {
     using T = typename Codec<S>::T;
@@ -322,10 +408,18 @@ __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
     T* dst = static_cast<T*>(cur ? p.buf0 : p.buf1) + (int64_t)c * p.clone_stride;
     const bool wall_row = y == 0 || y == p.ny - 1;
     const bool ring = p.ox1 > p.ox0 && y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1;
-    if (wall_row || ring)
-        step_warp<S, V, true, SCALED, COLL>(p, src, dst, c, y, seg, lane);
-    else
-        step_warp<S, V, false, SCALED, COLL>(p, src, dst, c, y, seg, lane);
+    if constexpr (OPEN) {
+        const bool grid = seg >= p.gs0 && seg <= p.gs1;  // segments around the entrance grid
+        if (wall_row || ring || grid)
+            step_warp<S, V, true, SCALED, COLL, true>(p, src, dst, c, y, seg, lane);
+        else
+            step_warp<S, V, false, SCALED, COLL, true>(p, src, dst, c, y, seg, lane);
+    } else {
+        if (wall_row || ring)
+            step_warp<S, V, true, SCALED, COLL, false>(p, src, dst, c, y, seg, lane);
+        else
+            step_warp<S, V, false, SCALED, COLL, false>(p, src, dst, c, y, seg, lane);
+    }
 }
 
 template <int S, int V, int WARPS>
@@ -348,6 +442,114 @@ cudaError_t launch_step(const StepParams& p, cudaStream_t s)
         go(std::integral_constant<int, 1>{});
     else
         go(std::integral_constant<int, 0>{});
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- open channel
+// Boundary columns of the open channel (Sec. 2), written into the state a
+// step launch has just produced (post-collision populations), one thread per
+// (row, listed clone):
+//   inlet  x = 0:      f = f^eq(rho = 1, (u_in(y), 0)), precomputed in FP64 on
+//                      the host (p.inlet_g holds f - w);
+//   outlet x = nx-1:   rho = 1 and u = 2 u(nx-2) - u(nx-3), the populations
+//                      regularized (Latt et al. 2008):
+//                      f = f^eq(1, u) + w_q / (2 cs2^2) Q_q : Pi,  Q_q = c_q c_q - cs2 I,
+//                      Pi = bc_pre * S,  bc_pre = -2 cs2 (tau(nx-1) - 1),
+//                      S the strain rate by finite differences: x one-sided from
+//                      the two upstream columns, y central on the extrapolated
+//                      column (one-sided on the wall rows).
+// The velocity of a post-collision state is sum c f / sum f (no body force).
+template <int S, bool SCALED>
+__device__ __forceinline__ void open_velocity(const typename Codec<S>::T* col, int64_t plane, float inv_scale,
+                                              float& ux, float& uy)
+{
+    using K = Carry<S, SCALED>;
+    float g[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) g[q] = K::in(col[q * plane], wf(q), inv_scale);
+    const float drho = (g[0] + (g[1] + g[3])) + ((g[2] + g[4]) + ((g[5] + g[7]) + (g[6] + g[8])));
+    const float jx = (g[1] - g[3]) + ((g[5] - g[7]) - (g[6] - g[8]));
+    const float jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+    const float inv = 1.0f / (1.0f + drho);
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
+template <int S, bool SCALED>
+__global__ void open_bc_kernel(const StepParams p)
+{
+    using T = typename Codec<S>::T;
+    using K = Carry<S, SCALED>;
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= p.ny) return;
+    const int c = p.clone_list[blockIdx.y];
+    const int cur = p.parity[c] ^ (p.step_in_batch & 1);
+    T* st = static_cast<T*>(cur ? p.buf0 : p.buf1) + (int64_t)c * p.clone_stride;
+    const int64_t plane = p.plane;
+    // inlet column
+#pragma unroll
+    for (int q = 0; q < 9; ++q) st[q * plane + (int64_t)y * p.pitch] = K::out(p.inlet_g[q * p.ny + y], wf(q), p.scale);
+    // outlet column: extrapolated velocity of rows y-1, y, y+1 (clamped)
+    const int ym = y > 0 ? y - 1 : y, yp = y < p.ny - 1 ? y + 1 : y;
+    float ex[3], ey[3], dxux = 0.f, dxuy = 0.f;
+    const int rows[3] = {ym, y, yp};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const T* r = st + (int64_t)rows[k] * p.pitch;
+        float u2, v2, u3, v3;
+        open_velocity<S, SCALED>(r + (p.nx - 2), plane, p.inv_scale, u2, v2);
+        open_velocity<S, SCALED>(r + (p.nx - 3), plane, p.inv_scale, u3, v3);
+        ex[k] = 2.0f * u2 - u3;
+        ey[k] = 2.0f * v2 - v3;
+        if (k == 1) {
+            dxux = u2 - u3;
+            dxuy = v2 - v3;
+        }
+    }
+    const float inv_dy = 1.0f / (float)(yp - ym);
+    const float dyux = (ex[2] - ex[0]) * inv_dy, dyuy = (ey[2] - ey[0]) * inv_dy;
+    const float pxx = p.bc_pre * dxux, pyy = p.bc_pre * dyuy, pxy = p.bc_pre * 0.5f * (dyux + dxuy);
+    const float ux = ex[1], uy = ey[1];
+    const float u2 = ux * ux + uy * uy;
+    T* o = st + (int64_t)y * p.pitch + (p.nx - 1);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float cxq = (float)cx(q), cyq = (float)cy(q);
+        const float cu = cxq * ux + cyq * uy;
+        const float qp = (cxq * cxq - (1.0f / 3.0f)) * pxx + 2.0f * cxq * cyq * pxy + (cyq * cyq - (1.0f / 3.0f)) * pyy;
+        const float gq = wf(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * u2 + 4.5f * qp);
+        o[q * plane] = K::out(gq, wf(q), p.scale);
+    }
+}
+
+// one step of an open channel: the fused step (OPEN instantiation) and the
+// boundary columns, on the same stream
+template <int S, int V, int WARPS>
+cudaError_t launch_step_open(const StepParams& p, cudaStream_t s)
+{
+    const dim3 block(32, WARPS);
+    const dim3 grid(p.nseg, (p.ny + WARPS - 1) / WARPS, p.n_list);
+    const dim3 bc_grid((p.ny + 127) / 128, p.n_list);
+    auto go = [&](auto coll, auto scaled) {
+        constexpr int C = decltype(coll)::value;
+        constexpr bool SC = decltype(scaled)::value;
+        step_kernel<S, V, WARPS, SC, C, true><<<grid, block, 0, s>>>(p);
+        open_bc_kernel<S, SC><<<bc_grid, 128, 0, s>>>(p);
+    };
+    auto by_scale = [&](auto coll) {
+        if constexpr (S == kFP32) {
+            go(coll, std::false_type{});
+        } else {
+            if (p.scale != 1.0f)
+                go(coll, std::true_type{});
+            else
+                go(coll, std::false_type{});
+        }
+    };
+    if (p.coll == 1)
+        by_scale(std::integral_constant<int, 1>{});
+    else
+        by_scale(std::integral_constant<int, 0>{});
     return cudaGetLastError();
 }
 

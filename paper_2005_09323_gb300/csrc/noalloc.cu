@@ -65,6 +65,8 @@ extern "C" int lbm_step_noalloc(const lbm_config* cfg, int32_t n_clones, const v
         return fail(LBM_ERR_ARG, "lbm_step_noalloc: obstacle outside the allowed region");
     if (f_in_dev == f_out_dev) return fail(LBM_ERR_ARG, "lbm_step_noalloc: input and output must differ");
     if (int rc = check_collision(c)) return rc;
+    if (c.open_x != 0) return fail(LBM_ERR_ARG, "lbm_step_noalloc: open channels step through an ensemble only");
+    if (int rc = check_open(c)) return rc;  // a periodic channel carries no grid or sponge
     const int32_t pitch = ((c.nx + 255) / 256) * 256;
     if ((int64_t)9 * pitch * c.ny >= ((int64_t)1 << 31))
         return fail(LBM_ERR_ARG, "lbm_step_noalloc: one clone must hold fewer than 2^31 population values");

@@ -99,6 +99,15 @@ struct StepParams {
     BgkConsts bgk;              // bgk_consts(omega, gx, gy)
     int32_t coll;               // 0: BGK; 1: central-moment collision with cm
     CmConsts cm;
+    // open channel (Sec. 2; launched through the open-channel instantiations
+    // only): the grid of bars, the sponge and the two boundary columns
+    int32_t open;               // 1: open channel
+    int32_t gx0, gx1, ggap, gperiod;  // grid cells x in [gx0, gx1), y mod gperiod >= ggap
+    int32_t gs0, gs1;           // segments whose warps take the general path for the grid
+    int32_t sx0;                // first sponge column (nx: no sponge)
+    const float* om_col;        // [nx] relaxation rate 1/tau(x) of each column
+    const float* inlet_g;       // [9][ny] inlet populations minus w_q (FP32 of the FP64 values)
+    float bc_pre;               // outlet stress factor -2 cs2 (tau(nx-1) - 1)
 };
 
 // consumer warps of the row-staged step kernel; each writes its own drag

@@ -51,7 +51,9 @@ class lbm_config(C.Structure):
                 ("gy", C.c_double), ("storage", C.c_int32), ("shift_exp", C.c_int32), ("max_steps", C.c_int32),
                 ("ckpt_stride", C.c_int32), ("n_snapshots", C.c_int32), ("init_amp", C.c_double),
                 ("collision", C.c_int32), ("omega_bulk", C.c_double), ("omega_3", C.c_double),
-                ("omega_4", C.c_double)]
+                ("omega_4", C.c_double), ("open_x", C.c_int32), ("u_in", C.c_double), ("grid_x0", C.c_int32),
+                ("grid_w", C.c_int32), ("grid_bar", C.c_int32), ("grid_gap", C.c_int32), ("sponge_len", C.c_int32),
+                ("sponge_tau", C.c_double)]
 
 
 class lbm_gktl_params(C.Structure):
@@ -71,14 +73,19 @@ COLLISION = {"bgk": 0, "cm": 1}
 
 def config(nx, ny, obstacle=(0, 0, 0, 0), tau=0.6, gx=0.0, gy=0.0, storage="fp32", shift_exp=0,
            max_steps=1000, ckpt_stride=0, n_snapshots=0, init_amp=0.01, collision="bgk", omega_bulk=1.0,
-           omega_3=1.0, omega_4=1.0) -> lbm_config:
+           omega_3=1.0, omega_4=1.0, open_x=0, u_in=0.0, grid=(0, 0, 0, 0), sponge_len=0,
+           sponge_tau=1.0) -> lbm_config:
     """collision "bgk" or "cm" (central moments: shear at 1/tau, the bulk,
-    third- and fourth-order central moments at omega_bulk, omega_3, omega_4)"""
+    third- and fourth-order central moments at omega_bulk, omega_3, omega_4);
+    open_x = 1: open channel with centreline inlet velocity u_in, entrance
+    grid (x0, width, bar, gap) and a sponge over the last sponge_len columns"""
     ox0, oy0, ow, oh = obstacle
+    gx0, gw, gbar, ggap = grid
     st = STORAGE[storage] if isinstance(storage, str) else int(storage)
     co = COLLISION[collision] if isinstance(collision, str) else int(collision)
     return lbm_config(nx, ny, ox0, oy0, ow, oh, tau, gx, gy, st, shift_exp, max_steps, ckpt_stride,
-                      n_snapshots, init_amp, co, omega_bulk, omega_3, omega_4)
+                      n_snapshots, init_amp, co, omega_bulk, omega_3, omega_4, open_x, u_in, gx0, gw, gbar, ggap,
+                      sponge_len, sponge_tau)
 
 
 _lib = None
