@@ -47,16 +47,39 @@ WORKLOADS = {
                    name="Direct sampling (Sec. 3): N={n} independent trajectories, D2Q9 LBGK {st}, 1024x256, "
                         "32x32 obstacle at x=256, tau=0.505, g_x=1e-06, 500 steps per step; drag autocorrelation "
                         "and waiting-time return times over the run"),
+    "open": dict(nx=513, ny=129, clones=64, side=16, cloning=False, open=True,
+                 name="Open channel of Sec. 2: N={n} independent trajectories, D2Q9 {st}, 513x129, 16x16 square at "
+                      "the centre, entrance grid of 8-row bars every 16 rows at x=16..23, parabolic inlet u_c=0.05, "
+                      "regularized outlet, sponge of 64 columns up to tau=1, tau=0.501 (Re_grid=1200), 500 steps "
+                      "per step; drag autocorrelation and waiting-time return times over the run"),
 }
+# open channel of Sec. 2: Re_grid = u_c (R/2) / nu = 1200 with u_c = 0.05, R = 16
+OPEN_UC = 0.05
+OPEN_TAU = 0.5 + 3.0 * OPEN_UC * 8 / 1200
+OPEN_GRID = (16, 8, 8, 8)     # x0, width, bar rows, gap rows
+OPEN_SPONGE = (64, 1.0)       # columns, tau at the outlet
 
 
 def workload(args):
     w = dict(WORKLOADS[args.workload])
     w["clones"] = args.clones or w["clones"]
     nx, ny, side = w["nx"], w["ny"], w["side"]
-    w["obst"] = (nx // 4 - side // 2, ny // 2 - side // 2, side, side)
-    w["collision"] = getattr(args, "collision", "bgk")
+    if w.get("open"):  # the square at the centre of the channel
+        w["obst"] = (nx // 2 - side // 2, ny // 2 - side // 2, side, side)
+    else:
+        w["obst"] = (nx // 4 - side // 2, ny // 2 - side // 2, side, side)
+    coll = getattr(args, "collision", None)
+    w["collision"] = coll or ("cm" if w.get("open") else "bgk")
     return w
+
+
+def channel_kwargs(w) -> dict:
+    """geometry and flow of the workload's channel, in the keywords that the
+    library's config() and the oracle's cfg() share"""
+    if w.get("open"):
+        return dict(tau=OPEN_TAU, gx=0.0, open_x=1, u_in=OPEN_UC, grid=OPEN_GRID, sponge_len=OPEN_SPONGE[0],
+                    sponge_tau=OPEN_SPONGE[1])
+    return dict(tau=TAU, gx=GX)
 EPS, N_SNAP = 0.002, 10
 K_SIGMA = 1.0
 SIGMA_DRAG = 1e-3        # drag scale used to set k (k = K_SIGMA / (SIGMA_DRAG * PERIOD))
@@ -68,11 +91,15 @@ METRIC = "Ensemble D2Q9 GLUPS & HBM-roofline fraction; time-to-return-time vs pl
 NCU_TRAFFIC = {
     ("gktl", "step_kernel<fp32, vec=4, warps=4>"): {
         "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp32.cu"),
-        "sha": "b014b575bcce569b", "bytes_per_site": 68.4726},
+        "sha": "efa4e050eb183a31", "bytes_per_site": 68.4732},
     ("precision", "step_rows_kernel<fp16, vec=4, warps=9>"): {
         "files": ("lbm_step_rows.cuh", "async_copy.cuh", "lbm_step.cuh", "lbm_device.cuh", "step_params.h",
                   "step_fp16.cu"),
-        "sha": "67c4d5757ae86952", "bytes_per_site": 32.5216},
+        "sha": "31f95bcc172e200e", "bytes_per_site": 32.5047},
+    # both kernels of an open-channel step (the step kernel and the outlet kernel)
+    ("open", "step_kernel<fp32, vec=2, warps=8, open> + open_bc_kernel"): {
+        "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_open_fp32.cu"),
+        "sha": "7e16c141d726f006", "bytes_per_site": 59.0499},
 }
 
 
@@ -175,10 +202,10 @@ class Clocks:
 
 # ---------------------------------------------------------------- CPU oracle
 def _oracle_worker(args):
-    steps, seed, barrier, nx, ny, obst, collision = args
+    steps, seed, barrier, nx, ny, obst, collision, chan = args
     sys.path.insert(0, ROOT)
     import oracle
-    c = oracle.cfg(nx, ny, obstacle=obst, tau=TAU, gx=GX, collision=1 if collision == "cm" else 0)
+    c = oracle.cfg(nx, ny, obstacle=obst, collision=1 if collision == "cm" else 0, **chan)
     f = oracle.init(c, seed, 0, 0.01)
     if barrier is not None:
         barrier.wait()
@@ -193,7 +220,7 @@ def oracle_rate(steps_per_proc: int, procs: int, w):
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
-    geo = (w["nx"], w["ny"], w["obst"], w.get("collision", "bgk"))
+    geo = (w["nx"], w["ny"], w["obst"], w.get("collision", "bgk"), channel_kwargs(w))
     if procs == 1:
         dt = _oracle_worker((steps_per_proc, 0, None) + geo)
         times = [dt]
@@ -252,7 +279,7 @@ def workload_config(args):
            "parallelism": f"replicas x{args.gpus}"}
     if w["cloning"]:
         cfg.update({"k_sigma": K_SIGMA, "eps": EPS, "n_snapshots": N_SNAP})
-    if args.collision == "cm":
+    if w["collision"] == "cm":
         cfg["workload"] += ", central-moment collision (shear 1/tau, bulk/3rd/4th-order rates 1)"
         cfg["collision"] = "central moments"
     return cfg
@@ -294,8 +321,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     total_periods = args.warmup + args.steps + 2 * (args.warmup + args.steps) + 2
     nx, ny = w["nx"], w["ny"]
-    cfg = L.config(nx, ny, obstacle=w["obst"], tau=TAU, gx=GX, max_steps=PERIOD * total_periods,
-                   n_snapshots=N_SNAP, init_amp=0.01, storage=args.storage, collision=args.collision)
+    cfg = L.config(nx, ny, obstacle=w["obst"], max_steps=PERIOD * total_periods, n_snapshots=N_SNAP, init_amp=0.01,
+                   storage=args.storage, collision=w["collision"], **channel_kwargs(w))
     n_clones = w["clones"]
     e = L.lbm_ensemble_create(cfg, n_clones, replica_seed(rank), stream)
     if args.variant == "auto":
@@ -304,6 +331,8 @@ def run_ours(args):
         variant = int(args.variant)
         L.lbm_ensemble_set_variant(e, variant)
     label = kernel_label(L, variant, args.storage)
+    if w.get("open"):  # the open instantiation, with the outlet kernel in each timed step
+        label = label[:-1] + ", open> + open_bc_kernel"
     k = K_SIGMA / (SIGMA_DRAG * PERIOD)
     s = torch.zeros(n_clones, dtype=torch.float64, device="cuda")
     W = torch.zeros_like(s)
@@ -390,7 +419,7 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t_e2e
 
     direct = None
-    if args.workload == "direct":  # statistics of the whole run after the first period (Sec. 3)
+    if args.workload in ("direct", "open"):  # statistics of the run after the first period (Sec. 3)
         t0s, t1s = PERIOD, state["t"]
         lag = min(2000, t1s - t0s - 1)
         cdev = torch.zeros(lag + 1, dtype=torch.float64, device="cuda")
@@ -406,7 +435,8 @@ def run_ours(args):
                   "return_times": [{"level": f"mean + {z:g} std", "events": int(n_ev),
                                     "r_steps": (None if not np.isfinite(r) else float(r))}
                                    for z, n_ev, r in zip(zs, ev, rt)],
-                  "note": "flow accelerating from rest under g_x: not stationary over the run"}
+                  "note": ("flow developing from the inlet profile over the run: not yet stationary"
+                           if w.get("open") else "flow accelerating from rest under g_x: not stationary over the run")}
 
     L.lbm_ensemble_destroy(e)
 
@@ -865,8 +895,9 @@ def main():
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
     ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
-    ap.add_argument("--collision", default="bgk", choices=["bgk", "cm"],
-                    help="gktl/precision/ams workloads: BGK or the central-moment collision")
+    ap.add_argument("--collision", default=None, choices=["bgk", "cm"],
+                    help="BGK or the central-moment collision (default: central moments for the open "
+                         "channel, BGK otherwise)")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()

@@ -542,6 +542,10 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
         if (c.sponge_len > 0) p.sx0 = c.nx - c.sponge_len;
         p.om_col = e->om_col;
         p.inlet_g = e->inlet_g;
+        p.open_u = e->open_u;
+        // the outlet column is the boundary kernel's: a row segment that would
+        // hold it alone is not launched
+        p.nseg = std::max(1, (c.nx - 1 + 32 * vec - 1) / (32 * vec));
         p.bc_pre = (float)(-2.0 / 3.0 * (open_tau(c, c.nx - 1) - 1.0));
     }
     return p;
@@ -580,7 +584,7 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
     const StepVariant& v = step_variants()[vi];
     const StepVariant::Launch launch = launcher(e, v);
     if (!launch) return fail(LBM_ERR_ARG, "the step variant has no open-channel instantiation");
-    const int per_step = e->cfg.open_x ? 2 : 1;  // an open channel adds the boundary-column kernel
+    const int per_step = e->cfg.open_x ? 2 : 1;  // an open channel adds the outlet kernel
     if (!e->use_graphs) {
         for (int s = 0; s < chunk; ++s) {
             cudaError_t err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
@@ -849,6 +853,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     if (c.open_x) {
         ALLOC(e->om_col, sizeof(float) * c.nx);
         ALLOC(e->inlet_g, sizeof(float) * 9 * c.ny);
+        ALLOC(e->open_u, sizeof(float) * 4 * c.ny * (size_t)n_clones);
     }
 #undef ALLOC
     std::vector<int32_t> iota(n_clones);
@@ -917,7 +922,7 @@ int lbm_ensemble_destroy(lbm_ensemble* e)
     void* ptrs[] = {e->buf[0], e->buf[1], e->parity_dev, e->t_dev, e->list_dev, e->all_dev, e->partials,
                     e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt,
                     e->fields_list_dev, e->cnn_x, e->cnn_pred, e->cnn_score, e->pot[0], e->pot[1], e->pot[2],
-                    e->pot_tmp[0], e->pot_tmp[1], e->om_col, e->inlet_g};
+                    e->pot_tmp[0], e->pot_tmp[1], e->om_col, e->inlet_g, e->open_u};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete e;

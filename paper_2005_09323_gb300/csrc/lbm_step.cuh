@@ -176,6 +176,18 @@ __device__ __forceinline__ void collide_at(float (&g)[9][V], int j, const StepPa
     }
 }
 
+// velocity sum c f / sum f of a node from its carried values g = f - w (no
+// body force: the velocity of a post-collision state of an open channel)
+__device__ __forceinline__ void open_velocity9(const float (&g)[9], float& ux, float& uy)
+{
+    const float drho = (g[0] + (g[1] + g[3])) + ((g[2] + g[4]) + ((g[5] + g[7]) + (g[6] + g[8])));
+    const float jx = (g[1] - g[3]) + ((g[5] - g[7]) - (g[6] - g[8]));
+    const float jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
+    const float inv = 1.0f / (1.0f + drho);
+    ux = jx * inv;
+    uy = jy * inv;
+}
+
 template <int S, int V, bool GENERAL, bool SCALED, int COLL, bool OPEN>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
                                           typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
@@ -202,7 +214,16 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
             plane_q = opp(q);
         }
         const T* rp = src + plane_q * plane + srow * p.pitch;
-        v[q] = ld_stream<T, V>(rp + x0);
+        if constexpr (OPEN) {
+            // lanes past the last column (nx need not be a multiple of 32 V)
+            // feed only the outlet column, which the boundary kernel rewrites
+            if (active)
+                v[q] = ld_stream<T, V>(rp + x0);
+            else
+                v[q] = Vec<T, V>{};
+        } else {
+            v[q] = ld_stream<T, V>(rp + x0);
+        }
         if (ex == 1) {
             const int xs = x0 == 0 ? p.nx - 1 : x0 - 1;
             if (lane == 0 || x0 == 0) edge[q] = ld_one(rp + xs);
@@ -298,19 +319,13 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
 
     // ---- phase 3: BGK collision with Guo forcing
     if constexpr (OPEN) {
-        if (x0 + V > p.sx0) {
-            // a segment reaching into the sponge: the rate of each column
+        // one collision body per site: the rate of a sponge column, else 1/tau
+        const bool sponge = x0 + V > p.sx0;
 #pragma unroll
-            for (int j = 0; j < V; ++j) {
-                const int x = x0 + j;
-                if (x >= p.sx0 && x < p.nx)
-                    collide_at<COLL, V>(g, j, p, __ldg(p.om_col + x));
-                else
-                    collide<COLL, V>(g, j, p);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
+        for (int j = 0; j < V; ++j) {
+            const int x = x0 + j;
+            const float om = sponge && x >= p.sx0 && x < p.nx ? __ldg(p.om_col + x) : p.bgk.om;
+            collide_at<COLL, V>(g, j, p, om);
         }
     } else {
 #pragma unroll
@@ -327,6 +342,11 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
                 }
             }
         }
+        // the inlet column holds the equilibrium of the inlet profile
+        if (x0 == 0) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) g[q][0] = __ldg(p.inlet_g + q * p.ny + y);
+        }
         // an open channel's nx need not be a multiple of V: sites past the
         // last column (row padding) are kept at rest
         if (x0 + V > p.nx) {
@@ -336,6 +356,24 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
 #pragma unroll
                     for (int q = 0; q < 9; ++q) g[q][j] = 0.f;
                 }
+        }
+        // the velocities of columns nx-2 and nx-3 as they are stored (encoded
+        // and decoded), from which the boundary kernel extrapolates the outlet
+        if (x0 + V > p.nx - 3 && x0 <= p.nx - 2) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const int x = x0 + j;
+                if (x == p.nx - 2 || x == p.nx - 3) {
+                    float h[9];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) h[q] = K::in(K::out(g[q][j], wf(q), p.scale), wf(q), p.inv_scale);
+                    float ux, uy;
+                    open_velocity9(h, ux, uy);
+                    float* u = p.open_u + ((int64_t)blockIdx.z * 4 + (x == p.nx - 2 ? 0 : 2)) * p.ny + y;
+                    u[0] = ux;
+                    u[p.ny] = uy;
+                }
+            }
         }
     }
 
@@ -394,6 +432,59 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
     }
 }
 
+// ---------------------------------------------------------------- open channel
+// Boundary columns of the open channel (Sec. 2), in the state a step launch
+// produces (post-collision populations):
+//   inlet  x = 0:      f = f^eq(rho = 1, (u_in(y), 0)): the step kernel's
+//                      thread for x = 0 stores p.inlet_g (FP64 on the host,
+//                      then FP32) instead of its collision result;
+//   outlet x = nx-1:   rho = 1 and u = 2 u(nx-2) - u(nx-3), the populations
+//                      regularized (Latt et al. 2008):
+//                      f = f^eq(1, u) + w_q / (2 cs2^2) Q_q : Pi,  Q_q = c_q c_q - cs2 I,
+//                      Pi = bc_pre * S,  bc_pre = -2 cs2 (tau(nx-1) - 1),
+//                      S the strain rate by finite differences: x one-sided from
+//                      the two upstream columns, y central on the extrapolated
+//                      column (one-sided on the wall rows).
+// The threads that own columns nx-2 and nx-3 leave their velocities (as
+// stored) in p.open_u ([list index][ux(nx-2), uy(nx-2), ux(nx-3), uy(nx-3)][ny]),
+// and open_bc_kernel, launched after the step on the same stream, writes the
+// outlet column from them: four coalesced floats per row.  A row segment that
+// would hold column nx-1 alone is not launched.  (Writing the outlet from the
+// block that finishes last for each clone instead, with an arrival counter,
+// measured slower: every block waits at a barrier before it can retire, and
+// the last clone's outlet lands on the kernel's tail.)
+
+// outlet populations of row y of listed clone li, into the state st
+template <int S, bool SCALED>
+__device__ __forceinline__ void open_outlet_row(const StepParams& p, typename Codec<S>::T* st, int li, int y)
+{
+    using K = Carry<S, SCALED>;
+    const float* u = p.open_u + (int64_t)li * 4 * p.ny;
+    const int ym = y > 0 ? y - 1 : y, yp = y < p.ny - 1 ? y + 1 : y;
+    // written by the step kernel just before (L2 loads)
+    const float u2 = __ldcg(u + y), v2 = __ldcg(u + p.ny + y), u3 = __ldcg(u + 2 * p.ny + y),
+                v3 = __ldcg(u + 3 * p.ny + y);
+    const float exm = 2.0f * __ldcg(u + ym) - __ldcg(u + 2 * p.ny + ym);
+    const float exp_ = 2.0f * __ldcg(u + yp) - __ldcg(u + 2 * p.ny + yp);
+    const float eym = 2.0f * __ldcg(u + p.ny + ym) - __ldcg(u + 3 * p.ny + ym);
+    const float eyp = 2.0f * __ldcg(u + p.ny + yp) - __ldcg(u + 3 * p.ny + yp);
+    const float inv_dy = 1.0f / (float)(yp - ym);
+    const float dxux = u2 - u3, dxuy = v2 - v3;
+    const float dyux = (exp_ - exm) * inv_dy, dyuy = (eyp - eym) * inv_dy;
+    const float pxx = p.bc_pre * dxux, pyy = p.bc_pre * dyuy, pxy = p.bc_pre * 0.5f * (dyux + dxuy);
+    const float ux = 2.0f * u2 - u3, uy = 2.0f * v2 - v3;
+    const float usq = ux * ux + uy * uy;
+    typename Codec<S>::T* o = st + (int64_t)y * p.pitch + (p.nx - 1);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const float cxq = (float)cx(q), cyq = (float)cy(q);
+        const float cu = cxq * ux + cyq * uy;
+        const float qp = (cxq * cxq - (1.0f / 3.0f)) * pxx + 2.0f * cxq * cyq * pxy + (cyq * cyq - (1.0f / 3.0f)) * pyy;
+        const float gq = wf(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq + 4.5f * qp);
+        o[q * p.plane] = K::out(gq, wf(q), p.scale);
+    }
+}
+
 template <int S, int V, int WARPS, bool SCALED, int COLL, bool OPEN = false>
 __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
 {
@@ -422,6 +513,22 @@ __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
     }
 }
 
+// the outlet column of an open channel, one thread per (row, listed clone),
+// launched after the step on the same stream
+constexpr int kBcThreads = 128;
+
+template <int S, bool SCALED>
+__global__ void __launch_bounds__(kBcThreads) open_bc_kernel(const StepParams p)
+{
+    using T = typename Codec<S>::T;
+    const int y = blockIdx.x * kBcThreads + threadIdx.x;
+    const int li = blockIdx.y;
+    const int c = p.clone_list[li];
+    const int cur = p.parity[c] ^ (p.step_in_batch & 1);
+    T* st = static_cast<T*>(cur ? p.buf0 : p.buf1) + (int64_t)c * p.clone_stride;
+    if (y < p.ny) open_outlet_row<S, SCALED>(p, st, li, y);
+}
+
 template <int S, int V, int WARPS>
 cudaError_t launch_step(const StepParams& p, cudaStream_t s)
 {
@@ -445,96 +552,21 @@ cudaError_t launch_step(const StepParams& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- open channel
-// Boundary columns of the open channel (Sec. 2), written into the state a
-// step launch has just produced (post-collision populations), one thread per
-// (row, listed clone):
-//   inlet  x = 0:      f = f^eq(rho = 1, (u_in(y), 0)), precomputed in FP64 on
-//                      the host (p.inlet_g holds f - w);
-//   outlet x = nx-1:   rho = 1 and u = 2 u(nx-2) - u(nx-3), the populations
-//                      regularized (Latt et al. 2008):
-//                      f = f^eq(1, u) + w_q / (2 cs2^2) Q_q : Pi,  Q_q = c_q c_q - cs2 I,
-//                      Pi = bc_pre * S,  bc_pre = -2 cs2 (tau(nx-1) - 1),
-//                      S the strain rate by finite differences: x one-sided from
-//                      the two upstream columns, y central on the extrapolated
-//                      column (one-sided on the wall rows).
-// The velocity of a post-collision state is sum c f / sum f (no body force).
-template <int S, bool SCALED>
-__device__ __forceinline__ void open_velocity(const typename Codec<S>::T* col, int64_t plane, float inv_scale,
-                                              float& ux, float& uy)
-{
-    using K = Carry<S, SCALED>;
-    float g[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) g[q] = K::in(col[q * plane], wf(q), inv_scale);
-    const float drho = (g[0] + (g[1] + g[3])) + ((g[2] + g[4]) + ((g[5] + g[7]) + (g[6] + g[8])));
-    const float jx = (g[1] - g[3]) + ((g[5] - g[7]) - (g[6] - g[8]));
-    const float jy = (g[2] - g[4]) + ((g[5] - g[7]) + (g[6] - g[8]));
-    const float inv = 1.0f / (1.0f + drho);
-    ux = jx * inv;
-    uy = jy * inv;
-}
-
-template <int S, bool SCALED>
-__global__ void open_bc_kernel(const StepParams p)
-{
-    using T = typename Codec<S>::T;
-    using K = Carry<S, SCALED>;
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= p.ny) return;
-    const int c = p.clone_list[blockIdx.y];
-    const int cur = p.parity[c] ^ (p.step_in_batch & 1);
-    T* st = static_cast<T*>(cur ? p.buf0 : p.buf1) + (int64_t)c * p.clone_stride;
-    const int64_t plane = p.plane;
-    // inlet column
-#pragma unroll
-    for (int q = 0; q < 9; ++q) st[q * plane + (int64_t)y * p.pitch] = K::out(p.inlet_g[q * p.ny + y], wf(q), p.scale);
-    // outlet column: extrapolated velocity of rows y-1, y, y+1 (clamped)
-    const int ym = y > 0 ? y - 1 : y, yp = y < p.ny - 1 ? y + 1 : y;
-    float ex[3], ey[3], dxux = 0.f, dxuy = 0.f;
-    const int rows[3] = {ym, y, yp};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const T* r = st + (int64_t)rows[k] * p.pitch;
-        float u2, v2, u3, v3;
-        open_velocity<S, SCALED>(r + (p.nx - 2), plane, p.inv_scale, u2, v2);
-        open_velocity<S, SCALED>(r + (p.nx - 3), plane, p.inv_scale, u3, v3);
-        ex[k] = 2.0f * u2 - u3;
-        ey[k] = 2.0f * v2 - v3;
-        if (k == 1) {
-            dxux = u2 - u3;
-            dxuy = v2 - v3;
-        }
-    }
-    const float inv_dy = 1.0f / (float)(yp - ym);
-    const float dyux = (ex[2] - ex[0]) * inv_dy, dyuy = (ey[2] - ey[0]) * inv_dy;
-    const float pxx = p.bc_pre * dxux, pyy = p.bc_pre * dyuy, pxy = p.bc_pre * 0.5f * (dyux + dxuy);
-    const float ux = ex[1], uy = ey[1];
-    const float u2 = ux * ux + uy * uy;
-    T* o = st + (int64_t)y * p.pitch + (p.nx - 1);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const float cxq = (float)cx(q), cyq = (float)cy(q);
-        const float cu = cxq * ux + cyq * uy;
-        const float qp = (cxq * cxq - (1.0f / 3.0f)) * pxx + 2.0f * cxq * cyq * pxy + (cyq * cyq - (1.0f / 3.0f)) * pyy;
-        const float gq = wf(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * u2 + 4.5f * qp);
-        o[q * plane] = K::out(gq, wf(q), p.scale);
-    }
-}
-
-// one step of an open channel: the fused step (OPEN instantiation) and the
-// boundary columns, on the same stream
+// one step of an open channel: the fused step's open-channel instantiation
+// (which also writes the inlet column), then the outlet column.  (Launching
+// the outlet kernel as a programmatic dependent of the step measured slower:
+// its waiting blocks hold SM slots during the step's tail.)
 template <int S, int V, int WARPS>
 cudaError_t launch_step_open(const StepParams& p, cudaStream_t s)
 {
     const dim3 block(32, WARPS);
     const dim3 grid(p.nseg, (p.ny + WARPS - 1) / WARPS, p.n_list);
-    const dim3 bc_grid((p.ny + 127) / 128, p.n_list);
+    const dim3 bc_grid((p.ny + kBcThreads - 1) / kBcThreads, p.n_list);
     auto go = [&](auto coll, auto scaled) {
         constexpr int C = decltype(coll)::value;
         constexpr bool SC = decltype(scaled)::value;
         step_kernel<S, V, WARPS, SC, C, true><<<grid, block, 0, s>>>(p);
-        open_bc_kernel<S, SC><<<bc_grid, 128, 0, s>>>(p);
+        open_bc_kernel<S, SC><<<bc_grid, kBcThreads, 0, s>>>(p);
     };
     auto by_scale = [&](auto coll) {
         if constexpr (S == kFP32) {

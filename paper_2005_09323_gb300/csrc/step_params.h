@@ -108,6 +108,7 @@ struct StepParams {
     const float* om_col;        // [nx] relaxation rate 1/tau(x) of each column
     const float* inlet_g;       // [9][ny] inlet populations minus w_q (FP32 of the FP64 values)
     float bc_pre;               // outlet stress factor -2 cs2 (tau(nx-1) - 1)
+    float* open_u;              // [list index][4][ny] velocities of columns nx-2, nx-3
 };
 
 // consumer warps of the row-staged step kernel; each writes its own drag
