@@ -61,6 +61,7 @@ def lib():
         L.orc_cm_collide.argtypes = [p, d, d, p, p, p, p]
         L.orc_tau_at.argtypes = [p, C.c_int]; L.orc_tau_at.restype = d
         L.orc_inlet_u.argtypes = [p, C.c_int]; L.orc_inlet_u.restype = d
+        L.orc_observables.argtypes = [p, p, p]; L.orc_observables.restype = C.c_int
         L.orc_perturb_alphas.argtypes = [u64, u64, i32, i32, p]
         L.orc_perturb.argtypes = [p, p, i32, p, p, d, p]
         L.orc_gktl_weights.argtypes = [i32, p, p, p]; L.orc_gktl_weights.restype = C.c_int
@@ -177,6 +178,16 @@ def macro(c: Cfg, f: np.ndarray):
     rho = np.zeros((c.ny, c.nx)); ux = np.zeros_like(rho); uy = np.zeros_like(rho)
     lib().orc_macro(C.byref(c), _ptr(f), _ptr(rho), _ptr(ux), _ptr(uy))
     return rho, ux, uy
+
+
+def observables(c: Cfg, f: np.ndarray) -> np.ndarray:
+    """[p_fb, p_base, gamma_top, gamma_bottom] of a post-collision state (Sec. 2.1
+    eq. drag_approx, Sec. 3.2 eq. avg_shear_def)"""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(4)
+    if lib().orc_observables(C.byref(c), _ptr(f), _ptr(out)) != 0:
+        raise ValueError("observables need a square with two fluid rows above and below and a column beside it")
+    return out
 
 
 def solid_mask(c: Cfg) -> np.ndarray:

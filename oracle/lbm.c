@@ -113,23 +113,28 @@ void orc_init(const orc_cfg* c, uint64_t seed, int32_t clone, double amp, double
         }
 }
 
+/* density and velocity of node (x, y) of post-collision populations: their
+ * momentum carries the whole force of the step, the fluid velocity half of it */
+static void node_macro(const orc_cfg* c, const double* f, int x, int y, double* rho, double* ux, double* uy)
+{
+    double r = 0, jx = 0, jy = 0;
+    for (int i = 0; i < 9; ++i) {
+        double v = f[IDX(c, i, x, y)];
+        r += v;
+        jx += v * CX[i];
+        jy += v * CY[i];
+    }
+    *rho = r;
+    *ux = (jx - 0.5 * c->gx) / r;
+    *uy = (jy - 0.5 * c->gy) / r;
+}
+
 void orc_macro(const orc_cfg* c, const double* f, double* rho, double* ux, double* uy)
 {
     for (int y = 0; y < c->ny; ++y)
         for (int x = 0; x < c->nx; ++x) {
-            double r = 0, jx = 0, jy = 0;
-            for (int i = 0; i < 9; ++i) {
-                double v = f[IDX(c, i, x, y)];
-                r += v;
-                jx += v * CX[i];
-                jy += v * CY[i];
-            }
-            /* the stored populations are post-collision: their momentum carries
-             * the whole force of the step, the fluid velocity half of it */
             size_t s = (size_t)y * c->nx + x;
-            rho[s] = r;
-            ux[s] = (jx - 0.5 * c->gx) / r;
-            uy[s] = (jy - 0.5 * c->gy) / r;
+            node_macro(c, f, x, y, rho + s, ux + s, uy + s);
         }
 }
 
@@ -438,3 +443,34 @@ void orc_perturb(const orc_cfg* c, const double* f, int32_t n_s, const double* s
                     f_out[IDX(c, i, x, y)] *= scale;
             }
 }
+
+/* Sec. 2.1 eq. (drag_approx) and Sec. 3.2 eq. (avg_shear_def); see oracle.h */
+int orc_observables(const orc_cfg* c, const double* f, double out[4])
+{
+    const int x0 = c->ox0, x1 = c->ox0 + c->ow, y0 = c->oy0, y1 = c->oy0 + c->oh;
+    if (c->ow <= 0 || x0 < 1 || x1 > c->nx - 1 || y0 < 2 || y1 > c->ny - 2) return -1;
+    double rho_at, ux_at, uy_at;
+    double pfb = 0.0, pbase = 0.0;
+    for (int y = y0; y < y1; ++y) {
+        node_macro(c, f, x0 - 1, y, &rho_at, &ux_at, &uy_at);
+        pfb += CS2 * rho_at;
+        node_macro(c, f, x1, y, &rho_at, &ux_at, &uy_at);
+        pbase += CS2 * rho_at;
+    }
+    double gt = 0.0, gb = 0.0;
+    for (int x = x0; x < x1; ++x) {
+        double u1, u2;
+        node_macro(c, f, x, y1, &rho_at, &u1, &uy_at);      /* 1/2 above the top wall */
+        node_macro(c, f, x, y1 + 1, &rho_at, &u2, &uy_at);  /* 3/2 above */
+        gt += (9.0 * u1 - u2) / 3.0;
+        node_macro(c, f, x, y0 - 1, &rho_at, &u1, &uy_at);  /* 1/2 below the bottom wall */
+        node_macro(c, f, x, y0 - 2, &rho_at, &u2, &uy_at);  /* 3/2 below */
+        gb -= (9.0 * u1 - u2) / 3.0;
+    }
+    out[0] = pfb;
+    out[1] = pbase;
+    out[2] = gt / c->ow;
+    out[3] = gb / c->ow;
+    return 0;
+}
+

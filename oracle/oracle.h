@@ -106,6 +106,23 @@ void orc_moments(const orc_cfg* c, const double* f, double* mass, double* px, do
  * rho = sum f, rho u = sum f c - F/2 (the step's force counted half) */
 void orc_macro(const orc_cfg* c, const double* f, double* rho, double* ux, double* uy);
 
+/* observables of the square (Sec. 2.1 and Sec. 3.2), from post-collision
+ * populations (velocity as orc_macro):
+ *   out[0] p_fb    = cs2 * sum of rho over the fluid column just upstream of
+ *                    the square (x = ox0 - 1), its rows [oy0, oy0 + oh): the
+ *                    forebody pressure integrated over the upstream face;
+ *   out[1] p_base  = the same over the column just downstream (x = ox0 + ow);
+ *                    eq. (drag_approx): f_d ~ p_fb - p_base;
+ *   out[2] gamma_top, out[3] gamma_bottom: eq. (avg_shear_def), the mean over
+ *                    the face's ow columns of d u_x / d y at the halfway wall,
+ *                    from the two fluid rows beside it (distances 1/2 and 3/2):
+ *                    du/dy = (9 u_1 - u_2) / 3 on the top face, the negative of
+ *                    that with the rows below on the bottom face (exact for
+ *                    u_x quadratic in the distance with u_x = 0 at the wall).
+ * Returns -1 (out untouched) without a square, or when the square leaves fewer
+ * than two fluid rows above or below it or no fluid column beside it. */
+int orc_observables(const orc_cfg* c, const double* f, double out[4]);
+
 /* ---------------- branching perturbation (App. D) -------------------- */
 void orc_perturb_alphas(uint64_t seed, uint64_t iter, int32_t slot, int32_t n_s, double* alpha);
 /* f_out = (f + eps * sum_n alpha_n snap_n) rescaled to the mass of f, fluid nodes only */
