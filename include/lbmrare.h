@@ -190,6 +190,36 @@ int lbm_ensemble_clone(lbm_ensemble* e, const int32_t* parent_dev, double eps, u
 int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, double eps,
                         uint64_t seed, uint64_t iter);
 
+/* The App. D perturbation of eq. (perturb_pop) applied in place to the n listed
+ * clones (host array of distinct indices): f <- (f + eps sum_n alpha_n f^(n)) *
+ * M / (M + eps sum_n alpha_n M^(n)) on fluid nodes, alpha_n from counter
+ * (4, iter, clone, n) as in lbm_ensemble_clone.  This is the periodic
+ * perturbation of the paper's check that the perturbation leaves the drag
+ * statistics unchanged (App. D).  eps = 0 does nothing; otherwise needs the
+ * snapshot bank.  Waits.  Errors: LBM_ERR_ARG, LBM_ERR_STATE. */
+int lbm_ensemble_perturb(lbm_ensemble* e, int32_t n, const int32_t* clones, double eps, uint64_t seed,
+                         uint64_t iter);
+
+/* Observables of the square after every step (Sec. 2.1 eq. drag_approx, Sec.
+ * 3.2 eq. avg_shear_def), recorded from the next step on while enabled, from
+ * the post-collision state of each step:
+ *   [0] p_fb   = cs2 sum over rows [obs_y0, obs_y0+obs_h) of rho(obs_x0 - 1, y):
+ *               the pressure integrated over the upstream face (forebody);
+ *   [1] p_base = the same at x = obs_x0 + obs_w (the base); f_d ~ p_fb - p_base;
+ *   [2] gamma_top, [3] gamma_bottom: the mean over the face's obs_w columns of
+ *       d u_x / d y at the halfway wall, (9 u_1 - u_2)/3 from the fluid rows at
+ *       distances 1/2 and 3/2 (negated on the bottom face, whose rows lie
+ *       below), with rho u = sum c f - F/2.
+ * FP64, fixed summation order.  Enabling needs a square with two fluid rows
+ * above and below it (obs_y0 >= 2, obs_y0 + obs_h <= ny - 2) and allocates
+ * [N][max_steps][4] doubles; each step then adds one small kernel.  Cloning
+ * and branching copy the history with the drag's.  Errors: LBM_ERR_ARG.
+ * lbm_ensemble_observables copies entries t0 <= t < t1 (t as in
+ * lbm_ensemble_drag) of every clone into dst[N][t1-t0][4] (host, waits; or
+ * device with dst_on_device != 0).  Errors: LBM_ERR_STATE if never enabled. */
+int lbm_ensemble_set_observables(lbm_ensemble* e, int32_t enable);
+int lbm_ensemble_observables(lbm_ensemble* e, int32_t t0, int32_t t1, double* dst, int32_t dst_on_device);
+
 /* Fluid mass and momentum sum_x sum_q f_q (1, c_q) per clone (host double[N]
  * each; any may be NULL), FP64 deterministic reduction.  Waits. */
 int lbm_ensemble_moments(lbm_ensemble* e, double* mass, double* px, double* py);

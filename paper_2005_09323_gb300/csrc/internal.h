@@ -59,6 +59,10 @@ int fields_launch(lbm_ensemble* e, const int32_t* list_dev, int32_t n, int32_t f
 // learned score of the listed clones (host list) into out[c * stride + k] (surrogate.cu)
 int score_clones(lbm_ensemble* e, const int32_t* clones, int32_t n, double* out, int32_t stride, int32_t k);
 
+// one launch of the observables kernel for step `step` of a chunk over the
+// listed clones (observables.cu)
+int observables_launch(lbm_ensemble* e, const int32_t* list_dev, int32_t n_list, int32_t step, cudaStream_t s);
+
 }  // namespace lbm
 
 struct cnn_model;
@@ -132,4 +136,8 @@ struct lbm_ensemble {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     double timed_ms;
     int64_t timed_launches;
+    // observables of the square after every step (lbm_ensemble_set_observables)
+    bool observe;
+    double* obs;              // [N][max_steps][4]: p_fb, p_base, gamma_top, gamma_bottom
 };
+

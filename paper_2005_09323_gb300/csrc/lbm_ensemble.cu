@@ -293,25 +293,29 @@ __global__ void bank_mass_final_kernel(const double* partial, int32_t nblocks, d
     snap_mass[blockIdx.x] = m;
 }
 
-// App. D: slot s with parent p != s (or s == inplace) becomes
+// perturb_kernel's `inplace` value that perturbs every listed slot in place
+constexpr int32_t kAllInPlace = -2;
+
+// App. D: slot s with parent p != s (or s == inplace, or every listed slot
+// with inplace == kAllInPlace) becomes
 //   f_s = (f_p + eps sum_n alpha_n f^(n)) * M_p / (M_p + eps sum_n alpha_n M^(n))
 // on fluid nodes, written in the shifted variable g = f - w.
 template <int S>
 __global__ void perturb_kernel(void* buf0, void* buf1, const int32_t* parity, const int32_t* parent, int32_t n_clones,
-                               int32_t* flag, int32_t inplace,
+                               int32_t* flag, int32_t inplace, const int32_t* slots,
                                int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny,
                                Solids sol, const void* snaps, int32_t n_s,
                                const double* snap_mass, const double* mass, double eps, uint64_t seed, uint64_t iter,
                                float scale, float inv_scale)
 {
     using T = typename Codec<S>::T;
-    const int s = blockIdx.y;
+    const int s = slots ? slots[blockIdx.y] : (int)blockIdx.y;
     const int p = parent[s];
     if (p < 0 || p >= n_clones) {  // rejected selection: leave the slot alone
         if (threadIdx.x == 0) flag[0] = 1;
         return;
     }
-    if (p == s && s != inplace) return;  // block-uniform
+    if (p == s && s != inplace && inplace != kAllInPlace) return;  // block-uniform
     __shared__ float alpha_eps[16];
     __shared__ float sc_m1[2];
     if (threadIdx.x == 0) {
@@ -584,11 +588,14 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
     const StepVariant& v = step_variants()[vi];
     const StepVariant::Launch launch = launcher(e, v);
     if (!launch) return fail(LBM_ERR_ARG, "the step variant has no open-channel instantiation");
-    const int per_step = e->cfg.open_x ? 2 : 1;  // an open channel adds the outlet kernel
+    // an open channel adds the outlet kernel, observables their own kernel
+    const int per_step = (e->cfg.open_x ? 2 : 1) + (e->observe ? 1 : 0);
     if (!e->use_graphs) {
         for (int s = 0; s < chunk; ++s) {
             cudaError_t err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
             if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
+            if (e->observe && observables_launch(e, list_dev, n_list, s, e->stream))
+                return cuda_fail(cudaGetLastError(), "observables kernel launch");
         }
         count_launches(chunk * per_step);
         return LBM_OK;
@@ -600,8 +607,11 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
         if (!e->cap_stream) LBM_CUDA(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
         LBM_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed));
         cudaError_t launch_err = cudaSuccess;
-        for (int s = 0; s < chunk && launch_err == cudaSuccess; ++s)
+        for (int s = 0; s < chunk && launch_err == cudaSuccess; ++s) {
             launch_err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->cap_stream);
+            if (launch_err == cudaSuccess && e->observe && observables_launch(e, list_dev, n_list, s, e->cap_stream))
+                launch_err = cudaGetLastError();
+        }
         cudaGraph_t graph = nullptr;
         const cudaError_t end_err = cudaStreamEndCapture(e->cap_stream, &graph);
         if (launch_err != cudaSuccess || end_err != cudaSuccess) {
@@ -722,7 +732,8 @@ int bank_masses(lbm_ensemble* e, int n_s)
     });
 }
 
-int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, double eps, uint64_t seed, uint64_t iter)
+int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, double eps, uint64_t seed, uint64_t iter,
+                const int32_t* slots = nullptr, int32_t n_slots = -1)
 {
     const Solids sol = solids_of(e->cfg);
     const int n_s = eps != 0.0 ? e->n_snaps_set : 0;
@@ -730,9 +741,9 @@ int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, dou
         constexpr int S = decltype(tag)::value;
         const int64_t sites = (int64_t)e->cfg.nx * e->cfg.ny;
         const int bx = (int)std::min<int64_t>((sites + 255) / 256, 1024);
-        dim3 grid(bx, e->n);
+        dim3 grid(bx, slots ? n_slots : e->n);
         perturb_kernel<S><<<grid, 256, 0, e->stream>>>(
-            e->buf[0], e->buf[1], e->parity_dev, parent_dev, e->n, e->flag_dev, inplace, e->clone_stride, e->plane, e->pitch, e->cfg.nx,
+            e->buf[0], e->buf[1], e->parity_dev, parent_dev, e->n, e->flag_dev, inplace, slots, e->clone_stride, e->plane, e->pitch, e->cfg.nx,
             e->cfg.ny, sol, e->snaps, n_s, e->snap_mass, e->mass_dev, eps, seed, iter, e->scale,
             e->inv_scale);
         count_launches(1);
@@ -922,7 +933,7 @@ int lbm_ensemble_destroy(lbm_ensemble* e)
     void* ptrs[] = {e->buf[0], e->buf[1], e->parity_dev, e->t_dev, e->list_dev, e->all_dev, e->partials,
                     e->drag, e->scores, e->flag_dev, e->red_partials, e->mass_dev, e->snaps, e->snap_mass, e->ckpt,
                     e->fields_list_dev, e->cnn_x, e->cnn_pred, e->cnn_score, e->pot[0], e->pot[1], e->pot[2],
-                    e->pot_tmp[0], e->pot_tmp[1], e->om_col, e->inlet_g, e->open_u};
+                    e->pot_tmp[0], e->pot_tmp[1], e->om_col, e->inlet_g, e->open_u, e->obs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete e;
@@ -1092,6 +1103,12 @@ int lbm_ensemble_clone(lbm_ensemble* e, const int32_t* parent_dev, double eps, u
         copy_history_kernel<<<grid, 256, 0, e->stream>>>(e->drag, e->cfg.max_steps, parent_dev, e->n, t);
         count_launches(1);
         LBM_CUDA(cudaGetLastError());
+        if (e->obs) {  // the observables of a copied trajectory are its parent's
+            dim3 g4((unsigned)std::min(64, (4 * t + 255) / 256), e->n);
+            copy_history_kernel<<<g4, 256, 0, e->stream>>>(e->obs, 4 * e->cfg.max_steps, parent_dev, e->n, 4 * t);
+            count_launches(1);
+            LBM_CUDA(cudaGetLastError());
+        }
     }
     return LBM_OK;
 }
@@ -1130,9 +1147,14 @@ int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, 
     // the drag history up to t_b is the source's own, copied after the replay:
     // the replay may run another step variant, whose per-warp drag partials
     // are summed in another grouping (the populations are identical bit for bit)
-    if (t_b > 0)
+    if (t_b > 0) {
         LBM_CUDA(cudaMemcpyAsync(e->drag + (size_t)dst * e->cfg.max_steps, e->drag + (size_t)src * e->cfg.max_steps,
                                  sizeof(double) * t_b, cudaMemcpyDeviceToDevice, e->stream));
+        if (e->obs)
+            LBM_CUDA(cudaMemcpyAsync(e->obs + (size_t)dst * 4 * e->cfg.max_steps,
+                                     e->obs + (size_t)src * 4 * e->cfg.max_steps, sizeof(double) * 4 * t_b,
+                                     cudaMemcpyDeviceToDevice, e->stream));
+    }
     if (eps != 0.0) {
         LBM_CUDA(cudaMemcpyAsync(e->list_dev, &dst, sizeof(int32_t), cudaMemcpyHostToDevice, e->stream));
         int rc = compute_masses(e, e->list_dev, 1);
@@ -1141,6 +1163,27 @@ int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, 
         if (rc) return rc;
         LBM_CUDA(cudaStreamSynchronize(e->stream));
     }
+    return LBM_OK;
+}
+
+int lbm_ensemble_perturb(lbm_ensemble* e, int32_t n, const int32_t* clones, double eps, uint64_t seed, uint64_t iter)
+{
+    if (!e || !clones) return fail(LBM_ERR_ARG, "null argument");
+    if (n < 1 || n > e->n) return fail(LBM_ERR_ARG, "clone count out of range");
+    std::vector<char> seen(e->n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (clones[i] < 0 || clones[i] >= e->n || seen[clones[i]]) return fail(LBM_ERR_ARG, "bad or repeated clone index");
+        seen[clones[i]] = 1;
+    }
+    if (!std::isfinite(eps) || eps < 0.0) return fail(LBM_ERR_ARG, "eps must be finite and >= 0");
+    if (eps == 0.0) return LBM_OK;  // the identity
+    if (e->n_snaps_set < 1) return fail(LBM_ERR_STATE, "perturbation needs the snapshot bank");
+    LBM_CUDA(cudaMemcpyAsync(e->list_dev, clones, sizeof(int32_t) * n, cudaMemcpyHostToDevice, e->stream));
+    int rc = compute_masses(e, e->list_dev, n);
+    if (rc) return rc;
+    rc = run_perturb(e, e->all_dev, kAllInPlace, eps, seed, iter, e->list_dev, n);
+    if (rc) return rc;
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
     return LBM_OK;
 }
 

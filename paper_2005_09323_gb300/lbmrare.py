@@ -35,7 +35,8 @@ EXPORTS = [
     "cnn_gradient", "cnn_get_gradient", "cnn_adam_step", "cnn_train_step", "lbm_ensemble_fields",
     "cnn_shape", "cnn_predict", "cnn_fit", "lbm_ensemble_attach_score", "lbm_ensemble_evaluate_score",
     "lbm_ensemble_score_history", "lbm_surrogate_dataset", "lbm_ensemble_set_snapshots_from_checkpoint",
-    "lbm_selftest_bounded_wait",
+    "lbm_selftest_bounded_wait", "lbm_ensemble_perturb", "lbm_ensemble_set_observables",
+    "lbm_ensemble_observables",
 ]
 
 
@@ -152,6 +153,9 @@ def lib():
             "cnn_set_conv_path": ([p, i32], C.c_int),
             "lbm_drag_autocorrelation": ([p, i32, i32, i32, p, p], C.c_int),
             "lbm_drag_return_times": ([p, i32, i32, i32, p, i32, p, p], C.c_int),
+            "lbm_ensemble_perturb": ([p, i32, p, d, u64, u64], C.c_int),
+            "lbm_ensemble_set_observables": ([p, i32], C.c_int),
+            "lbm_ensemble_observables": ([p, i32, i32, p, i32], C.c_int),
             "cnn_status": ([p, p], C.c_int),
             "cnn_predict": ([p, p, i64, p, p], C.c_int),
             "cnn_fit": ([p, p, p, i64, i32, i32, C.c_float, u64, p, p], C.c_int),
@@ -227,6 +231,27 @@ def lbm_ensemble_time(e, n: int) -> np.ndarray:
     t = np.zeros(n, dtype=np.int32)
     _check(lib().lbm_ensemble_time(e, _host(t)))
     return t
+
+
+def lbm_ensemble_perturb(e, clones, eps: float, seed: int, it: int):
+    a = np.ascontiguousarray(clones, dtype=np.int32)
+    _check(lib().lbm_ensemble_perturb(e, len(a), _host(a), eps, seed, it))
+
+
+def lbm_ensemble_set_observables(e, enable: bool):
+    _check(lib().lbm_ensemble_set_observables(e, 1 if enable else 0))
+
+
+def lbm_ensemble_observables(e, t0: int, t1: int, dst):
+    """dst: numpy float64 [N, t1-t0, 4] (host, waits) or torch float64 CUDA tensor (enqueued):
+    p_fb, p_base, gamma_top, gamma_bottom after each step."""
+    if isinstance(dst, np.ndarray):
+        if dst.dtype != np.float64 or not dst.flags.c_contiguous:
+            raise TypeError("dst must be a contiguous float64 array")
+        _check(lib().lbm_ensemble_observables(e, t0, t1, _host(dst), 0))
+    else:
+        import torch
+        _check(lib().lbm_ensemble_observables(e, t0, t1, _dev(dst, torch.float64), 1))
 
 
 def lbm_ensemble_drag(e, t0: int, t1: int, dst):
