@@ -50,14 +50,14 @@ WORKLOADS = {
     "open": dict(nx=513, ny=129, clones=64, side=16, cloning=False, open=True,
                  name="Open channel of Sec. 2: N={n} independent trajectories, D2Q9 {st}, 513x129, 16x16 square at "
                       "the centre, entrance grid of 8-row bars every 16 rows at x=16..23, parabolic inlet u_c=0.05, "
-                      "regularized outlet, sponge of 64 columns up to tau=1, tau=0.501 (Re_grid=1200), 500 steps "
+                      "regularized outlet, sponge of 128 columns up to tau=1, tau=0.501 (Re_grid=1200), 500 steps "
                       "per step; drag autocorrelation and waiting-time return times over the run"),
 }
 # open channel of Sec. 2: Re_grid = u_c (R/2) / nu = 1200 with u_c = 0.05, R = 16
 OPEN_UC = 0.05
 OPEN_TAU = 0.5 + 3.0 * OPEN_UC * 8 / 1200
 OPEN_GRID = (16, 8, 8, 8)     # x0, width, bar rows, gap rows
-OPEN_SPONGE = (64, 1.0)       # columns, tau at the outlet
+OPEN_SPONGE = (128, 1.0)      # columns, tau at the outlet
 
 
 def workload(args):
@@ -81,6 +81,7 @@ def channel_kwargs(w) -> dict:
                     sponge_tau=OPEN_SPONGE[1])
     return dict(tau=TAU, gx=GX)
 EPS, N_SNAP = 0.002, 10
+CHECK_STEPS, CHECK_PERIOD = 5000, 1000  # perturbation check: steps per bench step, perturbation period (tau_c / 2)
 K_SIGMA = 1.0
 SIGMA_DRAG = 1e-3        # drag scale used to set k (k = K_SIGMA / (SIGMA_DRAG * PERIOD))
 BYTES_PER_SITE = 72      # FP32: 9 loads + 9 stores of 4 bytes
@@ -882,6 +883,128 @@ def run_ams_run(args):
         "gpu_launches": launches // max(len(runs), 1)}))
 
 
+def ks_distance(a, b) -> float:
+    """two-sample Kolmogorov-Smirnov distance of the empirical distributions"""
+    import numpy as np
+    a, b = np.sort(np.ravel(a)), np.sort(np.ravel(b))
+    grid = np.concatenate([a, b])
+    return float(np.max(np.abs(np.searchsorted(a, grid, side="right") / len(a)
+                               - np.searchsorted(b, grid, side="right") / len(b))))
+
+
+def pooled_tau_c(x, max_lag: int) -> int:
+    """first lag at which the autocorrelation pooled over the rows of x is <= 0
+    (the correlation time of Sec. 3; -1 if none within max_lag); the lagged
+    sums by FFT, each lag divided by its number of products"""
+    import numpy as np
+    x = x - x.mean()
+    n = x.shape[1]
+    m = 1 << int(np.ceil(np.log2(2 * n)))
+    spec = np.fft.rfft(x, m, axis=1)
+    acf = np.fft.irfft(spec * np.conj(spec), m, axis=1)[:, :max_lag + 1].sum(axis=0)
+    acf /= x.shape[0] * (n - np.arange(max_lag + 1))
+    below = np.nonzero(acf[1:] <= 0.0)[0]
+    return int(below[0]) + 1 if len(below) else -1
+
+
+def run_perturb_check(args):
+    """The paper's check that the App. D perturbation leaves the drag statistics
+    unchanged: on the open channel of Sec. 2 (the open workload), half of the
+    trajectories are perturbed in place (eps = 0.002, 10 snapshots) every
+    CHECK_PERIOD steps, about tau_c / 2 of its drag, the other half run
+    unperturbed, and the square's observables are recorded after every step.
+    The App. D bank holds flow states of the unperturbed half, refilled when
+    the warm-up (the spin-up of the channel) ends.
+    One bench step = CHECK_STEPS lattice steps of the whole ensemble, the
+    perturbations and the observables included.  Reported: GLUPS, and the
+    statistics of each half over the timed steps, with the KS distance between
+    the halves against that between the two quarters of the unperturbed half
+    (a null reference of the same sample size)."""
+    import numpy as np
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = workload(argparse.Namespace(workload="open", clones=args.clones, collision=args.collision))
+    n = w["clones"]
+    half = list(range(n // 2))
+    total = CHECK_STEPS * (args.warmup + args.steps)
+    stream = torch.cuda.current_stream()
+    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], max_steps=total, n_snapshots=N_SNAP, init_amp=0.01,
+                   storage=args.storage, collision=w["collision"], **channel_kwargs(w))
+    e = L.lbm_ensemble_create(cfg, n, 31, stream)
+    L.lbm_ensemble_set_observables(e, True)
+    state = {"it": 0}
+    bank = [n // 2 + i * (n // 2) // N_SNAP for i in range(N_SNAP)]  # unperturbed trajectories
+
+    period = args.check_period
+
+    def bench_step():
+        for k in range(CHECK_STEPS // period):
+            L.lbm_ensemble_step(e, period)
+            if state["it"] == 0:  # a first bank for the spin-up
+                L.lbm_ensemble_set_snapshots(e, bank)
+            L.lbm_ensemble_perturb(e, half, EPS, 11, state["it"])
+            state["it"] += 1
+        # the remainder of the bench step, unperturbed until the next period
+        if CHECK_STEPS % period:
+            L.lbm_ensemble_step(e, CHECK_STEPS % period)
+
+    for _ in range(args.warmup):
+        bench_step()
+    L.lbm_ensemble_set_snapshots(e, bank)  # states of the developed flow
+    torch.cuda.synchronize()
+    l0 = L.lbm_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            bench_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = L.lbm_launch_count() - l0
+    ms = ev0.elapsed_time(ev1)
+    t0, t1 = CHECK_STEPS * args.warmup, total
+    drag = np.zeros((n, t1 - t0))
+    L.lbm_ensemble_drag(e, t0, t1, drag)
+    obs = np.zeros((n, t1 - t0, 4))
+    L.lbm_ensemble_observables(e, t0, t1, obs)
+    L.lbm_ensemble_destroy(e)
+
+    def stats(rows):
+        d, o = drag[rows], obs[rows]
+        dp = o[..., 0] - o[..., 1]
+        return {"clones": len(rows), "drag_mean": float(d.mean()), "drag_std": float(d.std()),
+                "tau_c_steps": pooled_tau_c(d, min(20000, d.shape[1] - 1)), "p_fb_minus_p_base_mean": float(dp.mean()),
+                "p_fb_minus_p_base_std": float(dp.std()), "gamma_top_mean": float(o[..., 2].mean()),
+                "gamma_top_std": float(o[..., 2].std()), "gamma_bottom_mean": float(o[..., 3].mean()),
+                "corr_drag_pressure_diff": float(np.corrcoef(d.ravel(), dp.ravel())[0, 1])}
+
+    pert, unpert = half, list(range(n // 2, n))
+    q = len(unpert) // 2
+    sites = n * w["nx"] * w["ny"]
+    print(json.dumps({
+        "metric": "Perturbation check (App. D): GLUPS with in-place perturbation and observables",
+        "value": sites * CHECK_STEPS * args.steps / (ms / 1e3) / 1e9, "unit": "GLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Perturbation check (App. D) on the open channel of Sec. 2: N={n} trajectories of "
+                               f"{w['nx']}x{w['ny']}, square, grid, sponge, tau={OPEN_TAU:.4f}, {w['collision']} "
+                               f"collision, {args.storage}; clones 0..{n // 2 - 1} perturbed in place every "
+                               f"{period} steps (eps={EPS}, bank of {N_SNAP} unperturbed states refilled "
+                               f"after the {CHECK_STEPS * args.warmup}-step warm-up), the rest unperturbed; "
+                               f"observables every step; {CHECK_STEPS} steps per step",
+                   "storage": args.storage, "collision": w["collision"]},
+        "perturbation_check": {
+            "window_steps": [t0, t1], "period_steps": period, "eps": EPS,
+            "perturbed": stats(pert), "unperturbed": stats(unpert),
+            "ks_drag_perturbed_vs_unperturbed": ks_distance(drag[pert], drag[unpert]),
+            "ks_drag_null_unperturbed_quarters": ks_distance(drag[unpert[:q]], drag[unpert[q:]]),
+            "note": "bench-length run from the inlet-profile start; the paper's check ran 1e5 tau_c"},
+        "gpu_launches": launches, "clocks": clk.summary()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -893,11 +1016,14 @@ def main():
                     help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run"])
+    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run",
+                                              "perturb-check"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--collision", default=None, choices=["bgk", "cm"],
                     help="BGK or the central-moment collision (default: central moments for the open "
                          "channel, BGK otherwise)")
+    ap.add_argument("--check-period", type=int, default=CHECK_PERIOD,
+                    help="perturb-check: steps between in-place perturbations (the paper: tau_c / 2)")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()
@@ -913,6 +1039,8 @@ def main():
         run_ams_branch(args)
     elif args.workload == "ams-run":
         run_ams_run(args)
+    elif args.workload == "perturb-check":
+        run_perturb_check(args)
     else:
         run_ours(args)
 

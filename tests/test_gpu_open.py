@@ -19,9 +19,9 @@ RATES = dict(omega_bulk=1.3, omega_3=0.9, omega_4=1.7)
 OPEN = dict(nx=203, ny=37, obstacle=(80, 14, 9, 7), tau=0.56, open_x=1, u_in=0.05, grid=(12, 4, 3, 4),
             sponge_len=30, sponge_tau=0.95, max_steps=400, init_amp=0.01)
 # the channel of Sec. 2: 513 x 129, R = 16 at the centre, bars of R/2 every R
-# from x = R, R/2 thick; Re_grid = 1200 on u_c = 0.05 and R/2; sponge of 4R
+# from x = R, R/2 thick; Re_grid = 1200 on u_c = 0.05 and R/2; sponge of 8R
 PAPER = dict(nx=513, ny=129, obstacle=(248, 56, 16, 16), tau=0.5 + 3 * 0.05 * 8 / 1200, open_x=1, u_in=0.05,
-             grid=(16, 8, 8, 8), sponge_len=64, sponge_tau=1.0, collision="cm", max_steps=200, init_amp=0.0)
+             grid=(16, 8, 8, 8), sponge_len=128, sponge_tau=1.0, collision="cm", max_steps=200, init_amp=0.0)
 
 
 @pytest.fixture(scope="module")
