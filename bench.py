@@ -911,8 +911,10 @@ def run_perturb_check(args):
     """The paper's check that the App. D perturbation leaves the drag statistics
     unchanged: on the open channel of Sec. 2 (the open workload), half of the
     trajectories are perturbed in place (eps = 0.002, 10 snapshots) every
-    CHECK_PERIOD steps, about tau_c / 2 of its drag, the other half run
-    unperturbed, and the square's observables are recorded after every step.
+    --check-period steps, the other half run unperturbed, and the square's
+    observables are recorded after every step.  The default period, 1000 steps,
+    is tau_c / 2 of the developed flow's drag (tau_c about 2060 steps over
+    steps 15000-65000).
     The App. D bank holds flow states of the unperturbed half, refilled when
     the warm-up (the spin-up of the channel) ends.
     One bench step = CHECK_STEPS lattice steps of the whole ensemble, the
