@@ -100,7 +100,7 @@ NCU_TRAFFIC = {
     # both kernels of an open-channel step (the step kernel and the outlet kernel)
     ("open", "step_kernel<fp32, vec=2, warps=8, open> + open_bc_kernel"): {
         "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_open_fp32.cu"),
-        "sha": "7e16c141d726f006", "bytes_per_site": 59.0499},
+        "sha": "7e16c141d726f006", "bytes_per_site": 59.0138},
 }
 
 
