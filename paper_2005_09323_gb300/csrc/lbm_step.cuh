@@ -66,8 +66,9 @@ __device__ __forceinline__ void bgk_pair(float& gq, float& go, float cu, float A
 }
 
 // BGK collision with Guo forcing of site j, in place on the carried values
-// g = f - w, in the pairwise form of BgkConsts
-template <int V>
+// g = f - w, in the pairwise form of BgkConsts.  FORCE = false compiles the
+// force terms out (a channel without body force: the open channel)
+template <int V, bool FORCE = true>
 __device__ __forceinline__ void bgk_collide(float (&g)[9][V], int j, const BgkConsts& k)
 {
     const float s1 = g[1][j] + g[3][j], d1 = g[1][j] - g[3][j];
@@ -77,25 +78,40 @@ __device__ __forceinline__ void bgk_collide(float (&g)[9][V], int j, const BgkCo
     const float drho = (g[0][j] + s1) + (s2 + (s5 + s6));
     const float jx = d1 + (d5 - d6), jy = d2 + (d5 + d6);
     const float inv = __fdividef(1.0f, 1.0f + drho);
-    const float ux = (jx + k.hgx) * inv, uy = (jy + k.hgy) * inv;
-    const float P = fmaf(k.om3, drho, k.om3);  // 3 om rho
-    const float Qc = 1.5f * P;                  // 4.5 om rho
-    const float u2 = fmaf(ux, ux, uy * uy);
-    float a0 = fmaf(k.om, drho, -(0.5f * P) * u2);
-    a0 = fmaf(-k.kgx, ux, fmaf(-k.kgy, uy, a0));
-    g[0][j] = fmaf(wf(0), a0, k.omm * g[0][j]);
-    bgk_pair(g[1][j], g[3][j], ux, k.A[0], k.B[0], wf(1), P, Qc, a0, k.omm);
-    bgk_pair(g[2][j], g[4][j], uy, k.A[1], k.B[1], wf(2), P, Qc, a0, k.omm);
-    bgk_pair(g[5][j], g[7][j], ux + uy, k.A[2], k.B[2], wf(5), P, Qc, a0, k.omm);
-    bgk_pair(g[6][j], g[8][j], uy - ux, k.A[3], k.B[3], wf(6), P, Qc, a0, k.omm);
+    if constexpr (FORCE) {
+        const float ux = (jx + k.hgx) * inv, uy = (jy + k.hgy) * inv;
+        const float P = fmaf(k.om3, drho, k.om3);  // 3 om rho
+        const float Qc = 1.5f * P;                  // 4.5 om rho
+        const float u2 = fmaf(ux, ux, uy * uy);
+        float a0 = fmaf(k.om, drho, -(0.5f * P) * u2);
+        a0 = fmaf(-k.kgx, ux, fmaf(-k.kgy, uy, a0));
+        g[0][j] = fmaf(wf(0), a0, k.omm * g[0][j]);
+        bgk_pair(g[1][j], g[3][j], ux, k.A[0], k.B[0], wf(1), P, Qc, a0, k.omm);
+        bgk_pair(g[2][j], g[4][j], uy, k.A[1], k.B[1], wf(2), P, Qc, a0, k.omm);
+        bgk_pair(g[5][j], g[7][j], ux + uy, k.A[2], k.B[2], wf(5), P, Qc, a0, k.omm);
+        bgk_pair(g[6][j], g[8][j], uy - ux, k.A[3], k.B[3], wf(6), P, Qc, a0, k.omm);
+    } else {
+        // F = 0: A = B = 0 and no force in a0 or u
+        const float ux = jx * inv, uy = jy * inv;
+        const float P = fmaf(k.om3, drho, k.om3);
+        const float Qc = 1.5f * P;
+        const float u2 = fmaf(ux, ux, uy * uy);
+        const float a0 = fmaf(k.om, drho, -(0.5f * P) * u2);
+        g[0][j] = fmaf(wf(0), a0, k.omm * g[0][j]);
+        bgk_pair(g[1][j], g[3][j], ux, 0.0f, 0.0f, wf(1), P, Qc, a0, k.omm);
+        bgk_pair(g[2][j], g[4][j], uy, 0.0f, 0.0f, wf(2), P, Qc, a0, k.omm);
+        bgk_pair(g[5][j], g[7][j], ux + uy, 0.0f, 0.0f, wf(5), P, Qc, a0, k.omm);
+        bgk_pair(g[6][j], g[8][j], uy - ux, 0.0f, 0.0f, wf(6), P, Qc, a0, k.omm);
+    }
 }
 
 // central-moment collision of site j, in place on the carried values g = f - w
 // (CmConsts): raw moments of g from the pair sums, the moments of
 // f - f^eq + S/2 from the closed-form moments of the discrete equilibrium and
 // of the Guo term, binomial shift to central moments, relaxation, shift back,
-// and the D2Q9 inverse of the raw-moment transform
-template <int V>
+// and the D2Q9 inverse of the raw-moment transform.  FORCE = false: the same
+// without body force (the open channel), the force terms compiled out
+template <int V, bool FORCE = true>
 __device__ __forceinline__ void cm_collide(float (&g)[9][V], int j, const BgkConsts& k, const CmConsts& m)
 {
     const float s1 = g[1][j] + g[3][j], d1 = g[1][j] - g[3][j];
@@ -106,43 +122,72 @@ __device__ __forceinline__ void cm_collide(float (&g)[9][V], int j, const BgkCon
     const float jx = d1 + (d5 - d6), jy = d2 + (d5 + d6);
     const float rho = 1.0f + drho;
     const float inv = __fdividef(1.0f, rho);
-    const float ux = (jx + k.hgx) * inv, uy = (jy + k.hgy) * inv;
-    const float fx = m.fx, fy = m.fy;
     // raw moments of g
     const float m22 = s5 + s6, m20 = s1 + m22, m02 = s2 + m22, m11 = s5 - s6, m21 = d5 + d6, m12 = d5 - d6;
-    // moments of f - f^eq + S/2 (those of order 0 and 1 vanish)
-    const float rux = rho * ux, ruy = rho * uy, uF = ux * fx + uy * fy;
-    const float M20 = m20 - drho * (1.0f / 3.0f) - rux * ux + ux * fx;
-    const float M02 = m02 - drho * (1.0f / 3.0f) - ruy * uy + uy * fy;
-    const float M11 = m11 - rux * uy + 0.5f * (ux * fy + uy * fx);
-    const float M21 = m21 - ruy * (1.0f / 3.0f) + fy * (1.0f / 6.0f);
-    const float M12 = m12 - rux * (1.0f / 3.0f) + fx * (1.0f / 6.0f);
-    const float M22 = m22 - drho * (1.0f / 9.0f) - (rux * ux + ruy * uy) * (1.0f / 3.0f) + uF * (1.0f / 3.0f);
-    // central moments, relaxed
-    const float k21 = M21 - 2.0f * ux * M11 - uy * M20;
-    const float k12 = M12 - 2.0f * uy * M11 - ux * M02;
-    const float k22 = M22 - 2.0f * ux * M12 - 2.0f * uy * M21 + ux * ux * M02 + uy * uy * M20 + 4.0f * ux * uy * M11;
-    const float r20 = m.a * M20 + m.b * M02, r02 = m.b * M20 + m.a * M02, r11 = m.ws * M11;
-    const float r21 = m.w3 * k21, r12 = m.w3 * k12, r22 = m.w4 * k22;
-    // back to raw moments
-    const float R21 = r21 + 2.0f * ux * r11 + uy * r20;
-    const float R12 = r12 + 2.0f * uy * r11 + ux * r02;
-    const float R22 = r22 + 2.0f * ux * r12 + 2.0f * uy * r21 + ux * ux * r02 + uy * uy * r20 + 4.0f * ux * uy * r11;
-    // Guo term S_q = w_q (3 c.F - 3 u.F + 9 (c.u)(c.F)) and the update g + S - x
-    const float t0 = -3.0f * uF;
-    g[0][j] = g[0][j] + wf(0) * t0 - (R22 - r20 - r02);
-    const float cu1 = ux, cF1 = fx, cu2 = uy, cF2 = fy;
-    const float cu5 = ux + uy, cF5 = fx + fy, cu6 = uy - ux, cF6 = fy - fx;
-    const float e1 = t0 + 9.0f * cu1 * cF1, e2 = t0 + 9.0f * cu2 * cF2;
-    const float e5 = t0 + 9.0f * cu5 * cF5, e6 = t0 + 9.0f * cu6 * cF6;
-    g[1][j] = g[1][j] + wf(1) * (e1 + 3.0f * cF1) - 0.5f * (r20 - R12 - R22);
-    g[3][j] = g[3][j] + wf(3) * (e1 - 3.0f * cF1) - 0.5f * (r20 + R12 - R22);
-    g[2][j] = g[2][j] + wf(2) * (e2 + 3.0f * cF2) - 0.5f * (r02 - R21 - R22);
-    g[4][j] = g[4][j] + wf(4) * (e2 - 3.0f * cF2) - 0.5f * (r02 + R21 - R22);
-    g[5][j] = g[5][j] + wf(5) * (e5 + 3.0f * cF5) - 0.25f * (r11 + R21 + R12 + R22);
-    g[7][j] = g[7][j] + wf(7) * (e5 - 3.0f * cF5) - 0.25f * (r11 - R21 - R12 + R22);
-    g[6][j] = g[6][j] + wf(6) * (e6 + 3.0f * cF6) - 0.25f * (-r11 + R21 - R12 + R22);
-    g[8][j] = g[8][j] + wf(8) * (e6 - 3.0f * cF6) - 0.25f * (-r11 - R21 + R12 + R22);
+    if constexpr (FORCE) {
+        const float ux = (jx + k.hgx) * inv, uy = (jy + k.hgy) * inv;
+        const float fx = m.fx, fy = m.fy;
+        // moments of f - f^eq + S/2 (those of order 0 and 1 vanish)
+        const float rux = rho * ux, ruy = rho * uy, uF = ux * fx + uy * fy;
+        const float M20 = m20 - drho * (1.0f / 3.0f) - rux * ux + ux * fx;
+        const float M02 = m02 - drho * (1.0f / 3.0f) - ruy * uy + uy * fy;
+        const float M11 = m11 - rux * uy + 0.5f * (ux * fy + uy * fx);
+        const float M21 = m21 - ruy * (1.0f / 3.0f) + fy * (1.0f / 6.0f);
+        const float M12 = m12 - rux * (1.0f / 3.0f) + fx * (1.0f / 6.0f);
+        const float M22 = m22 - drho * (1.0f / 9.0f) - (rux * ux + ruy * uy) * (1.0f / 3.0f) + uF * (1.0f / 3.0f);
+        // central moments, relaxed
+        const float k21 = M21 - 2.0f * ux * M11 - uy * M20;
+        const float k12 = M12 - 2.0f * uy * M11 - ux * M02;
+        const float k22 = M22 - 2.0f * ux * M12 - 2.0f * uy * M21 + ux * ux * M02 + uy * uy * M20 + 4.0f * ux * uy * M11;
+        const float r20 = m.a * M20 + m.b * M02, r02 = m.b * M20 + m.a * M02, r11 = m.ws * M11;
+        const float r21 = m.w3 * k21, r12 = m.w3 * k12, r22 = m.w4 * k22;
+        // back to raw moments
+        const float R21 = r21 + 2.0f * ux * r11 + uy * r20;
+        const float R12 = r12 + 2.0f * uy * r11 + ux * r02;
+        const float R22 = r22 + 2.0f * ux * r12 + 2.0f * uy * r21 + ux * ux * r02 + uy * uy * r20 + 4.0f * ux * uy * r11;
+        // Guo term S_q = w_q (3 c.F - 3 u.F + 9 (c.u)(c.F)) and the update g + S - x
+        const float t0 = -3.0f * uF;
+        g[0][j] = g[0][j] + wf(0) * t0 - (R22 - r20 - r02);
+        const float cu1 = ux, cF1 = fx, cu2 = uy, cF2 = fy;
+        const float cu5 = ux + uy, cF5 = fx + fy, cu6 = uy - ux, cF6 = fy - fx;
+        const float e1 = t0 + 9.0f * cu1 * cF1, e2 = t0 + 9.0f * cu2 * cF2;
+        const float e5 = t0 + 9.0f * cu5 * cF5, e6 = t0 + 9.0f * cu6 * cF6;
+        g[1][j] = g[1][j] + wf(1) * (e1 + 3.0f * cF1) - 0.5f * (r20 - R12 - R22);
+        g[3][j] = g[3][j] + wf(3) * (e1 - 3.0f * cF1) - 0.5f * (r20 + R12 - R22);
+        g[2][j] = g[2][j] + wf(2) * (e2 + 3.0f * cF2) - 0.5f * (r02 - R21 - R22);
+        g[4][j] = g[4][j] + wf(4) * (e2 - 3.0f * cF2) - 0.5f * (r02 + R21 - R22);
+        g[5][j] = g[5][j] + wf(5) * (e5 + 3.0f * cF5) - 0.25f * (r11 + R21 + R12 + R22);
+        g[7][j] = g[7][j] + wf(7) * (e5 - 3.0f * cF5) - 0.25f * (r11 - R21 - R12 + R22);
+        g[6][j] = g[6][j] + wf(6) * (e6 + 3.0f * cF6) - 0.25f * (-r11 + R21 - R12 + R22);
+        g[8][j] = g[8][j] + wf(8) * (e6 - 3.0f * cF6) - 0.25f * (-r11 - R21 + R12 + R22);
+    } else {
+        // the same collision with F = 0: no Guo term, u = sum c g / rho
+        const float ux = jx * inv, uy = jy * inv;
+        const float rux = rho * ux, ruy = rho * uy;
+        const float M20 = m20 - drho * (1.0f / 3.0f) - rux * ux;
+        const float M02 = m02 - drho * (1.0f / 3.0f) - ruy * uy;
+        const float M11 = m11 - rux * uy;
+        const float M21 = m21 - ruy * (1.0f / 3.0f);
+        const float M12 = m12 - rux * (1.0f / 3.0f);
+        const float M22 = m22 - drho * (1.0f / 9.0f) - (rux * ux + ruy * uy) * (1.0f / 3.0f);
+        const float k21 = M21 - 2.0f * ux * M11 - uy * M20;
+        const float k12 = M12 - 2.0f * uy * M11 - ux * M02;
+        const float k22 = M22 - 2.0f * ux * M12 - 2.0f * uy * M21 + ux * ux * M02 + uy * uy * M20 + 4.0f * ux * uy * M11;
+        const float r20 = m.a * M20 + m.b * M02, r02 = m.b * M20 + m.a * M02, r11 = m.ws * M11;
+        const float r21 = m.w3 * k21, r12 = m.w3 * k12, r22 = m.w4 * k22;
+        const float R21 = r21 + 2.0f * ux * r11 + uy * r20;
+        const float R12 = r12 + 2.0f * uy * r11 + ux * r02;
+        const float R22 = r22 + 2.0f * ux * r12 + 2.0f * uy * r21 + ux * ux * r02 + uy * uy * r20 + 4.0f * ux * uy * r11;
+        g[0][j] = g[0][j] - (R22 - r20 - r02);
+        g[1][j] = g[1][j] - 0.5f * (r20 - R12 - R22);
+        g[3][j] = g[3][j] - 0.5f * (r20 + R12 - R22);
+        g[2][j] = g[2][j] - 0.5f * (r02 - R21 - R22);
+        g[4][j] = g[4][j] - 0.5f * (r02 + R21 - R22);
+        g[5][j] = g[5][j] - 0.25f * (r11 + R21 + R12 + R22);
+        g[7][j] = g[7][j] - 0.25f * (r11 - R21 - R12 + R22);
+        g[6][j] = g[6][j] - 0.25f * (-r11 + R21 - R12 + R22);
+        g[8][j] = g[8][j] - 0.25f * (-r11 - R21 + R12 + R22);
+    }
 }
 
 // the collision selected at compile time: 0 BGK, 1 central moments
@@ -155,9 +200,10 @@ __device__ __forceinline__ void collide(float (&g)[9][V], int j, const StepParam
         cm_collide<V>(g, j, p.bgk, p.cm);
 }
 
-// the same collision at the relaxation rate om of a sponge column (open
-// channel, Sec. 2: no body force, so only the rate-dependent constants change;
-// the central-moment collision relaxes the shear moments at om)
+// the same collision at the relaxation rate om of a sponge column, without
+// body force (open channel, Sec. 2: the force terms are compiled out and only
+// the rate-dependent constants change; the central-moment collision relaxes
+// the shear moments at om)
 template <int COLL, int V>
 __device__ __forceinline__ void collide_at(float (&g)[9][V], int j, const StepParams& p, float om)
 {
@@ -166,13 +212,13 @@ __device__ __forceinline__ void collide_at(float (&g)[9][V], int j, const StepPa
     k.omm = 1.0f - om;
     k.om3 = 3.0f * om;
     if constexpr (COLL == 0) {
-        bgk_collide<V>(g, j, k);
+        bgk_collide<V, false>(g, j, k);
     } else {
         CmConsts m = p.cm;
         m.ws = om;
         m.a = 0.5f * (m.wb + om);
         m.b = 0.5f * (m.wb - om);
-        cm_collide<V>(g, j, k, m);
+        cm_collide<V, false>(g, j, k, m);
     }
 }
 
@@ -190,7 +236,8 @@ __device__ __forceinline__ void open_velocity9(const float (&g)[9], float& ux, f
 
 template <int S, int V, bool GENERAL, bool SCALED, int COLL, bool OPEN>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
-                                          typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane)
+                                          typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane,
+                                          bool grid_warp = false)
 {
     using T = typename Codec<S>::T;
     using K = Carry<S, SCALED>;
@@ -269,14 +316,20 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
         }
     }
     if constexpr (OPEN) {
-        if (GENERAL) {
+        if (GENERAL || grid_warp) {
             // links whose upstream node is solid (the square, or a bar of the
-            // open channel's grid) bounce back at this node
+            // open channel's grid) bounce back at this node; the bar rows among
+            // y - 1, y, y + 1 from one remainder.  Warps around the grid that
+            // are not wall or ring warps come here from the test-free path.
+            const int r0 = y % p.gperiod;
+            const bool bar_m = y > 0 && (r0 == 0 ? p.gperiod - 1 : r0 - 1) >= p.ggap;
+            const bool bar_0 = r0 >= p.ggap;
+            const bool bar_p = y + 1 < p.ny && (r0 + 1 == p.gperiod ? 0 : r0 + 1) >= p.ggap;
 #pragma unroll
             for (int q = 1; q < 9; ++q) {
                 const int ex = cx(q), ys = y - cy(q);
                 const bool sq_row = ys >= oy0 && ys < oy1;
-                const bool grid_row = ys >= 0 && ys < p.ny && ys % p.gperiod >= p.ggap;
+                const bool grid_row = cy(q) == 1 ? bar_m : (cy(q) == 0 ? bar_0 : bar_p);
                 if (!sq_row && !grid_row) continue;
                 bool hit[V];
                 bool any = false;
@@ -332,7 +385,7 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
         for (int j = 0; j < V; ++j) collide<COLL, V>(g, j, p);
     }
     if constexpr (OPEN) {
-        if (GENERAL && y % p.gperiod >= p.ggap) {
+        if ((GENERAL || grid_warp) && y % p.gperiod >= p.ggap) {  // this row is a bar row
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const int x = x0 + j;
@@ -500,11 +553,19 @@ __global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
     const bool wall_row = y == 0 || y == p.ny - 1;
     const bool ring = p.ox1 > p.ox0 && y >= p.ry0 && y <= p.ry1 && seg >= p.rs0 && seg <= p.rs1;
     if constexpr (OPEN) {
-        const bool grid = seg >= p.gs0 && seg <= p.gs1;  // segments around the entrance grid
-        if (wall_row || ring || grid)
-            step_warp<S, V, true, SCALED, COLL, true>(p, src, dst, c, y, seg, lane);
+        // segments around the entrance grid, in rows that are bars or next to
+        // one (a row whose neighbours are fluid has no link into a bar)
+        bool grid = false;
+        if (seg >= p.gs0 && seg <= p.gs1) {
+            const bool bar = y % p.gperiod >= p.ggap;
+            const bool bar_below = y > 0 && (y - 1) % p.gperiod >= p.ggap;
+            const bool bar_above = y + 1 < p.ny && (y + 1) % p.gperiod >= p.ggap;
+            grid = bar || bar_below || bar_above;
+        }
+        if (wall_row || ring)
+            step_warp<S, V, true, SCALED, COLL, true>(p, src, dst, c, y, seg, lane, grid);
         else
-            step_warp<S, V, false, SCALED, COLL, true>(p, src, dst, c, y, seg, lane);
+            step_warp<S, V, false, SCALED, COLL, true>(p, src, dst, c, y, seg, lane, grid);
     } else {
         if (wall_row || ring)
             step_warp<S, V, true, SCALED, COLL, false>(p, src, dst, c, y, seg, lane);
