@@ -589,16 +589,23 @@ int wgrad(cnn_model* m, int l, const bf16* x, const bf16* dy, int batch, cudaStr
 {
     const int cin = l == 0 ? kCin0 : kC;
     const int kp = kpad_fwd(cin);
-    const int tiles = batch * (m->H / kTH) * (m->W / kTW);
-    const int nblk = tiles < kWgradBlocks ? tiles : kWgradBlocks;
-    if (cin == kC)
-        conv_wgrad_kernel<kC><<<nblk, 128, 0, s>>>(x, dy, batch, m->H, m->W, m->wpart);
-    else
-        conv_wgrad_kernel<kCin0><<<nblk, 128, 0, s>>>(x, dy, batch, m->H, m->W, m->wpart);
+    int nblk = 0;
+    if (cin == kC && m->conv_path == 0 && conv3x3_wgrad_tc_supported(batch, m->H, m->W)) {
+        // hidden layers on the tensor cores (tcgen05): partial sums per CTA
+        if (int rc = conv3x3_wgrad_tc(x, dy, m->wpart, batch, m->H, m->W, m->err, s, &nblk)) return rc;
+    } else {
+        const int tiles = batch * (m->H / kTH) * (m->W / kTW);
+        nblk = tiles < kWgradBlocks ? tiles : kWgradBlocks;
+        if (cin == kC)
+            conv_wgrad_kernel<kC><<<nblk, 128, 0, s>>>(x, dy, batch, m->H, m->W, m->wpart);
+        else
+            conv_wgrad_kernel<kCin0><<<nblk, 128, 0, s>>>(x, dy, batch, m->H, m->W, m->wpart);
+        count_launches(1);
+    }
     const int n = kC * kp;
     reduce_partials_kernel<<<(n + 255) / 256, 256, 0, s>>>(m->wpart, nblk, n, m->grad + m->off[l]);
     LBM_CUDA(cudaGetLastError());
-    count_launches(2);
+    count_launches(1);
     return LBM_OK;
 }
 

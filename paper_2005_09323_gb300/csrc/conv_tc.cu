@@ -642,6 +642,260 @@ bool tc_shape(int B, int H, int W, TcShape& sh)
 
 size_t tc_smem_bytes(const TcShape& sh) { return 1024 + kWBytes + (size_t)kTcStages * 3 * sh.copy_stride; }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of a 32 -> 32 hidden layer (the layer's input x, its output
+// gradient dy, both NHWC BF16) on the tensor cores:
+//   dW[co][(ky*3 + kx)*32 + ci] = sum over pixels p of dy[p][co] x[p + (ky - 1, kx - 1)][ci],
+//   db[co] = sum over pixels of dy[p][co],
+// with x zero outside the image (the forward pass's padding).  The reduction
+// runs over pixels.  Per output row y and 128-pixel column half x0, one chain
+// of MMAs per ky, D_ky[m][co] += sum_p A_ky[m][p] B[co][p], with
+//   A_ky[kx*32 + ci][p] = x[y + ky - 1][x0 + p + kx - 1][ci]  (kx = 0, 1, 2),
+//   A_ky[96 + c][p]     = (c == 0),                           (lane 96: db)
+//   B[co][p]            = dy[y][x0 + p][co].
+// Both operands are MN-major with 64-byte swizzle, exactly as TMA lays out the
+// NHWC rows (each pixel's 32 channels one 64-byte row: 32 elements along MN,
+// the pixel along K): A's four 32-element groups along M are the three copies
+// of the input row that TMA loads at x offsets -1, 0, +1 and a constant plane,
+// kWgCopy bytes apart (the descriptor's leading offset), 8-pixel groups 512 B
+// apart (its stride offset).  M = 128, N = 32, K = 16 pixels per MMA.
+// A CTA takes bands of kWgBand output rows of one 128-pixel half of an image;
+// each input row is loaded once per band and serves three output rows.  The
+// three accumulators (3 x 32 columns) stay in tensor memory for the CTA's
+// whole share; the epilogue writes the CTA's partial sums in the layout of the
+// fixed-order cross-CTA reduction ([co][304], bias at column 288).
+constexpr int kWgThreads = 192;             // TMA producer, MMA issuer, 4 epilogue warps
+constexpr int kWgBand = 16;                 // output rows per work unit
+constexpr int kWgInSlots = 4;               // input-row ring
+constexpr int kWgDySlots = 2;               // output-gradient-row ring
+constexpr uint32_t kWgCopy = 128 * 64;      // one 128-pixel row of 32 channels
+constexpr uint32_t kWgSlot = 4 * kWgCopy;   // three x-shifted copies and the constant plane
+constexpr uint32_t kWgCols = 128;           // tensor-memory columns (power of 2; 96 used)
+// the instruction descriptor of kIdesc with A and B MN-major (bits 15, 16)
+constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);
+
+// shared-memory descriptor of an MN-major operand with 64-byte swizzle: the
+// 64-byte rows are successive K (pixels), 8-row groups 512 B apart (stride
+// offset); successive 32-element groups along MN lbo bytes apart (leading
+// offset), descriptor version 1
+__device__ inline uint64_t sw64_mn_desc(uint32_t saddr, uint32_t lbo)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // SWIZZLE_64B
+    return d;
+}
+
+__device__ inline void umma_f16_mn(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdescMN), "r"(accumulate)
+        : "memory");
+}
+
+struct WgShape {
+    int B, H, W;
+    int halves, bands, n_units;  // units: (image, band of output rows, 128-pixel half)
+};
+
+__device__ inline void wg_unit(const WgShape& sh, int u, int& b, int& y0, int& y1, int& x0)
+{
+    const int half = u % sh.halves, rest = u / sh.halves;
+    const int band = rest % sh.bands;
+    b = rest / sh.bands;
+    x0 = half * 128;
+    y0 = band * kWgBand;
+    y1 = y0 + kWgBand < sh.H ? y0 + kWgBand : sh.H;
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1)
+    conv_wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dymap,
+                         const WgShape sh, float* __restrict__ partial, int32_t* err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t in_full[kWgInSlots];
+    __shared__ __align__(8) uint64_t in_empty[kWgInSlots];
+    __shared__ __align__(8) uint64_t dy_full[kWgDySlots];
+    __shared__ __align__(8) uint64_t dy_empty[kWgDySlots];
+    __shared__ __align__(8) uint64_t done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+
+    const uint32_t raw = smem_addr(smem_raw);
+    unsigned char* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned (swizzle atoms)
+    const uint32_t in_s = smem_addr(smem);
+    const uint32_t dy_s = in_s + kWgInSlots * kWgSlot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // the constant plane of every input slot: channel 0 = 1 and the rest 0 in
+    // each pixel row (lane 96 of A, the bias gradient), swizzled as TMA would:
+    // logical 16-byte chunk 0 of row p sits at chunk (p >> 1) & 3
+    for (int i = threadIdx.x; i < kWgInSlots * 128 * 4; i += kWgThreads) {
+        const int sl = i / 512, p = (i >> 2) & 127, c = i & 3;
+        const uint4 v = c == ((p >> 1) & 3) ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(smem + sl * kWgSlot + 3 * kWgCopy + p * 64 + c * 16) = v;
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kWgInSlots; ++k) {
+            mbar_init(smem_addr(&in_full[k]), 1);
+            mbar_init(smem_addr(&in_empty[k]), 1);
+        }
+        for (int k = 0; k < kWgDySlots; ++k) {
+            mbar_init(smem_addr(&dy_full[k]), 1);
+            mbar_init(smem_addr(&dy_empty[k]), 1);
+        }
+        mbar_init(smem_addr(&done), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(kWgCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // constant planes -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- TMA producer: per unit the input rows y0 - 1 .. y1 and
+        // the output-gradient rows y0 .. y1 - 1, in the order the MMAs use them
+        if (lane == 0) {
+            int nin = 0, ndy = 0;
+            for (int u = blockIdx.x; u < sh.n_units && !abort_flag; u += gridDim.x) {
+                int b, y0, y1, x0;
+                wg_unit(sh, u, b, y0, y1, x0);
+                for (int i = 0; i < (y1 - y0) + 2; ++i) {
+                    const int r = y0 - 1 + i;
+                    const int sl = nin % kWgInSlots;
+                    if (nin >= kWgInSlots &&
+                        !mbar_wait_cycles(smem_addr(&in_empty[sl]), ((nin / kWgInSlots) - 1) & 1, kTcWaitCycles)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const uint32_t bar = smem_addr(&in_full[sl]);
+                    mbar_expect_tx(bar, 3 * kWgCopy);
+#pragma unroll
+                    for (int kx = 0; kx < 3; ++kx)
+                        tma_load_4d(in_s + sl * kWgSlot + kx * kWgCopy, &xmap, 0, x0 + kx - 1, r, b, bar);
+                    ++nin;
+                    if (i >= 2) {  // the output row r - 1 has its three input rows
+                        const int d = ndy % kWgDySlots;
+                        if (ndy >= kWgDySlots &&
+                            !mbar_wait_cycles(smem_addr(&dy_empty[d]), ((ndy / kWgDySlots) - 1) & 1, kTcWaitCycles)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                        const uint32_t dbar = smem_addr(&dy_full[d]);
+                        mbar_expect_tx(dbar, kWgCopy);
+                        tma_load_4d(dy_s + d * kWgCopy, &dymap, 0, x0, r - 1, b, dbar);
+                        ++ndy;
+                    }
+                }
+            }
+            // the shared memory must outlive every copy issued into it
+            for (int kk = nin - kWgInSlots > 0 ? nin - kWgInSlots : 0; kk < nin; ++kk)
+                mbar_wait_cycles(smem_addr(&in_full[kk % kWgInSlots]), (kk / kWgInSlots) & 1, kTcWaitCycles);
+            for (int kk = ndy - kWgDySlots > 0 ? ndy - kWgDySlots : 0; kk < ndy; ++kk)
+                mbar_wait_cycles(smem_addr(&dy_full[kk % kWgDySlots]), (kk / kWgDySlots) & 1, kTcWaitCycles);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int nin = 0, ndy = 0, rows = 0;
+            for (int u = blockIdx.x; u < sh.n_units && !abort_flag; u += gridDim.x) {
+                int b, y0, y1, x0;
+                wg_unit(sh, u, b, y0, y1, x0);
+                const int n_out = y1 - y0, base = nin;  // input row y0 - 1 is number base
+                bool ok = true;
+                for (int j = 0; j < n_out && ok; ++j) {
+                    for (int i = j == 0 ? 0 : j + 2; i <= j + 2 && ok; ++i)
+                        ok = mbar_wait_cycles(smem_addr(&in_full[(base + i) % kWgInSlots]),
+                                              ((base + i) / kWgInSlots) & 1, kTcWaitCycles);
+                    if (ok)
+                        ok = mbar_wait_cycles(smem_addr(&dy_full[ndy % kWgDySlots]), (ndy / kWgDySlots) & 1,
+                                              kTcWaitCycles);
+                    if (!ok || abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t b0 = dy_s + (ndy % kWgDySlots) * kWgCopy;
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky) {
+                        const uint32_t a0 = in_s + ((base + j + ky) % kWgInSlots) * kWgSlot;
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks)
+                            umma_f16_mn(tmem + ky * 32, sw64_mn_desc(a0 + ks * 1024, kWgCopy),
+                                        sw64_mn_desc(b0 + ks * 1024, kWgCopy), (rows | ks) != 0);
+                    }
+                    umma_commit(smem_addr(&dy_empty[ndy % kWgDySlots]));
+                    ++ndy;
+                    umma_commit(smem_addr(&in_empty[(base + j) % kWgInSlots]));  // its last output row
+                    ++rows;
+                }
+                if (!ok) {
+                    abort_flag = 1;
+                    break;
+                }
+                // the unit's last two input rows are free as well
+                umma_commit(smem_addr(&in_empty[(base + n_out) % kWgInSlots]));
+                umma_commit(smem_addr(&in_empty[(base + n_out + 1) % kWgInSlots]));
+                nin = base + n_out + 2;
+            }
+            // every MMA issued completes before the epilogue reads or the memory is freed
+            umma_commit(smem_addr(&done));
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warp w reads tensor-memory lanes 32 (w % 4) ..
+        const int q = warp & 3, m = 32 * q + lane;
+        float* out = partial + (int64_t)blockIdx.x * 32 * 304;
+        const bool work = (int)blockIdx.x < sh.n_units;
+        bool ok = mbar_wait_cycles(smem_addr(&done), 0, kTcWaitCycles);
+        ok = __all_sync(0xffffffffu, ok) && !abort_flag;
+        if (!ok) abort_flag = 1;
+        tc_fence_after();
+#pragma unroll 1
+        for (int ky = 0; ky < 3; ++ky) {
+            uint32_t r[32];
+            if (ok && work) {
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ky * 32), r);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c) r[c] = 0u;
+            }
+            if (m < 96) {
+                const int col = (ky * 3 + m / 32) * 32 + (m & 31);
+#pragma unroll
+                for (int co = 0; co < 32; ++co) out[co * 304 + col] = __uint_as_float(r[co]);
+            } else if (m == 96 && ky == 1) {
+#pragma unroll
+                for (int co = 0; co < 32; ++co) out[co * 304 + 288] = __uint_as_float(r[co]);
+            }
+        }
+        if (m < 32)  // padding columns of co = m
+            for (int c = 289; c < 304; ++c) out[m * 304 + c] = 0.f;
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0 && err) atomicExch(err, 1);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kWgCols) : "memory");
+    }
+}
+
 }  // namespace
 
 bool conv3x3_tc_supported(int B, int H, int W)
@@ -715,6 +969,44 @@ int conv3x3_tc(const void* x, const void* w, const void* mask, void* out, int B,
         return LBM_OK;
     };
     return bwd ? launch(conv_tc_kernel<true>) : launch(conv_tc_kernel<false>);
+}
+
+bool conv3x3_wgrad_tc_supported(int B, int H, int W)
+{
+    return tensor_map_encoder() != nullptr && B >= 1 && H >= 1 && W >= 128 && W % 128 == 0;
+}
+
+int conv3x3_wgrad_tc(const void* x, const void* dy, float* partial, int B, int H, int W, int32_t* err,
+                     cudaStream_t s, int* nblk)
+{
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(LBM_ERR_CUDA, "conv3x3_wgrad_tc: cuTensorMapEncodeTiled unavailable");
+    if (!conv3x3_wgrad_tc_supported(B, H, W)) return fail(LBM_ERR_ARG, "conv3x3_wgrad_tc: width must be a multiple of 128");
+    int dev = 0, sms = 152;
+    LBM_CUDA(cudaGetDevice(&dev));
+    LBM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUtensorMap maps[2];
+    const void* src[2] = {x, dy};
+    const cuuint64_t dims[4] = {32, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {64, (cuuint64_t)W * 64, (cuuint64_t)H * W * 64};
+    const cuuint32_t box[4] = {32, 128, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult r = encode(&maps[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(src[k]), dims, strides,
+                                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LBM_ERR_CUDA, "conv3x3_wgrad_tc: cuTensorMapEncodeTiled failed");
+    }
+    WgShape sh{B, H, W, W / 128, (H + kWgBand - 1) / kWgBand, 0};
+    sh.n_units = B * sh.bands * sh.halves;
+    const int grid = sh.n_units < sms ? sh.n_units : sms;
+    const size_t smem = 1024 + (size_t)kWgInSlots * kWgSlot + (size_t)kWgDySlots * kWgCopy;
+    LBM_CUDA(cudaFuncSetAttribute(conv_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conv_wgrad_tc_kernel<<<grid, kWgThreads, smem, s>>>(maps[0], maps[1], sh, partial, err);
+    LBM_CUDA(cudaGetLastError());
+    count_launches(1);
+    *nblk = grid;
+    return LBM_OK;
 }
 
 }  // namespace lbm

@@ -50,6 +50,12 @@ const std::vector<StepVariant>& step_variants();
 // timeout.  Supported shapes: W a multiple of 128 or a divisor of 128 (>= 8),
 // H a multiple of 2 * 128 / min(W, 128).
 bool conv3x3_tc_supported(int B, int H, int W);
+// weight gradient of a 32 -> 32 layer on the tensor cores (conv_tc.cu): per-CTA
+// partial sums [nblk][32][304] (bias at column 288) for the fixed-order
+// reduction; supported for widths that are a multiple of 128
+bool conv3x3_wgrad_tc_supported(int B, int H, int W);
+int conv3x3_wgrad_tc(const void* x, const void* dy, float* partial, int B, int H, int W, int32_t* err,
+                     cudaStream_t s, int* nblk);
 int conv3x3_tc(const void* x, const void* w, const void* mask, void* out, int B, int H, int W, bool bwd,
                int32_t* err, cudaStream_t s);
 

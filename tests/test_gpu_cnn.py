@@ -53,7 +53,7 @@ def model(L, request):
 
 
 @pytest.mark.parametrize("H,W,B", [(8, 32, 3), (16, 64, 2), (8, 256, 2), (32, 16, 1), (8, 128, 3), (64, 256, 2),
-                                   (24, 32, 2), (8, 48, 2), (8, 16, 2)])
+                                   (24, 32, 2), (8, 48, 2), (8, 16, 2), (40, 128, 2)])
 def test_tensor_core_path_matches_mma_sync(L, H, W, B):
     """The tcgen05 hidden layers against the mma.sync ones on the same model and
     inputs, for every block geometry (128-pixel blocks of 128/W rows, or of one
@@ -100,6 +100,31 @@ def test_tensor_core_forward_at_full_size_matches_oracle(L, orc):
         ref, _ = cnn.forward(p, x, store=bf16_round)
         got = pred.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-2 * (np.abs(ref).max() + 1e-3), (got, ref)
+    finally:
+        L.cnn_destroy(m)
+
+
+def test_tensor_core_gradient_at_full_size_matches_oracle(L, orc):
+    """64 x 256 inputs: the hidden layers' forward, data gradients and weight
+    gradients all on tcgen05 (the weight gradient reduces over pixels with
+    MN-major operands, four bands of 16 rows per image half).  Against the
+    oracle with BF16 storage of activations and gradients, 1.5e-2 relative L2
+    per layer, and the bias gradients."""
+    from oracle import cnn
+    m = L.cnn_create(64, 256, 2, 5)
+    try:
+        xt, x = inputs(2, 64, 256, 4)
+        y = np.array([0.7, -0.4], dtype=np.float32)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        L.cnn_gradient(m, xt, torch.tensor(y, device="cuda"), loss)
+        L.cnn_status(m)
+        g = L.cnn_get_gradient(m).astype(np.float64)
+        p = conv_layers_bf16(L.cnn_get_params(m))
+        _, ref16 = cnn.loss_and_grad(p, x, y.astype(np.float64), store=bf16_round)
+        off, _ = cnn.offsets()
+        for l in range(4):
+            sl = slice(off[l], off[l + 1])
+            assert np.linalg.norm(g[sl] - ref16[sl]) < 1.5e-2 * np.linalg.norm(ref16[sl]), l
     finally:
         L.cnn_destroy(m)
 
