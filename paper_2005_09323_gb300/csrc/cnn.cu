@@ -375,19 +375,31 @@ __global__ void head_backward_kernel(int B, int P, const float* pooled, const fl
     for (int i = tid; i < B * kC; i += blockDim.x) seed[i] = dp[i / kC] * head[i % kC] / (float)P;
 }
 
-// dY4[b][p][c] = seed[b][c] * (act4 > 0)
-__global__ void head_spread_kernel(const bf16* __restrict__ act, const float* __restrict__ seed, int B, int P,
+// dY4[b][p][c] = seed[b][c] * (act4 > 0): grid.y = image, one thread per
+// 16-byte vector (8 channels of a pixel), no index division
+__global__ void head_spread_kernel(const bf16* __restrict__ act, const float* __restrict__ seed, int P,
                                    bf16* __restrict__ dy)
 {
-    const int64_t n2 = (int64_t)B * P * kC / 2;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = 2 * i;
-        const int c = (int)(e % kC);
-        const int b = (int)(e / ((int64_t)P * kC));
-        const __nv_bfloat162 a = reinterpret_cast<const __nv_bfloat162*>(act)[i];
-        const float v0 = __bfloat162float(a.x) > 0.f ? seed[b * kC + c] : 0.f;
-        const float v1 = __bfloat162float(a.y) > 0.f ? seed[b * kC + c + 1] : 0.f;
-        reinterpret_cast<__nv_bfloat162*>(dy)[i] = __floats2bfloat162_rn(v0, v1);
+    __shared__ float sd[kC];
+    const int b = blockIdx.y;
+    if (threadIdx.x < kC) sd[threadIdx.x] = seed[b * kC + threadIdx.x];
+    __syncthreads();
+    const uint4* a = reinterpret_cast<const uint4*>(act + (int64_t)b * P * kC);
+    uint4* d = reinterpret_cast<uint4*>(dy + (int64_t)b * P * kC);
+    const int64_t nv = (int64_t)P * (kC / 8);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c0 = (int)(i & (kC / 8 - 1)) * 8;  // channel of the vector's first element
+        const uint4 v = a[i];
+        const __nv_bfloat162* e = reinterpret_cast<const __nv_bfloat162*>(&v);
+        uint4 o;
+        __nv_bfloat162* oe = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float v0 = __bfloat162float(e[k].x) > 0.f ? sd[c0 + 2 * k] : 0.f;
+            const float v1 = __bfloat162float(e[k].y) > 0.f ? sd[c0 + 2 * k + 1] : 0.f;
+            oe[k] = __floats2bfloat162_rn(v0, v1);
+        }
+        d[i] = o;
     }
 }
 
@@ -616,7 +628,11 @@ int gradient(cnn_model* m, const bf16* x, const float* y, int batch, float* loss
     const int P = m->H * m->W;
     head_backward_kernel<<<1, 256, 0, s>>>(batch, P, m->pooled, m->pred, y, m->master + m->off[kLayers],
                                           m->grad + m->off[kLayers], m->seed, loss);
-    head_spread_kernel<<<4 * 152, 256, 0, s>>>(m->act[kLayers - 1], m->seed, batch, P, m->dy[0]);
+    {
+        const int64_t nv = (int64_t)P * (kC / 8);
+        const int gx = (int)std::min<int64_t>((nv + 255) / 256, 64);
+        head_spread_kernel<<<dim3(gx, batch), 256, 0, s>>>(m->act[kLayers - 1], m->seed, P, m->dy[0]);
+    }
     LBM_CUDA(cudaGetLastError());
     count_launches(2);
     int cur = 0;

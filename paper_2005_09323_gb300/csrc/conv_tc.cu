@@ -648,31 +648,41 @@ size_t tc_smem_bytes(const TcShape& sh) { return 1024 + kWBytes + (size_t)kTcSta
 //   dW[co][(ky*3 + kx)*32 + ci] = sum over pixels p of dy[p][co] x[p + (ky - 1, kx - 1)][ci],
 //   db[co] = sum over pixels of dy[p][co],
 // with x zero outside the image (the forward pass's padding).  The reduction
-// runs over pixels.  Per output row y and 128-pixel column half x0, one chain
-// of MMAs per ky, D_ky[m][co] += sum_p A_ky[m][p] B[co][p], with
-//   A_ky[kx*32 + ci][p] = x[y + ky - 1][x0 + p + kx - 1][ci]  (kx = 0, 1, 2),
-//   A_ky[96 + c][p]     = (c == 0),                           (lane 96: db)
-//   B[co][p]            = dy[y][x0 + p][co].
-// Both operands are MN-major with 64-byte swizzle, exactly as TMA lays out the
-// NHWC rows (each pixel's 32 channels one 64-byte row: 32 elements along MN,
-// the pixel along K): A's four 32-element groups along M are the three copies
-// of the input row that TMA loads at x offsets -1, 0, +1 and a constant plane,
-// kWgCopy bytes apart (the descriptor's leading offset), 8-pixel groups 512 B
-// apart (its stride offset).  M = 128, N = 32, K = 16 pixels per MMA.
-// A CTA takes bands of kWgBand output rows of one 128-pixel half of an image;
-// each input row is loaded once per band and serves three output rows.  The
-// three accumulators (3 x 32 columns) stay in tensor memory for the CTA's
-// whole share; the epilogue writes the CTA's partial sums in the layout of the
+// runs over pixels.  A CTA takes bands of kWgBand output rows y0 .. y1 - 1 of
+// one 128-pixel half x0 of an image.  For each input row r = y0 - 1 .. y1 one
+// chain of 8 MMAs (K = 16 pixels each) accumulates
+//   D[m][n] += sum_p A_r[m][p] B_r[n][p],
+//   A_r[kx*32 + ci][p] = x[r][x0 + p + kx - 1][ci]   (kx = 0, 1, 2),
+//   A_r[96 + c][p]     = (c == 0),
+//   B_r[ky*32 + co][p] = dy[r - ky + 1][x0 + p][co]  if that row is in the band, else 0,
+// so that D[kx*32 + ci][ky*32 + co] is dW of tap (ky, kx) and D[96][32 + co]
+// is db.  M = 128, N = 96: each input row is read once and serves all nine taps.
+// Both operands are MN-major with 64-byte swizzle, as TMA lays out the NHWC
+// rows (a pixel's 32 channels one 64-byte row: 32 elements along MN, the pixel
+// along K), 8-pixel groups 512 B apart (the descriptors' stride offset):
+//   A: the three copies of the input row TMA loads at x offsets -1, 0, +1 and
+//      a constant plane, kWgCopy bytes apart (the leading offset);
+//   B: three consecutive slots of a ring of output-gradient rows, kWgCopy
+//      bytes apart.  The ring runs to lower addresses (stream row t in slot
+//      kWgDySlots - 1 - t mod kWgDySlots), so rows r + 1, r, r - 1 are slots
+//      s, s + 1, s + 2; the rows in slots 0 and 1 are written a second time
+//      into slots kWgDySlots and kWgDySlots + 1, so the three are contiguous
+//      at the wrap too.  The rows just outside a band enter the stream as zero
+//      rows (TMA loads far outside the image, zero-filled).
+// The accumulator (96 columns) stays in tensor memory for the CTA's whole
+// share; the epilogue writes the CTA's partial sums in the layout of the
 // fixed-order cross-CTA reduction ([co][304], bias at column 288).
 constexpr int kWgThreads = 192;             // TMA producer, MMA issuer, 4 epilogue warps
 constexpr int kWgBand = 16;                 // output rows per work unit
-constexpr int kWgInSlots = 4;               // input-row ring
-constexpr int kWgDySlots = 2;               // output-gradient-row ring
+constexpr int kWgInSlots = 3;               // input-row ring (5 slots measured the same)
+constexpr int kWgDySlots = 6;               // output-gradient ring (plus two mirror slots)
 constexpr uint32_t kWgCopy = 128 * 64;      // one 128-pixel row of 32 channels
 constexpr uint32_t kWgSlot = 4 * kWgCopy;   // three x-shifted copies and the constant plane
 constexpr uint32_t kWgCols = 128;           // tensor-memory columns (power of 2; 96 used)
-// the instruction descriptor of kIdesc with A and B MN-major (bits 15, 16)
-constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);
+constexpr int kWgZeroRow = -64;             // a row far outside any image: TMA fills zeros
+// kind::f16, FP32 accumulate, BF16 A and B, both MN-major (bits 15, 16), N = 96, M = 128
+constexpr uint32_t kIdescMN =
+    (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
 
 // shared-memory descriptor of an MN-major operand with 64-byte swizzle: the
 // 64-byte rows are successive K (pixels), 8-row groups 512 B apart (stride
@@ -712,6 +722,9 @@ __device__ inline void wg_unit(const WgShape& sh, int u, int& b, int& y0, int& y
     y1 = y0 + kWgBand < sh.H ? y0 + kWgBand : sh.H;
 }
 
+// ring slot of output-gradient stream row t (the ring runs to lower addresses)
+__device__ inline int wg_dy_slot(int t) { return kWgDySlots - 1 - t % kWgDySlots; }
+
 __global__ void __launch_bounds__(kWgThreads, 1)
     conv_wgrad_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dymap,
                          const WgShape sh, float* __restrict__ partial, int32_t* err)
@@ -728,12 +741,12 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const uint32_t raw = smem_addr(smem_raw);
     unsigned char* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned (swizzle atoms)
     const uint32_t in_s = smem_addr(smem);
-    const uint32_t dy_s = in_s + kWgInSlots * kWgSlot;
+    const uint32_t dy_s = in_s + kWgInSlots * kWgSlot;  // kWgDySlots + 2 slots of kWgCopy
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // the constant plane of every input slot: channel 0 = 1 and the rest 0 in
-    // each pixel row (lane 96 of A, the bias gradient), swizzled as TMA would:
-    // logical 16-byte chunk 0 of row p sits at chunk (p >> 1) & 3
+    // each pixel row (lane 96 of A), swizzled as TMA would: logical 16-byte
+    // chunk 0 of row p sits at chunk (p >> 1) & 3
     for (int i = threadIdx.x; i < kWgInSlots * 128 * 4; i += kWgThreads) {
         const int sl = i / 512, p = (i >> 2) & 127, c = i & 3;
         const uint4 v = c == ((p >> 1) & 3) ? make_uint4(0x3F80u, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
@@ -765,92 +778,93 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        // ---------------- TMA producer: per unit the input rows y0 - 1 .. y1 and
-        // the output-gradient rows y0 .. y1 - 1, in the order the MMAs use them
+        // ---------------- TMA producer.  Per unit the stream of output-
+        // gradient rows is: zero, zero, dy rows y0 .. y1 - 1, zero, zero; input
+        // row i (r = y0 - 1 + i) is issued after stream row i + 2, which its
+        // window (stream rows i .. i + 2) needs last.
         if (lane == 0) {
             int nin = 0, ndy = 0;
+            auto issue_dy = [&](int y, int b, int x0) -> bool {
+                const int sl = wg_dy_slot(ndy);
+                if (ndy >= kWgDySlots &&
+                    !mbar_wait_cycles(smem_addr(&dy_empty[sl]), ((ndy / kWgDySlots) - 1) & 1, kTcWaitCycles))
+                    return false;
+                const uint32_t bar = smem_addr(&dy_full[sl]);
+                const bool mirror = sl < 2;
+                mbar_expect_tx(bar, mirror ? 2 * kWgCopy : kWgCopy);
+                tma_load_4d(dy_s + sl * kWgCopy, &dymap, 0, x0, y, b, bar);
+                if (mirror) tma_load_4d(dy_s + (kWgDySlots + sl) * kWgCopy, &dymap, 0, x0, y, b, bar);
+                ++ndy;
+                return true;
+            };
             for (int u = blockIdx.x; u < sh.n_units && !abort_flag; u += gridDim.x) {
                 int b, y0, y1, x0;
                 wg_unit(sh, u, b, y0, y1, x0);
-                for (int i = 0; i < (y1 - y0) + 2; ++i) {
-                    const int r = y0 - 1 + i;
+                const int n_out = y1 - y0;
+                bool ok = issue_dy(kWgZeroRow, b, x0) && issue_dy(kWgZeroRow, b, x0);
+                for (int i = 0; i < n_out + 2 && ok; ++i) {
+                    ok = issue_dy(i < n_out ? y0 + i : kWgZeroRow, b, x0);
+                    if (!ok) break;
                     const int sl = nin % kWgInSlots;
                     if (nin >= kWgInSlots &&
                         !mbar_wait_cycles(smem_addr(&in_empty[sl]), ((nin / kWgInSlots) - 1) & 1, kTcWaitCycles)) {
-                        abort_flag = 1;
+                        ok = false;
                         break;
                     }
                     const uint32_t bar = smem_addr(&in_full[sl]);
                     mbar_expect_tx(bar, 3 * kWgCopy);
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx)
-                        tma_load_4d(in_s + sl * kWgSlot + kx * kWgCopy, &xmap, 0, x0 + kx - 1, r, b, bar);
+                        tma_load_4d(in_s + sl * kWgSlot + kx * kWgCopy, &xmap, 0, x0 + kx - 1, y0 - 1 + i, b, bar);
                     ++nin;
-                    if (i >= 2) {  // the output row r - 1 has its three input rows
-                        const int d = ndy % kWgDySlots;
-                        if (ndy >= kWgDySlots &&
-                            !mbar_wait_cycles(smem_addr(&dy_empty[d]), ((ndy / kWgDySlots) - 1) & 1, kTcWaitCycles)) {
-                            abort_flag = 1;
-                            break;
-                        }
-                        const uint32_t dbar = smem_addr(&dy_full[d]);
-                        mbar_expect_tx(dbar, kWgCopy);
-                        tma_load_4d(dy_s + d * kWgCopy, &dymap, 0, x0, r - 1, b, dbar);
-                        ++ndy;
-                    }
                 }
+                if (!ok) abort_flag = 1;
             }
             // the shared memory must outlive every copy issued into it
             for (int kk = nin - kWgInSlots > 0 ? nin - kWgInSlots : 0; kk < nin; ++kk)
                 mbar_wait_cycles(smem_addr(&in_full[kk % kWgInSlots]), (kk / kWgInSlots) & 1, kTcWaitCycles);
             for (int kk = ndy - kWgDySlots > 0 ? ndy - kWgDySlots : 0; kk < ndy; ++kk)
-                mbar_wait_cycles(smem_addr(&dy_full[kk % kWgDySlots]), (kk / kWgDySlots) & 1, kTcWaitCycles);
+                mbar_wait_cycles(smem_addr(&dy_full[wg_dy_slot(kk)]), (kk / kWgDySlots) & 1, kTcWaitCycles);
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int nin = 0, ndy = 0, rows = 0;
-            for (int u = blockIdx.x; u < sh.n_units && !abort_flag; u += gridDim.x) {
+            int nin = 0, ndy = 0;  // input rows and stream rows consumed
+            bool first = true, ok = true;
+            for (int u = blockIdx.x; u < sh.n_units && ok && !abort_flag; u += gridDim.x) {
                 int b, y0, y1, x0;
                 wg_unit(sh, u, b, y0, y1, x0);
-                const int n_out = y1 - y0, base = nin;  // input row y0 - 1 is number base
-                bool ok = true;
-                for (int j = 0; j < n_out && ok; ++j) {
-                    for (int i = j == 0 ? 0 : j + 2; i <= j + 2 && ok; ++i)
-                        ok = mbar_wait_cycles(smem_addr(&in_full[(base + i) % kWgInSlots]),
-                                              ((base + i) / kWgInSlots) & 1, kTcWaitCycles);
+                const int n_out = y1 - y0, t0 = ndy;  // the unit's first stream row
+                for (int i = 0; i < n_out + 2 && ok; ++i) {
+                    for (int t = i == 0 ? t0 : t0 + i + 2; t <= t0 + i + 2 && ok; ++t)
+                        ok = mbar_wait_cycles(smem_addr(&dy_full[wg_dy_slot(t)]), (t / kWgDySlots) & 1, kTcWaitCycles);
                     if (ok)
-                        ok = mbar_wait_cycles(smem_addr(&dy_full[ndy % kWgDySlots]), (ndy / kWgDySlots) & 1,
+                        ok = mbar_wait_cycles(smem_addr(&in_full[nin % kWgInSlots]), (nin / kWgInSlots) & 1,
                                               kTcWaitCycles);
                     if (!ok || abort_flag) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t b0 = dy_s + (ndy % kWgDySlots) * kWgCopy;
+                    const uint32_t a0 = in_s + (nin % kWgInSlots) * kWgSlot;
+                    const uint32_t b0 = dy_s + wg_dy_slot(t0 + i + 2) * kWgCopy;  // rows r + 1, r, r - 1
 #pragma unroll
-                    for (int ky = 0; ky < 3; ++ky) {
-                        const uint32_t a0 = in_s + ((base + j + ky) % kWgInSlots) * kWgSlot;
-#pragma unroll
-                        for (int ks = 0; ks < 8; ++ks)
-                            umma_f16_mn(tmem + ky * 32, sw64_mn_desc(a0 + ks * 1024, kWgCopy),
-                                        sw64_mn_desc(b0 + ks * 1024, kWgCopy), (rows | ks) != 0);
-                    }
-                    umma_commit(smem_addr(&dy_empty[ndy % kWgDySlots]));
-                    ++ndy;
-                    umma_commit(smem_addr(&in_empty[(base + j) % kWgInSlots]));  // its last output row
-                    ++rows;
+                    for (int ks = 0; ks < 8; ++ks)
+                        umma_f16_mn(tmem, sw64_mn_desc(a0 + ks * 1024, kWgCopy), sw64_mn_desc(b0 + ks * 1024, kWgCopy),
+                                    (first && ks == 0) ? 0u : 1u);
+                    first = false;
+                    umma_commit(smem_addr(&in_empty[nin % kWgInSlots]));
+                    ++nin;
+                    umma_commit(smem_addr(&dy_empty[wg_dy_slot(t0 + i)]));  // leaves the window
                 }
-                if (!ok) {
-                    abort_flag = 1;
-                    break;
-                }
-                // the unit's last two input rows are free as well
-                umma_commit(smem_addr(&in_empty[(base + n_out) % kWgInSlots]));
-                umma_commit(smem_addr(&in_empty[(base + n_out + 1) % kWgInSlots]));
-                nin = base + n_out + 2;
+                if (!ok) break;
+                // the window's last two rows are free as well
+                umma_commit(smem_addr(&dy_empty[wg_dy_slot(t0 + n_out + 2)]));
+                umma_commit(smem_addr(&dy_empty[wg_dy_slot(t0 + n_out + 3)]));
+                ndy = t0 + n_out + 4;
             }
+            if (!ok) abort_flag = 1;
             // every MMA issued completes before the epilogue reads or the memory is freed
             umma_commit(smem_addr(&done));
         }
@@ -1000,7 +1014,7 @@ int conv3x3_wgrad_tc(const void* x, const void* dy, float* partial, int B, int H
     WgShape sh{B, H, W, W / 128, (H + kWgBand - 1) / kWgBand, 0};
     sh.n_units = B * sh.bands * sh.halves;
     const int grid = sh.n_units < sms ? sh.n_units : sms;
-    const size_t smem = 1024 + (size_t)kWgInSlots * kWgSlot + (size_t)kWgDySlots * kWgCopy;
+    const size_t smem = 1024 + (size_t)kWgInSlots * kWgSlot + (size_t)(kWgDySlots + 2) * kWgCopy;
     LBM_CUDA(cudaFuncSetAttribute(conv_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conv_wgrad_tc_kernel<<<grid, kWgThreads, smem, s>>>(maps[0], maps[1], sh, partial, err);
     LBM_CUDA(cudaGetLastError());
