@@ -836,12 +836,18 @@ def run_ams_run(args):
     from paper_2005_09323_gb300 import lbmrare as L
     torch.cuda.set_device(0)
     L.lib()
-    w = workload(argparse.Namespace(workload="ams", clones=args.clones))
+    open_ch = args.ams_channel == "open"
+    if open_ch:  # the paper's channel (Sec. 2) with its production collision
+        w = workload(argparse.Namespace(workload="open", clones=args.clones or 256, collision=args.collision))
+        chan = dict(channel_kwargs(w), collision=w["collision"])
+    else:
+        w = workload(argparse.Namespace(workload="ams", clones=args.clones))
+        chan = dict(tau=TAU, gx=GX)
     n, t_a, J, stride = w["clones"], 2000, 40, 250
     window = args.ams_window
     stream = torch.cuda.current_stream()
-    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], tau=TAU, gx=GX, storage=L.STORAGE[args.storage],
-                   max_steps=t_a, ckpt_stride=stride, n_snapshots=N_SNAP)
+    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], storage=L.STORAGE[args.storage], max_steps=t_a,
+                   ckpt_stride=stride, n_snapshots=N_SNAP, **chan)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     runs, inits, iters, launches = [], [], [], 0
     for step in range(args.warmup + args.steps):
@@ -881,10 +887,12 @@ def run_ams_run(args):
         "metric": "AMS run time (initial ensemble + kill/branch iterations)", "value": ms, "unit": "ms per run",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"AMS: N={n} trajectories of {w['nx']}x{w['ny']} ({args.storage}), T_a={t_a}, "
+        "config": {"workload": f"AMS: N={n} trajectories of {w['nx']}x{w['ny']} "
+                               f"{'open channel of Sec. 2, ' + w['collision'] + ' collision, ' if open_ch else ''}"
+                               f"({args.storage}), T_a={t_a}, "
                                f"up to {J} iterations, score = {score}, checkpoints every {stride} steps, "
                                f"App. D bank of {N_SNAP} refilled at each branch",
-                   "storage": args.storage, "score_window": window},
+                   "storage": args.storage, "score_window": window, "channel": args.ams_channel},
         "initial_ensemble": {"ms": init_ms, "glups": n * w["nx"] * w["ny"] * t_a / (init_ms / 1e3) / 1e9},
         "branch_phase": {"iterations": it_med, "ms_per_iteration": (ms - init_ms) / max(it_med, 1)},
         "gpu_launches": launches // max(len(runs), 1)}))
@@ -1033,6 +1041,8 @@ def main():
                          "channel, BGK otherwise)")
     ap.add_argument("--check-period", type=int, default=CHECK_PERIOD,
                     help="perturb-check: steps between in-place perturbations (the paper: tau_c / 2)")
+    ap.add_argument("--ams-channel", default="periodic", choices=["periodic", "open"],
+                    help="ams-run: the periodic AMS channel or the paper's open channel")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()

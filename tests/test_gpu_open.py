@@ -227,3 +227,56 @@ def test_open_argument_errors(L):
     with pytest.raises(L.LbmError):
         L.lbm_step_noalloc(cfg, n, a, torch.zeros_like(a), torch.zeros(n, dtype=torch.float64, device="cuda"),
                            torch.cuda.current_stream())
+
+
+def test_open_branch_replays_bitwise(L):
+    """AMS branching on the open channel: with eps = 0 the branch is the source
+    trajectory bit for bit (state, drag and the square's observables); with a
+    perturbation it departs from the source after t_b"""
+    kw = dict(OPEN, collision="cm", max_steps=160, ckpt_stride=25, n_snapshots=2)
+    with Ens(L, 3, seed=6, **kw) as e:
+        L.lbm_ensemble_set_observables(e.h, True)
+        L.lbm_ensemble_step(e.h, 120)
+        L.lbm_ensemble_branch(e.h, 1, 2, 87, 0.0, 3, 1)
+        assert list(L.lbm_ensemble_time(e.h, 3)) == [120, 87, 120]
+        L.lbm_ensemble_step_clones(e.h, 33, [1])
+        assert np.array_equal(e.pops(1), e.pops(2))
+        d = e.drag(0, 120)
+        assert np.array_equal(d[1], d[2])
+        o = np.zeros((3, 120, 4))
+        L.lbm_ensemble_observables(e.h, 0, 120, o)
+        assert np.array_equal(o[1], o[2])
+        L.lbm_ensemble_set_snapshots(e.h, [0, 2])
+        L.lbm_ensemble_branch(e.h, 1, 2, 50, 0.002, 3, 2)
+        L.lbm_ensemble_step_clones(e.h, 70, [1])
+        d = e.drag(0, 120)
+        assert np.array_equal(d[1, :50], d[2, :50])
+        assert not np.array_equal(d[1, 50:], d[2, 50:])
+
+
+def test_open_gktl_and_ams_runs_are_deterministic(L):
+    """the GKTL and AMS drivers on the open channel: finite estimator weights,
+    rising AMS levels, and two runs from the same seeds agree bit for bit"""
+    n, t_a = 8, 200
+    kw = dict(OPEN, collision="cm", max_steps=t_a, ckpt_stride=25, n_snapshots=2)
+    results = []
+    for _ in range(2):
+        with Ens(L, n, seed=11, **kw) as e:
+            L.lbm_ensemble_set_snapshots(e.h, [0, 1])
+            logR = torch.zeros(4, dtype=torch.float64, device="cuda")
+            parent = torch.zeros((4, n), dtype=torch.int32, device="cuda")
+            L.lbm_gktl_run(e.h, 25, 4, 5.0, 0.002, 9, 0, logR, parent)
+            g = (logR.cpu().numpy(), parent.cpu().numpy(), e.drag(0, 100))
+        with Ens(L, n, seed=12, **kw) as e:
+            L.lbm_ensemble_set_snapshots(e.h, [0, 1])
+            Q = torch.zeros(n, dtype=torch.float64, device="cuda")
+            it, lw, levels = L.lbm_ams_run(e.h, t_a, 20, 6, float("inf"), 0.002, 13, Q)
+            a = (it, lw, np.asarray(levels), Q.cpu().numpy())
+        results.append((g, a))
+    (g0, a0), (g1, a1) = results
+    assert np.all(np.isfinite(g0[0])) and np.all((g0[1] >= 0) & (g0[1] < n))
+    assert a0[0] == 6 and np.isfinite(a0[1]) and np.all(np.diff(a0[2]) > 0)
+    for x, y in zip(g0, g1):
+        assert np.array_equal(x, y)
+    assert a0[0] == a1[0] and a0[1] == a1[1]
+    assert np.array_equal(a0[2], a1[2]) and np.array_equal(a0[3], a1[3])
