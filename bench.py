@@ -757,19 +757,27 @@ def run_ams_branch(args):
     bench step = one branch of 2000 lattice steps of one 512x128 trajectory of
     the AMS workload with a checkpoint every 250 steps, taken in turn from a
     pool of 16 trajectories; timed with step-chunk graphs (the default) and
-    with one direct launch per lattice step."""
+    with one direct launch per lattice step.  --ams-channel open: the same on
+    one trajectory of the open channel of Sec. 2 (two launches per step)."""
     import torch
 
     from paper_2005_09323_gb300 import lbmrare as L
     torch.cuda.set_device(0)
     L.lib()
-    w = workload(argparse.Namespace(workload="ams", clones=16))
+    open_ch = args.ams_channel == "open"
+    if open_ch:  # the paper's channel (Sec. 2) with its production collision
+        w = workload(argparse.Namespace(workload="open", clones=16, collision=args.collision))
+        chan = dict(channel_kwargs(w), collision=w["collision"])
+    else:
+        w = workload(argparse.Namespace(workload="ams", clones=16))
+        chan = dict(tau=TAU, gx=GX)
     n, branch, stride = 16, 2000, 250
-    if 2 * (args.steps + args.warmup) > n * (10000 // branch):
-        raise SystemExit("ams-branch: at most 27 steps + warm-up")
+    modes = [("graphs", True), ("direct", False)]
+    if len(modes) * (args.steps + args.warmup) > n * (10000 // branch):
+        raise SystemExit(f"ams-branch: at most {n * (10000 // branch) // len(modes)} steps + warm-up")
     stream = torch.cuda.current_stream()
-    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], tau=TAU, gx=GX, storage=L.STORAGE[args.storage],
-                   max_steps=10000, ckpt_stride=stride)
+    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], storage=L.STORAGE[args.storage], max_steps=10000,
+                   ckpt_stride=stride, **chan)
     e = L.lbm_ensemble_create(cfg, n, 1, stream)
     if args.variant != "auto":
         L.lbm_ensemble_set_variant(e, int(args.variant))
@@ -782,7 +790,7 @@ def run_ams_branch(args):
 
     res = {}
     launches = 0
-    for graphs in (True, False):
+    for mode, graphs in modes:
         L.lbm_ensemble_set_graphs(e, graphs)
         for _ in range(args.warmup):
             one_branch()
@@ -795,27 +803,27 @@ def run_ams_branch(args):
         ev[1].record(stream)
         torch.cuda.synchronize()
         ms = ev[0].elapsed_time(ev[1]) / args.steps
-        res[graphs] = ms
-        if graphs:
+        res[mode] = ms
+        if mode == "graphs":
             launches = L.lbm_launch_count() - l0
     L.lbm_ensemble_destroy(e)
     sites = w["nx"] * w["ny"]
     glups = {g: sites * branch / (ms / 1e3) / 1e9 for g, ms in res.items()}
     bps = BYTES_PER_SITE if args.storage == "fp32" else BYTES_PER_SITE // 2
     hbm, peak_kind = peaks()
-    achieved = bps * sites * branch / (res[True] / 1e3) / 1e9
+    achieved = bps * sites * branch / (res["graphs"] / 1e3) / 1e9
     print(json.dumps({
-        "metric": "AMS branch-phase stepping rate (one trajectory)", "value": glups[True], "unit": "GLUPS",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[True], "higher_is_better": True,
+        "metric": "AMS branch-phase stepping rate (one trajectory)", "value": glups["graphs"], "unit": "GLUPS",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["graphs"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"AMS branch: one {w['nx']}x{w['ny']} trajectory ({args.storage}), {branch} lattice "
                                f"steps per bench step, checkpoint every {stride} steps, pool of {n}",
-                   "storage": args.storage,
+                   "storage": args.storage, "channel": args.ams_channel,
                    "l2": "working set of one trajectory (two buffers) is L2-resident; no flush: this is the "
                          "branch phase as AMS runs it"},
-        "direct_launches": {"value": glups[False], "unit": "GLUPS", "ms_per_step": res[False],
-                            "us_per_lattice_step": 1e3 * res[False] / branch},
-        "graphs": {"us_per_lattice_step": 1e3 * res[True] / branch, "speedup": res[False] / res[True]},
+        "direct_launches": {"value": glups["direct"], "unit": "GLUPS", "ms_per_step": res["direct"],
+                            "us_per_lattice_step": 1e3 * res["direct"] / branch},
+        "graphs": {"us_per_lattice_step": 1e3 * res["graphs"] / branch, "speedup": res["direct"] / res["graphs"]},
         "roofline": {"bound": "latency", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs; algorithmic bytes of an L2-resident "
                                                    f"working set, so frac may exceed 1"},
