@@ -562,12 +562,23 @@ def run_return_time(args):
     tau 0.505, g_x 1e-6) after a 2000-step spin-up, with the averaging window
     equal to the horizon as in the paper's GKTL experiments: T_a = T = 10000
     steps, cloning every 500 steps, so that the tilted integral is T F_T.
-    k sigma_I = 2 with sigma_I the spread of that integral over direct runs.
-    Levels a = mean + z sigma of F_T (z = 2, 3) from the direct runs; the
-    direct estimate's relative error is binomial at the Gaussian tail
-    probability (the paper's unbiased reference), the GKTL one is measured over
-    independent replicas.  Wall time to 20% = seconds per replica x (relative
-    error / 0.2)^2."""
+    Levels a = mean + z sigma of F_T (z = 2, 3, 4) from the direct runs.  For
+    each level the GKTL runs are tilted towards it, as the paper chooses k for
+    the extremes of interest: k sigma_I = z with sigma_I the spread of the
+    integral over the direct runs, which centres the tilted F_T near the level
+    for a Gaussian integral.  The direct estimate's relative error is binomial
+    at the Gaussian tail probability (the paper's unbiased reference), the GKTL
+    one is measured over independent replicas.  Wall time to 20% = seconds per
+    replica x (relative error / 0.2)^2.
+
+    --rt-channel open: the same on the turbulent open channel of Sec. 2 (the
+    open workload: 64 trajectories of 513 x 129, central moments, tau 0.501),
+    where perturbed clones separate as the paper's cloning assumes: every
+    replica is a fresh ensemble spun up for 15000 steps (not timed), then
+    T_a = T = 20000 steps (10 tau_c) with cloning every 1000 steps (tau_c / 2);
+    the network sees 64 x 256 blocks of 2 x 2 nodes (the outlet column and the
+    top row are past the last whole block).  Every ensemble is autotuned
+    before it is stepped."""
     import math
 
     import numpy as np
@@ -576,19 +587,27 @@ def run_return_time(args):
     from paper_2005_09323_gb300 import lbmrare as L
     torch.cuda.set_device(0)
     L.lib()
-    w = WORKLOADS["gktl"]
-    nx, ny, n = w["nx"], w["ny"], w["clones"]
-    obst = (nx // 4 - w["side"] // 2, ny // 2 - w["side"] // 2, w["side"], w["side"])
-    spin, t_a, periods = 2000, 10000, 20
+    open_ch = args.rt_channel == "open"
+    if open_ch:  # the paper's turbulent channel (Sec. 2) with its production collision
+        w = workload(argparse.Namespace(workload="open", clones=args.clones or 64, collision=args.collision))
+        nx, ny, n, obst = w["nx"], w["ny"], w["clones"], w["obst"]
+        chan = dict(channel_kwargs(w), collision=w["collision"])
+        spin, t_a, periods, period = 15000, 20000, 20, 1000
+    else:
+        w = WORKLOADS["gktl"]
+        nx, ny, n = w["nx"], w["ny"], w["clones"]
+        obst = (nx // 4 - w["side"] // 2, ny // 2 - w["side"] // 2, w["side"], w["side"])
+        chan = dict(tau=TAU, gx=GX)
+        spin, t_a, periods, period = 2000, 10000, 20, PERIOD
     window = t_a
     R = max(3, args.steps)
     stream = torch.cuda.current_stream()
-    factor, rho_s, u_s = 4, 1000.0, 50.0
-    zs = (2.0, 3.0)
+    factor, rho_s, u_s = (2 if open_ch else 4), 1000.0, 50.0
+    zs = (2.0, 3.0, 4.0)
 
     def make(storage, seed, extra=0):
-        cfg = L.config(nx, ny, obstacle=obst, tau=TAU, gx=GX, max_steps=spin + t_a + extra, n_snapshots=N_SNAP,
-                       storage=storage)
+        cfg = L.config(nx, ny, obstacle=obst, max_steps=spin + t_a + extra, n_snapshots=N_SNAP, storage=storage,
+                       **chan)
         return L.lbm_ensemble_create(cfg, n, seed, stream)
 
     # learned score, trained on an ensemble run of its own (cost reported)
@@ -597,6 +616,7 @@ def run_return_time(args):
     H, W = ny // factor, nx // factor
     m = L.cnn_create(H, W, 64, 1)
     e = make("fp32", 777, extra=40 * 250 + 2000)
+    L.lbm_ensemble_autotune(e)
     L.lbm_ensemble_step(e, spin)
     n_snaps = 40
     x = torch.zeros((n_snaps * n, H, W, 8), dtype=torch.bfloat16, device="cuda")
@@ -610,6 +630,7 @@ def run_return_time(args):
 
     def replica(storage, k, kappa, learned, seed):
         e = make(storage, seed)
+        L.lbm_ensemble_autotune(e)
         if learned:
             L.lbm_ensemble_attach_score(e, m, factor, rho_s, u_s)
         L.lbm_ensemble_step(e, spin)
@@ -621,7 +642,7 @@ def run_return_time(args):
         corr = torch.zeros(n, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        L.lbm_gktl_run(e, PERIOD, periods, k, EPS, seed, window, logR, parent, integ, maxima,
+        L.lbm_gktl_run(e, period, periods, k, EPS, seed, window, logR, parent, integ, maxima,
                        kappa=kappa, correction_dev=corr, refresh_snapshots=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -636,41 +657,44 @@ def run_return_time(args):
     F = torch.cat([d["maxima"] for d in direct]).cpu().numpy()
     I = torch.cat([d["integ"] for d in direct]).cpu().numpy()
     mu, sd, sd_i = float(F.mean()), float(F.std()), float(I.std())
-    k = 2.0 / sd_i
     levels = [mu + z * sd for z in zs]
     p_gauss = [0.5 * math.erfc(z / math.sqrt(2.0)) for z in zs]
     variants = {"fp32_gktl": ("fp32", 0.0, False), "fp32_gktl_learned": ("fp32", 0.5, True),
                 "fp16_gktl_learned": ("fp16", 0.5, True)}
-    runs = {"plain_fp32_direct": direct}
+    # runs[name][j]: the replicas whose estimate serves level j (the direct
+    # runs serve every level; GKTL runs are tilted towards their level)
+    runs = {"plain_fp32_direct": [direct] * len(zs)}
     for name, (st, kappa, learned) in variants.items():
-        runs[name] = [replica(st, k, kappa, learned, 200 + r) for r in range(R)]
+        runs[name] = [[replica(st, z / sd_i, kappa, learned, 200 + 100 * jz + r) for r in range(R)]
+                      for jz, z in enumerate(zs)]
     L.cnn_destroy(m)
     lv = torch.tensor(levels, dtype=torch.float64, device="cuda")
     out = {}
-    for name, rs in runs.items():
-        ps = []
-        for d in rs:
-            p = torch.zeros(len(levels), dtype=torch.float64, device="cuda")
-            L.gktl_probability(d["k"], d["logR"], d["integ"], d["maxima"], lv, float(t_a), float(window), p,
-                               correction_dev=d["corr"])
-            ps.append(p.cpu().numpy())
-        ps = np.array(ps)  # [R][levels]
-        t_rep = float(np.mean([d["dt"] for d in rs]))
+    for name, per in runs.items():
         per_level = []
         for j, z in enumerate(zs):
-            mean = float(ps[:, j].mean())
+            ps = []
+            for d in per[j]:
+                p = torch.zeros(len(levels), dtype=torch.float64, device="cuda")
+                L.gktl_probability(d["k"], d["logR"], d["integ"], d["maxima"], lv, float(t_a), float(window), p,
+                                   correction_dev=d["corr"])
+                ps.append(float(p[j]))
+            ps = np.array(ps)
+            t_rep = float(np.mean([d["dt"] for d in per[j]]))
+            mean = float(ps.mean())
             if name == "plain_fp32_direct":
                 cv = math.sqrt((1 - p_gauss[j]) / (n * p_gauss[j]))
             else:
-                cv = float(ps[:, j].std(ddof=1) / mean) if mean > 0 else float("inf")
+                cv = float(ps.std(ddof=1) / mean) if mean > 0 else float("inf")
             need = (cv / 0.2) ** 2
-            per_level.append({"z": z, "level": levels[j], "P_mean": mean, "P_gauss": p_gauss[j],
+            per_level.append({"z": z, "level": levels[j], "k_sigma_I": z if name != "plain_fp32_direct" else 0.0,
+                              "P_mean": mean, "P_gauss": p_gauss[j], "replicas_reaching": int((ps > 0).sum()),
                               "relative_error_per_replica": cv, "replicas_for_20pct": need,
-                              "seconds_to_20pct": t_rep * need,
+                              "seconds_per_replica": t_rep, "seconds_to_20pct": t_rep * need,
+                              "distinct_ancestors_mean": float(np.mean([d["ancestors"] for d in per[j]])),
                               # one window per trajectory: waiting time in windows of T steps
                               "return_time_steps": (-window / math.log1p(-mean)) if 0 < mean < 1 else None})
-        out[name] = {"seconds_per_replica": t_rep, "levels": per_level,
-                     "distinct_ancestors_mean": float(np.mean([d["ancestors"] for d in rs]))}
+        out[name] = {"levels": per_level}
     j3 = len(zs) - 1
     plain = out["plain_fp32_direct"]["levels"][j3]["seconds_to_20pct"]
     best_name = min(variants, key=lambda v: out[v]["levels"][j3]["seconds_to_20pct"])
@@ -679,11 +703,16 @@ def run_return_time(args):
         "metric": "time to a 20%-accurate return-time estimate of extreme time-averaged drag",
         "value": best, "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": R, "warmup": 0,
         "data": "synthetic", "dtype": "per variant",
-        "config": {"workload": f"GKTL batched ensemble: N={n} clones, {nx}x{ny}, T_a=T={t_a} steps, cloning every "
-                               f"{PERIOD} steps, k sigma_I = 2, eps={EPS}, spin-up {spin} steps; levels mean + z sigma "
-                               f"of F_T, z = {zs}", "replicas": R, "k_per_step": k, "F_T_mean": mu, "F_T_std": sd},
+        "config": {"workload": f"GKTL batched ensemble: N={n} clones, {nx}x{ny} "
+                               f"{'open channel of Sec. 2' if open_ch else 'periodic channel'}, T_a=T={t_a} steps, "
+                               f"cloning every {period} steps, k sigma_I = z for level mean + z sigma of F_T, "
+                               f"z = {zs}, eps={EPS}, spin-up {spin} steps", "channel": args.rt_channel,
+                   "replicas": R, "sigma_I": sd_i, "F_T_mean": mu, "F_T_std": sd},
         "variants": out, "best_variant_at_highest_level": best_name,
         "speedup_vs_plain_at_highest_level": plain / best if best > 0 else None,
+        "speedup_vs_plain_per_level": {
+            str(z): out["plain_fp32_direct"]["levels"][j]["seconds_to_20pct"]
+            / min(out[v]["levels"][j]["seconds_to_20pct"] for v in variants) for j, z in enumerate(zs)},
         "surrogate_training": {"seconds": t_train, "samples": n_snaps * n, "epochs": len(losses),
                                "loss_first_last": [float(losses[0]), float(losses[-1])]}}))
 
@@ -1051,6 +1080,9 @@ def main():
                     help="perturb-check: steps between in-place perturbations (the paper: tau_c / 2)")
     ap.add_argument("--ams-channel", default="periodic", choices=["periodic", "open"],
                     help="ams-run: the periodic AMS channel or the paper's open channel")
+    ap.add_argument("--rt-channel", default="open", choices=["periodic", "open"],
+                    help="return-time workload: the turbulent open channel of Sec. 2 (default) or the periodic "
+                         "GKTL channel")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()

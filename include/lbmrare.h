@@ -424,7 +424,7 @@ int cnn_fit(cnn_model* m, const void* x_dev, const float* y_dev, int64_t n, int3
  * scored, the series following branches (lbm_ams_run with score_kind 1), and
  * lbm_gktl_run may use it as a pre-screen potential (kappa).  The model input is
  * the ensemble's fields downsampled by factor; its height and width must be
- * ny/factor and nx/factor. */
+ * ny/factor and nx/factor (floor division, as lbm_ensemble_fields). */
 int lbm_ensemble_attach_score(lbm_ensemble* e, cnn_model* m, int32_t factor, float rho_scale, float u_scale);
 /* score of every clone now, into out_dev[N] (device) */
 int lbm_ensemble_evaluate_score(lbm_ensemble* e, double* out_dev);
@@ -446,7 +446,11 @@ int lbm_surrogate_dataset(lbm_ensemble* e, int32_t n_snaps, int32_t every, int32
 /* Network input of the listed clones (host array): the block mean over
  * factor x factor nodes of (rho - 1) * rho_scale, u_x * u_scale, u_y * u_scale,
  * with u = (sum f c - F/2)/rho the velocity of the stored post-collision state,
- * into dst_dev BF16 [n][ny/factor][nx/factor][8] (channels 3..7 zero).  Waits. */
+ * into dst_dev BF16 [n][ny/factor][nx/factor][8] (channels 3..7 zero).  The
+ * blocks tile the lattice from node (0, 0) with floor division: rows and
+ * columns past the last whole block (the outlet column and top row of a
+ * 513 x 129 open channel at factor 4) are not in the input.  LBM_ERR_ARG
+ * unless 1 <= factor <= min(nx, ny).  Waits. */
 int lbm_ensemble_fields(lbm_ensemble* e, const int32_t* clones, int32_t n, int32_t factor, float rho_scale,
                         float u_scale, void* dst_dev);
 

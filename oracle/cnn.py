@@ -148,14 +148,16 @@ class Adam:
 def fields(c, f, factor, rho_scale, u_scale):
     """network input of one clone's populations f [9][ny][nx] (FP64): block
     means of (rho - 1, u_x, u_y) of the post-collision state, scaled, plus five
-    zero channels -> [ny/factor][nx/factor][8]"""
+    zero channels -> [ny // factor][nx // factor][8].  The blocks tile the
+    lattice from node (0, 0); rows and columns past the last whole block are
+    not in the input."""
     from oracle import macro
     rho, ux, uy = macro(c, f)
     ny, nx = rho.shape
     H, W = ny // factor, nx // factor
 
     def pool(a):
-        return a.reshape(H, factor, W, factor).mean(axis=(1, 3))
+        return a[:H * factor, :W * factor].reshape(H, factor, W, factor).mean(axis=(1, 3))
     out = np.zeros((H, W, 8))
     out[..., 0] = pool(rho - 1.0) * rho_scale
     out[..., 1] = pool(ux) * u_scale

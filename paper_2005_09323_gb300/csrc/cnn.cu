@@ -447,7 +447,9 @@ __global__ void gather_kernel(const bf16* __restrict__ x, const float* __restric
 }
 
 // K8: block-mean of (rho, u_x, u_y) over factor x factor nodes of each listed
-// clone -> [n][ny/factor][nx/factor][8] BF16 network input
+// clone -> [n][ny/factor][nx/factor][8] BF16 network input (floor division:
+// rows and columns past the last whole block, e.g. the outlet column and top
+// row of a 513 x 129 open channel at factor 4, are left out)
 template <int S>
 __global__ void fields_kernel(const void* buf0, const void* buf1, const int32_t* parity, const int32_t* list, int n,
                               int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny, int factor,
@@ -493,8 +495,8 @@ __global__ void fields_kernel(const void* buf0, const void* buf1, const int32_t*
 int fields_launch(lbm_ensemble* e, const int32_t* list_dev, int32_t n, int32_t factor, float rho_scale, float u_scale,
                   void* dst_dev)
 {
-    if (factor < 1 || e->cfg.nx % factor || e->cfg.ny % factor)
-        return fail(LBM_ERR_ARG, "fields: factor must divide nx and ny");
+    if (factor < 1 || factor > e->cfg.nx || factor > e->cfg.ny)
+        return fail(LBM_ERR_ARG, "fields: factor must be in [1, min(nx, ny)]");
     const int64_t total = (int64_t)n * (e->cfg.ny / factor) * (e->cfg.nx / factor);
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     auto launch = [&](auto tag) {

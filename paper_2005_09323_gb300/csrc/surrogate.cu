@@ -87,7 +87,7 @@ int lbm_ensemble_attach_score(lbm_ensemble* e, cnn_model* m, int32_t factor, flo
     int32_t H = 0, W = 0, mb = 0;
     int rc = cnn_shape(m, &H, &W, &mb);
     if (rc) return rc;
-    if (factor < 1 || e->cfg.nx % factor || e->cfg.ny % factor || e->cfg.ny / factor != H || e->cfg.nx / factor != W)
+    if (factor < 1 || factor > e->cfg.nx || factor > e->cfg.ny || e->cfg.ny / factor != H || e->cfg.nx / factor != W)
         return fail(LBM_ERR_ARG, "lbm_ensemble_attach_score: the model's input size is not the downsampled channel");
     if (!std::isfinite(rho_scale) || !std::isfinite(u_scale)) return fail(LBM_ERR_ARG, "scales must be finite");
     cudaError_t err;
@@ -138,7 +138,8 @@ int lbm_surrogate_dataset(lbm_ensemble* e, int32_t n_snaps, int32_t every, int32
 {
     if (!e || !x_dev || !y_dev) return fail(LBM_ERR_ARG, "lbm_surrogate_dataset: null argument");
     if (n_snaps < 1 || every < 1 || horizon < 1) return fail(LBM_ERR_ARG, "lbm_surrogate_dataset: counts");
-    if (factor < 1 || e->cfg.nx % factor || e->cfg.ny % factor) return fail(LBM_ERR_ARG, "factor must divide nx, ny");
+    if (factor < 1 || factor > e->cfg.nx || factor > e->cfg.ny)
+        return fail(LBM_ERR_ARG, "lbm_surrogate_dataset: factor must be in [1, min(nx, ny)]");
     const int32_t t0 = e->t_host[0];
     for (int i = 1; i < e->n; ++i)
         if (e->t_host[i] != t0) return fail(LBM_ERR_STATE, "clones at different times");

@@ -522,8 +522,8 @@ def lbm_ensemble_fields(e, clones, factor: int, rho_scale: float, u_scale: float
     """dst_dev: bfloat16 CUDA tensor [len(clones)][ny/factor][nx/factor][8]"""
     a = np.ascontiguousarray(clones, dtype=np.int32)
     ptr = _bf16_input(dst_dev)
-    if factor < 1 or nx % factor or ny % factor:
-        raise ValueError("factor must divide nx and ny")
+    if factor < 1 or factor > min(nx, ny):
+        raise ValueError("factor must be in [1, min(nx, ny)]")
     if tuple(dst_dev.shape) != (len(a), ny // factor, nx // factor, 8):
         raise TypeError(f"dst_dev is {tuple(dst_dev.shape)}, needs {(len(a), ny // factor, nx // factor, 8)}")
     _check(lib().lbm_ensemble_fields(e, _host(a), len(a), factor, rho_scale, u_scale, ptr))

@@ -200,20 +200,22 @@ def test_training_fits_a_known_target(L, model):
     assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:20]), (losses[:5], losses[-5:])
 
 
-def test_fields_match_oracle(L, orc):
+@pytest.mark.parametrize("nx,ny,factor", [(128, 32, 4), (136, 32, 3)])
+def test_fields_match_oracle(L, orc, nx, ny, factor):
+    """block means of the flow fields; at 136 x 32 with factor 3 the last
+    column and the last two rows are past the last whole block"""
     from oracle import cnn
-    nx, ny = 128, 32
     kw = dict(nx=nx, ny=ny, obstacle=(30, 12, 8, 8), tau=0.6, gx=2e-5, max_steps=20)
     cfg = L.config(**kw)
     e = L.lbm_ensemble_create(cfg, 3, 5, torch.cuda.current_stream())
     try:
         L.lbm_ensemble_step(e, 15)
-        dst = torch.zeros((2, ny // 4, nx // 4, 8), dtype=torch.bfloat16, device="cuda")
-        L.lbm_ensemble_fields(e, [2, 0], 4, 1000.0, 50.0, dst, nx, ny)
+        dst = torch.zeros((2, ny // factor, nx // factor, 8), dtype=torch.bfloat16, device="cuda")
+        L.lbm_ensemble_fields(e, [2, 0], factor, 1000.0, 50.0, dst, nx, ny)
         oc = orc.cfg(nx, ny, obstacle=(30, 12, 8, 8), tau=0.6, gx=2e-5)
         for i, c in enumerate([2, 0]):
             f = L.lbm_ensemble_get_populations(e, c, nx, ny)
-            ref = cnn.fields(oc, f, 4, 1000.0, 50.0)
+            ref = cnn.fields(oc, f, factor, 1000.0, 50.0)
             got = dst[i].float().cpu().numpy()
             for ch in range(3):
                 scale = np.abs(ref[..., ch]).max()

@@ -88,3 +88,34 @@ def test_adam_first_step_moves_by_lr():
     q = opt.step(p, g)
     # bias-corrected first step: lr * g / (|g| + eps)
     assert np.allclose(q, p - 0.01 * g / (np.abs(g) + 1e-8))
+
+
+@pytest.mark.parametrize("nx,ny,factor", [(13, 10, 4), (16, 8, 4), (513, 129, 4)])
+def test_fields_block_means_on_ragged_lattices(nx, ny, factor):
+    """network input of a constructed equilibrium state (numpy f^eq, no force,
+    so rho and u are those of the construction) against block means taken by
+    loops: blocks tile the lattice from node (0, 0); rows and columns past the
+    last whole block (here the top row and outlet column of 513 x 129) are not
+    in the input"""
+    import oracle as orc
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    rho = 1.0 + 1e-3 * np.sin(0.7 * X) + 2e-3 * np.cos(0.3 * Y)
+    ux = 0.01 * np.cos(0.2 * X + 0.1 * Y)
+    uy = -0.005 * np.sin(0.5 * Y) + 1e-4 * X
+    cu = cx[:, None, None] * ux + cy[:, None, None] * uy
+    f = w[:, None, None] * rho * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
+    c = orc.cfg(nx, ny, tau=0.6)
+    got = cnn.fields(c, f, factor, 1000.0, 50.0)
+    H, W = ny // factor, nx // factor
+    assert got.shape == (H, W, 8)
+    for by in range(H):
+        for bx in range(W):
+            cells = [(y, x) for y in range(by * factor, (by + 1) * factor) for x in range(bx * factor, (bx + 1) * factor)]
+            want = [1000.0 * np.mean([rho[y, x] - 1.0 for y, x in cells]),
+                    50.0 * np.mean([ux[y, x] for y, x in cells]),
+                    50.0 * np.mean([uy[y, x] for y, x in cells])]
+            assert np.allclose(got[by, bx, :3], want, rtol=1e-10, atol=1e-13), (by, bx)
+    assert np.all(got[..., 3:] == 0)
