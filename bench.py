@@ -935,6 +935,88 @@ def run_ams_run(args):
         "gpu_launches": launches // max(len(runs), 1)}))
 
 
+def run_ams_estimate(args):
+    """Seconds to a 20%-accurate estimate of P(max_t D(t) >= a), the extreme
+    instantaneous drag of Sec. 4.1, by AMS (App. B.1) against direct sampling,
+    on the open channel of Sec. 2 (central moments, tau 0.501).
+
+    Every run is a fresh ensemble of N = 32 trajectories spun up for 15000
+    steps (not timed); T_a = 2000 steps (about tau_c), score = the
+    instantaneous drag, checkpoints every 250 steps, App. D bank refilled at
+    each branch.  Direct sampling: runs with no iteration give the maxima Q of
+    N independent trajectories; levels a = mean + z sigma of Q (z = 2, 3, 4).
+    AMS: per level, runs that kill until the level is reached (at most 40 N
+    iterations); the generalized-AMS estimate is exp(log weight) x the
+    fraction of final maxima >= a, its relative error the spread over runs.
+    The direct-sampling error is binomial at the AMS mean (the unbiased
+    estimate of p).  Seconds to 20% = seconds per run x (relative error / 0.2)^2,
+    a direct run being N trajectories."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = workload(argparse.Namespace(workload="open", clones=args.clones or 32, collision=args.collision))
+    n, spin, t_a, stride = w["clones"], 15000, 2000, 250
+    R = max(3, args.steps)
+    stream = torch.cuda.current_stream()
+    cfg = L.config(w["nx"], w["ny"], obstacle=w["obst"], storage=L.STORAGE[args.storage], max_steps=spin + t_a,
+                   ckpt_stride=stride, n_snapshots=N_SNAP, collision=w["collision"], **channel_kwargs(w))
+    zs = (2.0, 3.0, 4.0)
+
+    def run(seed, level, max_iter):
+        e = L.lbm_ensemble_create(cfg, n, seed, stream)
+        try:
+            L.lbm_ensemble_autotune(e)
+            L.lbm_ensemble_step(e, spin)
+            L.lbm_ensemble_set_snapshots(e, [i * n // N_SNAP for i in range(N_SNAP)])
+            Q = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, lw, _ = L.lbm_ams_run(e, t_a, 1, max_iter, level, EPS, seed, Q, refresh_snapshots=True)
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, it, lw, Q.cpu().numpy()
+        finally:
+            L.lbm_ensemble_destroy(e)
+
+    direct = [run(500 + r, float("inf"), 0) for r in range(2 * R)]
+    Qd = np.concatenate([d[3] for d in direct])
+    t_direct = float(np.mean([d[0] for d in direct]))  # one run = N trajectories
+    mu, sd = float(Qd.mean()), float(Qd.std())
+    levels = []
+    for z in zs:
+        a = mu + z * sd
+        rs = [run(700 + 100 * int(z) + r, a, 40 * n) for r in range(R)]
+        ps = np.array([math.exp(lw) * float((Q >= a).mean()) for _, _, lw, Q in rs])
+        p = float(ps.mean())
+        t_run = float(np.mean([r[0] for r in rs]))
+        cv = float(ps.std(ddof=1) / p) if p > 0 else float("inf")
+        p_dir = float((Qd >= a).mean())
+        cv_dir = math.sqrt((1 - p) / (n * p)) if 0 < p < 1 else float("inf")
+        levels.append({"z": z, "level": a, "P_ams": p, "P_direct_sample": p_dir,
+                       "direct_events": int((Qd >= a).sum()), "direct_trajectories": int(Qd.size),
+                       "ams_iterations_mean": float(np.mean([r[1] for r in rs])),
+                       "ams_runs_reaching": int((ps > 0).sum()), "ams_relative_error_per_run": cv,
+                       "ams_seconds_per_run": t_run, "ams_seconds_to_20pct": t_run * (cv / 0.2) ** 2,
+                       "direct_seconds_per_run": t_direct, "direct_seconds_to_20pct": t_direct * (cv_dir / 0.2) ** 2,
+                       "speedup": (t_direct * cv_dir ** 2) / (t_run * cv ** 2) if cv > 0 and p > 0 else None,
+                       "return_time_steps": (-t_a / math.log1p(-p)) if 0 < p < 1 else None})
+    top = levels[-1]
+    print(json.dumps({
+        "metric": "time to a 20%-accurate estimate of P(max instantaneous drag >= a), AMS vs direct sampling",
+        "value": top["ams_seconds_to_20pct"], "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": R,
+        "warmup": 0, "data": "synthetic", "dtype": args.storage,
+        "config": {"workload": f"AMS (App. B.1) on the open channel of Sec. 2: N={n} trajectories of "
+                               f"{w['nx']}x{w['ny']}, {w['collision']} collision, spin-up {spin} steps, T_a={t_a}, "
+                               f"score = instantaneous drag, checkpoints every {stride} steps; levels mean + z sigma "
+                               f"of the direct maxima, z = {zs}", "runs_per_level": R, "direct_runs": 2 * R,
+                   "Q_mean": mu, "Q_std": sd},
+        "levels": levels}))
+
+
 def ks_distance(a, b) -> float:
     """two-sample Kolmogorov-Smirnov distance of the empirical distributions"""
     import numpy as np
@@ -1070,7 +1152,7 @@ def main():
                     help="fused-step variant index, or 'auto' to autotune (profiling captures fix it)")
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run",
+    ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run", "ams-estimate",
                                               "perturb-check"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--collision", default=None, choices=["bgk", "cm"],
@@ -1096,6 +1178,8 @@ def main():
         run_precision_report(args)
     elif args.workload == "ams-branch":
         run_ams_branch(args)
+    elif args.workload == "ams-estimate":
+        run_ams_estimate(args)
     elif args.workload == "ams-run":
         run_ams_run(args)
     elif args.workload == "perturb-check":
