@@ -558,10 +558,19 @@ def run_return_time(args):
     relative error, plain FP32 direct sampling against the batched GKTL form
     (FP32, FP32 + learned potential, FP16 storage + learned potential).
 
-    Workload: the GKTL ensemble (64 clones of 1024 x 256, 32 x 32 obstacle,
-    tau 0.505, g_x 1e-6) after a 2000-step spin-up, with the averaging window
-    equal to the horizon as in the paper's GKTL experiments: T_a = T = 10000
-    steps, cloning every 500 steps, so that the tilted integral is T F_T.
+    Workload (--rt-channel open, the default): the turbulent open channel of
+    Sec. 2 (the open workload: 64 trajectories of 513 x 129, central moments,
+    tau 0.501), where perturbed clones separate as the paper's cloning
+    assumes.  Every replica is a fresh ensemble spun up for 15000 steps (not
+    timed), then T_a = T = 20000 steps (10 tau_c) with cloning every 1000
+    steps (tau_c / 2), the averaging window equal to the horizon as in the
+    paper's GKTL experiments, so that the tilted integral is T F_T.  The
+    network of the learned potential sees 64 x 256 blocks of 2 x 2 nodes (the
+    outlet column and the top row are past the last whole block).
+    --rt-channel periodic: the GKTL ensemble (64 clones of 1024 x 256, 32 x 32
+    obstacle, tau 0.505, g_x 1e-6) after a 2000-step spin-up, T_a = T = 10000
+    steps, cloning every 500 steps, the network on 4 x 4 blocks.
+
     Levels a = mean + z sigma of F_T (z = 2, 3, 4) from the direct runs.  For
     each level the GKTL runs are tilted towards it, as the paper chooses k for
     the extremes of interest: k sigma_I = z with sigma_I the spread of the
@@ -569,16 +578,8 @@ def run_return_time(args):
     for a Gaussian integral.  The direct estimate's relative error is binomial
     at the Gaussian tail probability (the paper's unbiased reference), the GKTL
     one is measured over independent replicas.  Wall time to 20% = seconds per
-    replica x (relative error / 0.2)^2.
-
-    --rt-channel open: the same on the turbulent open channel of Sec. 2 (the
-    open workload: 64 trajectories of 513 x 129, central moments, tau 0.501),
-    where perturbed clones separate as the paper's cloning assumes: every
-    replica is a fresh ensemble spun up for 15000 steps (not timed), then
-    T_a = T = 20000 steps (10 tau_c) with cloning every 1000 steps (tau_c / 2);
-    the network sees 64 x 256 blocks of 2 x 2 nodes (the outlet column and the
-    top row are past the last whole block).  Every ensemble is autotuned
-    before it is stepped."""
+    replica x (relative error / 0.2)^2.  Every ensemble is autotuned before it
+    is stepped."""
     import math
 
     import numpy as np
@@ -683,10 +684,10 @@ def run_return_time(args):
             t_rep = float(np.mean([d["dt"] for d in per[j]]))
             mean = float(ps.mean())
             if name == "plain_fp32_direct":
-                cv = math.sqrt((1 - p_gauss[j]) / (n * p_gauss[j]))
+                cv = binomial_cv(p_gauss[j], n)
             else:
                 cv = float(ps.std(ddof=1) / mean) if mean > 0 else float("inf")
-            need = (cv / 0.2) ** 2
+            need = seconds_to_rel_error(1.0, cv)
             per_level.append({"z": z, "level": levels[j], "k_sigma_I": z if name != "plain_fp32_direct" else 0.0,
                               "P_mean": mean, "P_gauss": p_gauss[j], "replicas_reaching": int((ps > 0).sum()),
                               "relative_error_per_replica": cv, "replicas_for_20pct": need,
@@ -990,18 +991,19 @@ def run_ams_estimate(args):
     for z in zs:
         a = mu + z * sd
         rs = [run(700 + 100 * int(z) + r, a, 40 * n) for r in range(R)]
-        ps = np.array([math.exp(lw) * float((Q >= a).mean()) for _, _, lw, Q in rs])
+        ps = np.array([ams_estimate(lw, Q, a) for _, _, lw, Q in rs])
         p = float(ps.mean())
         t_run = float(np.mean([r[0] for r in rs]))
         cv = float(ps.std(ddof=1) / p) if p > 0 else float("inf")
         p_dir = float((Qd >= a).mean())
-        cv_dir = math.sqrt((1 - p) / (n * p)) if 0 < p < 1 else float("inf")
+        cv_dir = binomial_cv(p, n)
         levels.append({"z": z, "level": a, "P_ams": p, "P_direct_sample": p_dir,
                        "direct_events": int((Qd >= a).sum()), "direct_trajectories": int(Qd.size),
                        "ams_iterations_mean": float(np.mean([r[1] for r in rs])),
                        "ams_runs_reaching": int((ps > 0).sum()), "ams_relative_error_per_run": cv,
-                       "ams_seconds_per_run": t_run, "ams_seconds_to_20pct": t_run * (cv / 0.2) ** 2,
-                       "direct_seconds_per_run": t_direct, "direct_seconds_to_20pct": t_direct * (cv_dir / 0.2) ** 2,
+                       "ams_seconds_per_run": t_run, "ams_seconds_to_20pct": seconds_to_rel_error(t_run, cv),
+                       "direct_seconds_per_run": t_direct,
+                       "direct_seconds_to_20pct": seconds_to_rel_error(t_direct, cv_dir),
                        "speedup": (t_direct * cv_dir ** 2) / (t_run * cv ** 2) if cv > 0 and p > 0 else None,
                        "return_time_steps": (-t_a / math.log1p(-p)) if 0 < p < 1 else None})
     top = levels[-1]
@@ -1015,6 +1017,29 @@ def run_ams_estimate(args):
                                f"of the direct maxima, z = {zs}", "runs_per_level": R, "direct_runs": 2 * R,
                    "Q_mean": mu, "Q_std": sd},
         "levels": levels}))
+
+
+def binomial_cv(p: float, n: int) -> float:
+    """relative error of a direct-sampling frequency of probability p over n
+    independent samples (inf unless 0 < p < 1)"""
+    import math
+    return math.sqrt((1.0 - p) / (n * p)) if 0.0 < p < 1.0 else float("inf")
+
+
+def seconds_to_rel_error(seconds_per_run: float, cv_per_run: float, target: float = 0.2) -> float:
+    """wall time for independent runs to average to a relative error `target`:
+    the error of a mean of m runs is cv / sqrt(m)"""
+    return seconds_per_run * (cv_per_run / target) ** 2
+
+
+def ams_estimate(log_weight: float, maxima, level: float) -> float:
+    """generalized-AMS estimate of P(max score >= level) from one run (App.
+    B.1): the product of the survival fractions (1 - K_j / N), exp(log_weight),
+    times the fraction of the final ensemble's maxima at or above the level"""
+    import math
+
+    import numpy as np
+    return math.exp(log_weight) * float((np.asarray(maxima) >= level).mean())
 
 
 def ks_distance(a, b) -> float:

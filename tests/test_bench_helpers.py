@@ -1,7 +1,9 @@
 """Host helpers of bench.py on the CPU: the two-sample KS distance of the
 perturbation check, the pooled correlation time (FFT lagged sums against the
-direct sums, and the quarter period of a sine), and the lookup of the recorded
-DRAM traffic by kernel label."""
+direct sums, and the quarter period of a sine), the lookup of the recorded
+DRAM traffic by kernel label, and the arithmetic of the estimate benches (the
+binomial error of a direct frequency and the time to a target error, against
+simulation; the generalized-AMS estimate of one run, by hand)."""
 import os
 import sys
 
@@ -48,3 +50,31 @@ def test_traffic_records_are_keyed_without_warps():
         assert "warps=" not in key
         assert 0 < rec["bytes_per_site"] < 80
         assert len(bench.kernel_sha(rec["files"])) == 16
+
+
+def test_binomial_cv_matches_simulated_frequencies():
+    rng = np.random.default_rng(2)
+    p, n = 0.03, 400
+    freqs = rng.binomial(n, p, size=20000) / n
+    assert abs(freqs.std() / freqs.mean() / bench.binomial_cv(p, n) - 1) < 0.02
+    assert bench.binomial_cv(0.0, 10) == float("inf") and bench.binomial_cv(1.0, 10) == float("inf")
+
+
+def test_seconds_to_rel_error_from_averaged_runs():
+    # a mean of m runs with per-run error cv has error cv / sqrt(m): 16 runs
+    # of 2 s at cv = 0.8 reach 0.2
+    assert abs(bench.seconds_to_rel_error(2.0, 0.8) - 32.0) < 1e-12
+    rng = np.random.default_rng(3)
+    runs = rng.exponential(1.0, size=(20000, 25))  # cv 1 per run, 25 runs -> 0.2
+    means = runs.mean(axis=1)
+    assert abs(means.std() / means.mean() - 0.2) < 0.01
+    assert abs(bench.seconds_to_rel_error(1.0, 1.0) - 25.0) < 1e-12
+
+
+def test_ams_estimate_on_a_hand_computed_run():
+    # N = 4, two iterations killing one each: weight (3/4)^2; 2 of 4 final maxima
+    # at or above the level (one exactly at it)
+    lw = 2 * np.log(1 - 1 / 4)
+    assert abs(bench.ams_estimate(lw, [0.5, 0.7, 0.9, 0.7], 0.7) - 0.5625 * 0.75) < 1e-15
+    assert abs(bench.ams_estimate(lw, [0.5, 0.6, 0.9, 0.7], 0.7) - 0.5625 * 0.5) < 1e-15
+    assert bench.ams_estimate(0.0, [0.1, 0.2], 0.3) == 0.0
