@@ -158,10 +158,16 @@ def peaks():
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
+    """nvidia-smi clock and throttle-reason samples every 200 ms while the
+    timed region runs, kept as CSV in $LBM_CLOCKS_DIR (default: the system's
+    temporary directory)"""
+
     def __init__(self, index: int):
+        import tempfile
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        out = os.environ.get("LBM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
