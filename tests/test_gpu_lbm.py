@@ -384,6 +384,30 @@ def test_argument_errors(L):
             e.drag(0, 5)
 
 
+def test_zero_steps_and_size_limits(L):
+    """zero-step calls change nothing; a history filled to max_steps takes no
+    further step; creation rejects, before any allocation, clone counts outside
+    [1, 65535], a clone of 2^31 or more values (9 x 32768 x 8192) and lattices
+    below the minimum"""
+    with Ens(L, 2, **dict(RAGGED, max_steps=10)) as e:
+        before = [e.pops(c) for c in range(2)]
+        L.lbm_ensemble_step(e.h, 0)
+        L.lbm_ensemble_step_clones(e.h, 0, [1])
+        for c in range(2):
+            assert np.array_equal(e.pops(c), before[c])
+        L.lbm_ensemble_step(e.h, 10)
+        assert np.all(np.isfinite(e.drag(0, 10)))
+        with pytest.raises(L.LbmError):
+            L.lbm_ensemble_step(e.h, 1)
+    stream = torch.cuda.current_stream()
+    big = dict(RAGGED, nx=32768, ny=8192, obstacle=(100, 100, 8, 8))
+    for kw, n in [(RAGGED, 0), (RAGGED, 65536), (big, 1), (dict(RAGGED, nx=4, obstacle=(0, 0, 0, 0)), 1),
+                  (dict(RAGGED, ny=1, obstacle=(0, 0, 0, 0)), 1)]:
+        with pytest.raises(L.LbmError) as ei:
+            L.lbm_ensemble_create(L.config(**kw), n, 0, stream)
+        assert ei.value.status == L.LBM_ERR_ARG
+
+
 @pytest.mark.parametrize("storage,tol", [("fp16", 3e-3), ("bf16", 3e-2)])
 def test_reduced_precision_storage(L, orc, storage, tol):
     """Shifted 16-bit storage: g = f - w in FP16 (11-bit significand) or BF16
