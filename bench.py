@@ -481,6 +481,9 @@ def run_ours(args):
                     "d2h_bytes_per_step": 8 * n_clones * PERIOD + 4 * n_clones},
             "gpu_launches": launches,
             "clocks": clocks,
+            # GLUPS over fluid sites only (the solid cells are updated too)
+            "fluid_only": {"value": value * (1.0 - solid_cells(w) / (nx * ny)), "unit": "GLUPS",
+                           "fluid_fraction": 1.0 - solid_cells(w) / (nx * ny)},
         }
         if direct is not None:
             line["direct_sampling"] = direct
@@ -1023,6 +1026,17 @@ def run_ams_estimate(args):
                                f"of the direct maxima, z = {zs}", "runs_per_level": R, "direct_runs": 2 * R,
                    "Q_mean": mu, "Q_std": sd},
         "levels": levels}))
+
+
+def solid_cells(w) -> int:
+    """solid cells of the workload's channel: the square and, in the open
+    channel, the entrance grid's bars (rows with y mod (bar + gap) >= gap over
+    the grid's columns)"""
+    n = w["obst"][2] * w["obst"][3]
+    if w.get("open"):
+        _, width, bar, gap = OPEN_GRID
+        n += width * sum(1 for y in range(w["ny"]) if y % (bar + gap) >= gap)
+    return n
 
 
 def binomial_cv(p: float, n: int) -> float:

@@ -78,3 +78,13 @@ def test_ams_estimate_on_a_hand_computed_run():
     assert abs(bench.ams_estimate(lw, [0.5, 0.7, 0.9, 0.7], 0.7) - 0.5625 * 0.75) < 1e-15
     assert abs(bench.ams_estimate(lw, [0.5, 0.6, 0.9, 0.7], 0.7) - 0.5625 * 0.5) < 1e-15
     assert bench.ams_estimate(0.0, [0.1, 0.2], 0.3) == 0.0
+
+
+def test_solid_cells_of_the_workloads():
+    import argparse
+    gktl = bench.workload(argparse.Namespace(workload="gktl", clones=None))
+    assert bench.solid_cells(gktl) == 32 * 32
+    # open channel: the 16 x 16 square and 8 bars of 8 rows (rows 8-15, 24-31,
+    # ..., 120-127 of 129) over the grid's 8 columns
+    opn = bench.workload(argparse.Namespace(workload="open", clones=None))
+    assert bench.solid_cells(opn) == 16 * 16 + 8 * 64
