@@ -384,6 +384,40 @@ def test_argument_errors(L):
             e.drag(0, 5)
 
 
+def test_ams_workload_full_size_sampled_parity(L, orc):
+    """The AMS workload's launch shape: 256 trajectories of 512 x 128 with a
+    16 x 16 obstacle at x = 128, tau 0.505, autotuned as the bench runs it;
+    three sampled trajectories against the oracle over 20 steps."""
+    kw = dict(nx=512, ny=128, obstacle=si.channel(512, 128, 16), tau=0.505, gx=1e-6, max_steps=40)
+    with Ens(L, 256, seed=21, **kw) as e:
+        L.lbm_ensemble_autotune(e.h)
+        L.lbm_ensemble_step(e.h, 20)
+        d = e.drag(0, 20)
+        oc = oracle_cfg(orc, kw)
+        for c in (0, 137, 255):
+            f_ref, d_ref = orc.run(oc, orc.init(oc, 21, c, 0.01), 20)
+            assert rel(e.pops(c), f_ref) < POP_TOL
+            assert rel(d[c], d_ref) < DRAG_TOL
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 3e-3), ("bf16", 3e-2)])
+def test_precision_workload_full_size_sampled_parity(L, orc, storage, tol):
+    """The precision workload's launch shape: 16 clones of 2048 x 512 with a
+    64 x 64 obstacle at x = 512, shifted 16-bit storage, autotuned as the bench
+    runs it (the row-staged kernel); two sampled clones against the FP64
+    oracle over 20 steps, relative to the largest |f - w| as for CFG1."""
+    kw = dict(nx=2048, ny=512, obstacle=si.channel(2048, 512, 64), tau=0.505, gx=1e-6, max_steps=40)
+    with Ens(L, 16, seed=31, storage=storage, **kw) as e:
+        L.lbm_ensemble_autotune(e.h)
+        L.lbm_ensemble_step(e.h, 20)
+        assert np.all(np.isfinite(e.drag(0, 20)))
+        oc = oracle_cfg(orc, kw)
+        w = orc.feq(1.0, 0.0, 0.0)[:, None, None]
+        for c in (0, 15):
+            f_ref, _ = orc.run(oc, orc.init(oc, 31, c, 0.01), 20)
+            assert np.abs(e.pops(c) - f_ref).max() / np.abs(f_ref - w).max() < tol, c
+
+
 def test_zero_steps_and_size_limits(L):
     """zero-step calls change nothing; a history filled to max_steps takes no
     further step; creation rejects, before any allocation, clone counts outside
