@@ -288,6 +288,22 @@ def test_clone_exact_copy_and_perturbation(L, orc):
         assert np.array_equal(e.pops(3), before[2])  # kept its own slot (a copy of 2 since the first call)
 
 
+def test_clone_with_a_rejected_parent(L):
+    """a parent index outside [0, N) (a rejected selection writes -1) leaves its
+    slot unchanged while the other slots are cloned, and the next synchronising
+    call reports LBM_ERR_NONFINITE (the rejection's cause)"""
+    with Ens(L, 3, seed=3, **dict(RAGGED, max_steps=20)) as e:
+        L.lbm_ensemble_step(e.h, 5)
+        before = [e.pops(c) for c in range(3)]
+        L.lbm_ensemble_clone(e.h, torch.tensor([0, 0, -1], dtype=torch.int32, device="cuda"), 0.0, 1, 0)
+        after = [e.pops(c) for c in range(3)]
+        assert np.array_equal(after[0], before[0]) and np.array_equal(after[1], before[0])
+        assert np.array_equal(after[2], before[2])
+        with pytest.raises(L.LbmError) as ei:
+            e.drag(0, 5)
+        assert ei.value.status == L.LBM_ERR_NONFINITE
+
+
 def test_snapshot_bank_from_checkpoints(L, orc):
     """The App. D bank refilled from checkpointed states (the flow at the
     branching time) perturbs exactly like states taken live at that time."""
