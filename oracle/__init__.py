@@ -11,6 +11,7 @@ compiles them (``build()``) and marshals numpy arrays through ctypes.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -22,20 +23,26 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _SOURCES = ["philox.c", "lbm.c", "select.c", "ou.c"]
 
 
+def compile_sources(src_dir: str, out: str, extra=()) -> str:
+    """gcc, -O2, IEEE FP64 (no contraction into fused multiply-adds, so x86 and
+    Arm hosts round alike) of the oracle's C sources found in src_dir into
+    the shared library out, with the extra compiler arguments given"""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", *extra,
+           *[os.path.join(src_dir, s) for s in _SOURCES], "-lm", "-o", tmp]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle's C sources into ``oracle/liboracle.so`` (gcc, -O2, IEEE FP64:
-    no contraction into fused multiply-adds, so x86 and Arm hosts round alike)."""
+    """Compile the oracle's C sources into ``oracle/liboracle.so``."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
     if not force and os.path.exists(_SO):
         so_m = os.path.getmtime(_SO)
         if all(os.path.getmtime(s) <= so_m for s in srcs):
             return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           *[os.path.join(_HERE, s) for s in _SOURCES], "-lm", "-o", tmp]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    return compile_sources(_HERE, _SO)
 
 
 _lib = None
@@ -45,34 +52,52 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_SO)
-        d, i32, i64, u64, p = C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p
-        L.orc_philox4x64.argtypes = [p, p, p]
-        L.orc_u01.argtypes = [u64]; L.orc_u01.restype = d
-        L.orc_below.argtypes = [u64, u64]; L.orc_below.restype = u64
-        L.orc_feq.argtypes = [d, d, d, p]
-        L.orc_guo.argtypes = [d, d, d, d, p]
-        L.orc_init.argtypes = [p, u64, i32, d, p]
-        L.orc_step.argtypes = [p, p, p, p, p]
-        L.orc_run.argtypes = [p, p, p, i32, p]
-        L.orc_moments.argtypes = [p, p, p, p, p]
-        L.orc_macro.argtypes = [p, p, p, p, p]
-        L.orc_is_solid.argtypes = [p, C.c_int, C.c_int]; L.orc_is_solid.restype = C.c_int
-        L.orc_cm_collide.argtypes = [p, d, d, p, p, p, p]
-        L.orc_tau_at.argtypes = [p, C.c_int]; L.orc_tau_at.restype = d
-        L.orc_inlet_u.argtypes = [p, C.c_int]; L.orc_inlet_u.restype = d
-        L.orc_observables.argtypes = [p, p, p]; L.orc_observables.restype = C.c_int
-        L.orc_perturb_alphas.argtypes = [u64, u64, i32, i32, p]
-        L.orc_perturb.argtypes = [p, p, i32, p, p, d, p]
-        L.orc_gktl_weights.argtypes = [i32, p, p, p]; L.orc_gktl_weights.restype = C.c_int
-        L.orc_gktl_select.argtypes = [i32, p, u64, u64, p]; L.orc_gktl_select.restype = C.c_int
-        L.orc_ams_select.argtypes = [i32, p, u64, u64, p, p, p, p]; L.orc_ams_select.restype = C.c_int
-        L.orc_ou_noise.argtypes = [u64, u64, u64, u64]; L.orc_ou_noise.restype = d
-        L.orc_ou_gktl.argtypes = [i32, i32, i32, d, d, u64, p, i32, p]; L.orc_ou_gktl.restype = d
-        L.orc_ou_direct_max.argtypes = [i64, i32, d, u64, i32, p, p]
-        L.orc_ou_ams.argtypes = [i32, i32, d, d, i32, u64, p]; L.orc_ou_ams.restype = d
-        _lib = L
+        _lib = _load(_SO)
     return _lib
+
+
+@contextlib.contextmanager
+def using(path: str):
+    """Within the block every wrapper of this module calls the library at path
+    (a build of modified sources: the mutation tests plant one mistake each)
+    instead of liboracle.so."""
+    global _lib
+    saved = lib()
+    _lib = _load(path)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _load(path: str):
+    L = C.CDLL(path)
+    d, i32, i64, u64, p = C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p
+    L.orc_philox4x64.argtypes = [p, p, p]
+    L.orc_u01.argtypes = [u64]; L.orc_u01.restype = d
+    L.orc_below.argtypes = [u64, u64]; L.orc_below.restype = u64
+    L.orc_feq.argtypes = [d, d, d, p]
+    L.orc_guo.argtypes = [d, d, d, d, p]
+    L.orc_init.argtypes = [p, u64, i32, d, p]
+    L.orc_step.argtypes = [p, p, p, p, p]
+    L.orc_run.argtypes = [p, p, p, i32, p]
+    L.orc_moments.argtypes = [p, p, p, p, p]
+    L.orc_macro.argtypes = [p, p, p, p, p]
+    L.orc_is_solid.argtypes = [p, C.c_int, C.c_int]; L.orc_is_solid.restype = C.c_int
+    L.orc_cm_collide.argtypes = [p, d, d, p, p, p, p]
+    L.orc_tau_at.argtypes = [p, C.c_int]; L.orc_tau_at.restype = d
+    L.orc_inlet_u.argtypes = [p, C.c_int]; L.orc_inlet_u.restype = d
+    L.orc_observables.argtypes = [p, p, p]; L.orc_observables.restype = C.c_int
+    L.orc_perturb_alphas.argtypes = [u64, u64, i32, i32, p]
+    L.orc_perturb.argtypes = [p, p, i32, p, p, d, p]
+    L.orc_gktl_weights.argtypes = [i32, p, p, p]; L.orc_gktl_weights.restype = C.c_int
+    L.orc_gktl_select.argtypes = [i32, p, u64, u64, p]; L.orc_gktl_select.restype = C.c_int
+    L.orc_ams_select.argtypes = [i32, p, u64, u64, p, p, p, p]; L.orc_ams_select.restype = C.c_int
+    L.orc_ou_noise.argtypes = [u64, u64, u64, u64]; L.orc_ou_noise.restype = d
+    L.orc_ou_gktl.argtypes = [i32, i32, i32, d, d, u64, p, i32, p]; L.orc_ou_gktl.restype = d
+    L.orc_ou_direct_max.argtypes = [i64, i32, d, u64, i32, p, p]
+    L.orc_ou_ams.argtypes = [i32, i32, d, d, i32, u64, p]; L.orc_ou_ams.restype = d
+    return L
 
 
 def _ptr(a: np.ndarray):

@@ -1,0 +1,108 @@
+"""The pins catch plausible mistakes: each case copies the oracle's C sources,
+plants one mistake in the copy (a dropped factor, a wrong sign or index, a
+first-order formula for a second-order one, an off-by-one), compiles it on its
+own, and runs the existing pin named beside it against that build; the pin
+must fail.  A control build of the unmodified copy passes every pin used here,
+so a failure comes from the planted mistake and not from the harness."""
+import os
+import shutil
+
+import pytest
+
+from tests import test_oracle_lbm as T_lbm
+from tests import test_oracle_open as T_open
+from tests import test_oracle_select as T_sel
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+
+
+def momentum_balance(orc):
+    T_lbm.test_momentum_balance_pins_drag(orc)
+
+
+def equilibrium_moments(orc):
+    T_lbm.test_equilibrium_moments(orc, 1.03, 0.05, -0.02)
+
+
+PINS = {
+    "momentum balance": momentum_balance,
+    "equilibrium moments": equilibrium_moments,
+    "perturbation keeps the mass": T_lbm.test_perturbation_preserves_mass,
+    "GKTL weights sum to N": T_sel.test_weights_sum_to_n_and_normaliser,
+    "AMS survivor uniform among the others": T_sel.test_ams_survivor_uniform,
+    "inlet column": T_open.test_inlet_column_is_the_equilibrium_of_the_profile,
+    "outlet column": T_open.test_outlet_column_is_regularized_with_the_extrapolated_velocity,
+    "sponge profile": T_open.test_sponge_profile,
+    "grid of bars": T_open.test_grid_of_bars_matches_the_stated_geometry,
+    "drag counts the square only": T_open.test_drag_counts_the_square_only,
+}
+
+# (case, file, text in the oracle, planted text, pin that must fail)
+MUTANTS = [
+    ("Guo factor (1 - 1/(2 tau)) dropped", "lbm.c",
+     "+ (1.0 - 1.0 / (2.0 * tau)) * S[i];", "+ S[i];", "momentum balance"),
+    ("half-force velocity shift dropped", "lbm.c",
+     "double ux = (jx + 0.5 * c->gx) / rho;", "double ux = jx / rho;", "momentum balance"),
+    ("bounce-back into the same direction", "lbm.c",
+     "fout[IDX(c, OPP[i], x, y)] = v;", "fout[IDX(c, i, x, y)] = v;", "momentum balance"),
+    ("drag sign flipped", "lbm.c",
+     "ox += 2.0 * CX[i] * v;", "ox -= 2.0 * CX[i] * v;", "momentum balance"),
+    ("relaxation by tau instead of 1/tau", "lbm.c",
+     "f[i] - (f[i] - feq[i]) / tau +", "f[i] - (f[i] - feq[i]) * tau +", "momentum balance"),
+    ("equilibrium's second-order term doubled", "lbm.c",
+     "quad / (2.0 * CS2 * CS2)", "quad / (CS2 * CS2)", "equilibrium moments"),
+    ("perturbation not rescaled to the mass", "lbm.c",
+     "double scale = m_before / m_after;", "double scale = 1.0;", "perturbation keeps the mass"),
+    ("GKTL weights not scaled by N", "select.c",
+     "W[i] = (double)n * exp(s[i] - m) / sum;", "W[i] = exp(s[i] - m) / sum;", "GKTL weights sum to N"),
+    ("AMS survivor drawn among all, the killed included", "select.c",
+     "if (Q[i] == z) continue;", "/* every index counts */", "AMS survivor uniform among the others"),
+    ("inlet parabola through the node centres", "lbm.c",
+     "double h = c->ny, yy = y + 0.5;", "double h = c->ny, yy = y;", "inlet column"),
+    ("outlet velocity copied (first order)", "lbm.c",
+     "ux[y] = 2.0 * vx[0] - vx[1];", "ux[y] = vx[0];", "outlet column"),
+    ("outlet stress with the wrong sign", "lbm.c",
+     "const double pre = -2.0 * CS2 * (tau_out - 1.0);", "const double pre = 2.0 * CS2 * (tau_out - 1.0);",
+     "outlet column"),
+    ("sponge ramp linear", "lbm.c",
+     "return c->tau + (c->sponge_tau - c->tau) * s * s;", "return c->tau + (c->sponge_tau - c->tau) * s;",
+     "sponge profile"),
+    ("bar rows off by one", "lbm.c",
+     "(y % (c->grid_bar + c->grid_gap)) >= c->grid_gap;", "(y % (c->grid_bar + c->grid_gap)) > c->grid_gap;",
+     "grid of bars"),
+    ("drag counts the links into the bars", "lbm.c",
+     "} else if (in_obstacle(c, xn, yn)) {", "} else if (orc_is_solid(c, xn, yn)) {",
+     "drag counts the square only"),
+]
+
+
+def build_copy(orc, tmp, file=None, old=None, new=None):
+    src = os.path.join(tmp, "src")
+    os.makedirs(src)
+    for f in os.listdir(ORACLE):
+        if f.endswith((".c", ".h")):
+            shutil.copy(os.path.join(ORACLE, f), src)
+    if file is not None:
+        path = os.path.join(src, file)
+        text = open(path).read()
+        assert text.count(old) == 1, f"the oracle no longer holds {old!r} once: update this case"
+        with open(path, "w") as fh:
+            fh.write(text.replace(old, new))
+    # references between the copy's own functions bind inside the copy
+    return orc.compile_sources(src, os.path.join(tmp, "liboracle_copy.so"), extra=("-Wl,-Bsymbolic",))
+
+
+def test_control_copy_passes_every_pin(orc, tmp_path):
+    lib = build_copy(orc, str(tmp_path))
+    with orc.using(lib):
+        for pin in PINS.values():
+            pin(orc)
+
+
+@pytest.mark.parametrize("case,file,old,new,pin", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_planted_mistake(orc, tmp_path, case, file, old, new, pin):
+    lib = build_copy(orc, str(tmp_path), file, old, new)
+    with orc.using(lib):
+        with pytest.raises(AssertionError):
+            PINS[pin](orc)
