@@ -10,7 +10,10 @@ import shutil
 import pytest
 
 from tests import test_oracle_lbm as T_lbm
+from tests import test_oracle_mrt as T_mrt
+from tests import test_oracle_observables as T_obs
 from tests import test_oracle_open as T_open
+from tests import test_oracle_rng as T_rng
 from tests import test_oracle_select as T_sel
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -25,6 +28,18 @@ def equilibrium_moments(orc):
     T_lbm.test_equilibrium_moments(orc, 1.03, 0.05, -0.02)
 
 
+def mean_copies(orc):
+    T_sel.test_selection_mean_copies_equal_weights(orc, 4, 0.8, 40000)
+
+
+def constructed_fields(orc):
+    T_obs.test_constructed_fields(orc, 0.0)
+
+
+def ou_normaliser(orc):
+    T_sel.test_ou_gktl_normaliser_matches_scgf(orc, 1.0)
+
+
 PINS = {
     "momentum balance": momentum_balance,
     "equilibrium moments": equilibrium_moments,
@@ -36,6 +51,12 @@ PINS = {
     "sponge profile": T_open.test_sponge_profile,
     "grid of bars": T_open.test_grid_of_bars_matches_the_stated_geometry,
     "drag counts the square only": T_open.test_drag_counts_the_square_only,
+    "central moments relax at their rates": T_mrt.test_each_central_moment_relaxes_at_its_rate,
+    "equal rates give BGK": T_mrt.test_equal_rates_is_bgk,
+    "Philox against numpy": T_rng.test_philox_many_counters,
+    "mean copies equal the weights": mean_copies,
+    "observables on constructed fields": constructed_fields,
+    "OU GKTL normaliser": ou_normaliser,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -74,6 +95,20 @@ MUTANTS = [
     ("drag counts the links into the bars", "lbm.c",
      "} else if (in_obstacle(c, xn, yn)) {", "} else if (orc_is_solid(c, xn, yn)) {",
      "drag counts the square only"),
+    ("k11 relaxed at the bulk rate", "lbm.c",
+     "Om[5][5] = ws;", "Om[5][5] = wb;", "central moments relax at their rates"),
+    ("central-moment forcing without its half step", "lbm.c",
+     "d[i] = f[i] - feq[i] + 0.5 * S[i];", "d[i] = f[i] - feq[i];", "equal rates give BGK"),
+    ("Philox multiplier altered", "philox.c",
+     "M0 = 0xD2E7470EE14C6C93ULL", "M0 = 0xD2E7470EE14C6C95ULL", "Philox against numpy"),
+    ("systematic resampling without its uniform", "select.c",
+     "double point = (U + (double)k) * spacing;", "double point = (double)k * spacing;",
+     "mean copies equal the weights"),
+    ("wall shear from one row (first order)", "lbm.c",
+     "gt += (9.0 * u1 - u2) / 3.0;", "gt += 2.0 * u1;", "observables on constructed fields"),
+    ("OU noise doubled in the GKTL process", "ou.c",
+     "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
+     "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),
 ]
 
 
