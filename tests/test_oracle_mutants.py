@@ -1,9 +1,10 @@
-"""The pins catch plausible mistakes: each case copies the oracle's C sources,
-plants one mistake in the copy (a dropped factor, a wrong sign or index, a
-first-order formula for a second-order one, an off-by-one), compiles it on its
-own, and runs the existing pin named beside it against that build; the pin
-must fail.  A control build of the unmodified copy passes every pin used here,
-so a failure comes from the planted mistake and not from the harness."""
+"""The pins catch plausible mistakes: each case copies the oracle's C sources
+(or its FP64 CNN, oracle/cnn.py), plants one mistake in the copy (a dropped
+factor, a wrong sign or index, a first-order formula for a second-order one,
+an off-by-one), compiles or loads it on its own, and runs the existing pin
+named beside it against that copy; the pin must fail.  A control copy without
+a mistake passes every pin used here, so a failure comes from the planted
+mistake and not from the harness."""
 import os
 import shutil
 
@@ -141,3 +142,58 @@ def test_pin_catches_planted_mistake(orc, tmp_path, case, file, old, new, pin):
     with orc.using(lib):
         with pytest.raises(AssertionError):
             PINS[pin](orc)
+
+
+# ---------------------------------------------------------------- the FP64 CNN (oracle/cnn.py)
+from tests import test_oracle_cnn as T_cnn  # noqa: E402
+
+CNN_PINS = {
+    "identity kernel and shift": lambda: T_cnn.test_conv_identity_kernel_and_shift(),
+    "gradient by central differences": lambda: T_cnn.test_gradient_by_central_differences(0),
+    "Adam's first step": lambda: T_cnn.test_adam_first_step_moves_by_lr(),
+    "block means on a ragged lattice": lambda: T_cnn.test_fields_block_means_on_ragged_lattices(13, 10, 4),
+}
+
+CNN_MUTANTS = [
+    ("kernel flipped (convolution for correlation)",
+     'out += np.einsum("bhwc,oc->bhwo", xp[:, ky:ky + H, kx:kx + W, :], w[:, ky, kx, :])',
+     'out += np.einsum("bhwc,oc->bhwo", xp[:, ky:ky + H, kx:kx + W, :], w[:, 2 - ky, 2 - kx, :])',
+     "identity kernel and shift"),
+    ("input gradient without the tap's shift",
+     "dxp[:, ky:ky + H, kx:kx + W, :] +=", "dxp[:, 1:1 + H, 1:1 + W, :] +=", "gradient by central differences"),
+    ("weight gradient with transposed taps",
+     "dw[:, ky, kx, :] = np.einsum", "dw[:, kx, ky, :] = np.einsum", "gradient by central differences"),
+    ("ReLU derivative taken as 1 everywhere",
+     "dpre = store(da * (acts[l + 1] > 0))", "dpre = store(da * (acts[l + 1] >= 0))",
+     "gradient by central differences"),
+    ("mean pool over the rows only",
+     "P = acts[-1].shape[1] * acts[-1].shape[2]", "P = acts[-1].shape[1]", "gradient by central differences"),
+    ("Adam without bias correction",
+     "mh = self.m / (1 - self.b1 ** self.t)", "mh = self.m", "Adam's first step"),
+    ("blocks cropped from the far corner",
+     "a[:H * factor, :W * factor]", "a[-H * factor:, -W * factor:]", "block means on a ragged lattice"),
+]
+
+
+def cnn_copy(old=None, new=None):
+    import types
+    src = open(os.path.join(ORACLE, "cnn.py")).read()
+    if old is not None:
+        assert src.count(old) == 1, f"oracle/cnn.py no longer holds {old!r} once: update this case"
+        src = src.replace(old, new)
+    mod = types.ModuleType("oracle_cnn_copy")
+    exec(compile(src, "oracle/cnn.py (copy)", "exec"), mod.__dict__)
+    return mod
+
+
+def test_cnn_control_copy_passes_every_pin(orc, monkeypatch):
+    monkeypatch.setattr(T_cnn, "cnn", cnn_copy())
+    for pin in CNN_PINS.values():
+        pin()
+
+
+@pytest.mark.parametrize("case,old,new,pin", CNN_MUTANTS, ids=[m[0] for m in CNN_MUTANTS])
+def test_cnn_pin_catches_planted_mistake(orc, monkeypatch, case, old, new, pin):
+    monkeypatch.setattr(T_cnn, "cnn", cnn_copy(old, new))
+    with pytest.raises(AssertionError):
+        CNN_PINS[pin]()
