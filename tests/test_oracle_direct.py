@@ -16,6 +16,9 @@ def test_autocorrelation_small_cases(orc):
     c, tc = orc.autocorrelation(np.sin(2 * np.pi * t / 400.0), 150)
     assert abs(tc - 100) <= 1
     assert np.allclose(c[:50], np.cos(2 * np.pi * np.arange(50) / 400.0), atol=1e-2)
+    # the correlation of the fluctuations: a constant offset changes nothing
+    c2, tc2 = orc.autocorrelation(np.array([1.0, -1.0, 1.0, -1.0, 1.0, -1.0]) + 7.0, 2)
+    assert np.allclose(c2, [1.0, -1.0, 1.0], atol=1e-14) and tc2 == 1
 
 
 def ar1(rng, rho, n, length):

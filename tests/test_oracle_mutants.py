@@ -1,5 +1,6 @@
 """The pins catch plausible mistakes: each case copies the oracle's C sources
-(or its FP64 CNN, oracle/cnn.py), plants one mistake in the copy (a dropped
+(or its FP64 CNN, oracle/cnn.py, or its direct-sampling statistics in
+oracle/__init__.py), plants one mistake in the copy (a dropped
 factor, a wrong sign or index, a first-order formula for a second-order one,
 an off-by-one), compiles or loads it on its own, and runs the existing pin
 named beside it against that copy; the pin must fail.  A control copy without
@@ -197,3 +198,53 @@ def test_cnn_pin_catches_planted_mistake(orc, monkeypatch, case, old, new, pin):
     monkeypatch.setattr(T_cnn, "cnn", cnn_copy(old, new))
     with pytest.raises(AssertionError):
         CNN_PINS[pin]()
+
+
+# ---------------------------------------------------------------- direct-sampling statistics (oracle/__init__.py)
+from tests import test_oracle_direct as T_dir  # noqa: E402
+
+DIRECT_PINS = {
+    "autocorrelation small cases": T_dir.test_autocorrelation_small_cases,
+    "return times hand counted": T_dir.test_return_times_hand_counted,
+    "AR(1) up-crossings": T_dir.test_return_time_of_ar1_matches_the_upcrossing_probability,
+}
+
+DIRECT_MUTANTS = [
+    ("mean not removed", "    x = d - mu\n", "    x = d\n", "autocorrelation small cases"),
+    ("lag products averaged over the whole length",
+     "c[tau] = np.mean(x[:, tau:] * x[:, :length - tau]) / var",
+     "c[tau] = np.sum(x[:, tau:] * x[:, :length - tau]) / x.size / var", "autocorrelation small cases"),
+    ("observed time of one trajectory only",
+     "r = np.where(events > 0, n * length / np.maximum(events, 1), np.inf)",
+     "r = np.where(events > 0, length / np.maximum(events, 1), np.inf)", "AR(1) up-crossings"),
+    ("same-fluctuation gap inclusive",
+     "t - last_above > gap", "t - last_above >= gap", "return times hand counted"),
+    ("a series starting above the level counts an event",
+     "if t > 0 and row[t - 1] < a", "if (t == 0 or row[t - 1] < a)", "return times hand counted"),
+]
+
+
+def oracle_copy(old=None, new=None):
+    import types
+    path = os.path.join(ORACLE, "__init__.py")
+    src = open(path).read()
+    if old is not None:
+        assert src.count(old) == 1, f"oracle/__init__.py no longer holds {old!r} once: update this case"
+        src = src.replace(old, new)
+    mod = types.ModuleType("oracle_copy")
+    mod.__file__ = path  # the copy finds the compiled library beside the original
+    exec(compile(src, "oracle/__init__.py (copy)", "exec"), mod.__dict__)
+    return mod
+
+
+def test_direct_statistics_control_copy_passes_every_pin(orc):
+    copy = oracle_copy()
+    for pin in DIRECT_PINS.values():
+        pin(copy)
+
+
+@pytest.mark.parametrize("case,old,new,pin", DIRECT_MUTANTS, ids=[m[0] for m in DIRECT_MUTANTS])
+def test_direct_statistics_pin_catches_planted_mistake(orc, case, old, new, pin):
+    copy = oracle_copy(old, new)
+    with pytest.raises(AssertionError):
+        DIRECT_PINS[pin](copy)
