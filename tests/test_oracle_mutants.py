@@ -59,6 +59,7 @@ PINS = {
     "mean copies equal the weights": mean_copies,
     "observables on constructed fields": constructed_fields,
     "OU GKTL normaliser": ou_normaliser,
+    "draws use their documented counters": T_rng.test_draws_of_the_method_use_their_documented_counters,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -108,6 +109,15 @@ MUTANTS = [
      "mean copies equal the weights"),
     ("wall shear from one row (first order)", "lbm.c",
      "gt += (9.0 * u1 - u2) / 3.0;", "gt += 2.0 * u1;", "observables on constructed fields"),
+    ("initial velocity counter with clone and site swapped", "lbm.c",
+     "uint64_t ctr[4] = {5u, (uint64_t)clone, site, 0u}", "uint64_t ctr[4] = {5u, site, (uint64_t)clone, 0u}",
+     "draws use their documented counters"),
+    ("App. D weight counter with iteration and slot swapped", "lbm.c",
+     "uint64_t ctr[4] = {4u, iter, (uint64_t)slot, (uint64_t)n}",
+     "uint64_t ctr[4] = {4u, (uint64_t)slot, iter, (uint64_t)n}", "draws use their documented counters"),
+    ("AMS survivor counter with iteration and killed index swapped", "select.c",
+     "stream_word(3u, seed, iter, (uint64_t)killed[k])", "stream_word(3u, seed, (uint64_t)killed[k], iter)",
+     "draws use their documented counters"),
     ("OU noise doubled in the GKTL process", "ou.c",
      "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
      "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),

@@ -52,3 +52,31 @@ def test_below_is_multiply_high(orc):
         assert orc.below(x, m) == (x * m) >> 64
     assert orc.below(MASK, 7) == 6
     assert orc.below(0, 7) == 0
+
+
+def test_draws_of_the_method_use_their_documented_counters(orc):
+    """Every random draw of the method is one Philox4x64-10 block with key
+    (seed, 0), its words turned into 53-bit uniforms (top bits) or into an
+    index by a multiply-high: the initial velocity of clone c at site
+    s = y nx + x is amp (2u - 1) from words 0 and 1 of counter (5, c, s, 0);
+    the App. D weight alpha_n of slot s at iteration j is word 0 of
+    (4, j, s, n); the AMS survivor of killed trajectory k at iteration j is
+    the r-th of the N - |K| others, r = word 0 of (3, j, k, 0) times
+    (N - |K|) over 2^64.  Checked against numpy's Philox."""
+    def u01(w):
+        return (w >> 11) / 2.0**53
+
+    nx, ny, seed, clone, amp = 16, 8, 99, 3, 0.01
+    c = orc.cfg(nx, ny, tau=0.6)
+    _, ux, uy = orc.macro(c, orc.init(c, seed, clone, amp))
+    for x, y in [(0, 0), (5, 3), (15, 7), (9, 1)]:
+        b = numpy_block([5, clone, y * nx + x, 0], [seed, 0])
+        assert abs(ux[y, x] - amp * (2 * u01(b[0]) - 1)) < 1e-15
+        assert abs(uy[y, x] - amp * (2 * u01(b[1]) - 1)) < 1e-15
+    alpha = orc.perturb_alphas(9, 3, 5, 4)
+    for n in range(4):
+        assert alpha[n] == u01(numpy_block([4, 3, 5, n], [9, 0])[0])
+    Q = np.arange(8.0)  # trajectory 0 is killed; the survivor is one of 1..7
+    for it in range(6):
+        _, surv, _ = orc.ams_select(Q, 77, it)
+        assert surv[0] == 1 + ((numpy_block([3, it, 0, 0], [77, 0])[0] * 7) >> 64)
