@@ -60,6 +60,7 @@ PINS = {
     "observables on constructed fields": constructed_fields,
     "OU GKTL normaliser": ou_normaliser,
     "draws use their documented counters": T_rng.test_draws_of_the_method_use_their_documented_counters,
+    "integer weights copied exactly": T_sel.test_integer_weights_are_copied_exactly,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -118,6 +119,20 @@ MUTANTS = [
     ("AMS survivor counter with iteration and killed index swapped", "select.c",
      "stream_word(3u, seed, iter, (uint64_t)killed[k])", "stream_word(3u, seed, (uint64_t)killed[k], iter)",
      "draws use their documented counters"),
+    ("extra copies placed for the parents in descending order", "select.c",
+     "    for (int32_t i = 0; i < n; ++i)\n        for (int32_t e = 1; e < cnt[i]; ++e) {",
+     "    for (int32_t i = n - 1; i >= 0; --i)\n        for (int32_t e = 1; e < cnt[i]; ++e) {",
+     "integer weights copied exactly"),
+    ("log R without the 1/N", "select.c",
+     "*logR = m + log(sum / (double)n);", "*logR = m + log(sum);", "GKTL weights sum to N"),
+    ("y force taken from g_x", "lbm.c",
+     "double uy = (jy + 0.5 * c->gy) / rho;", "double uy = (jy + 0.5 * c->gx) / rho;", "momentum balance"),
+    ("forebody pressure from the square's own column", "lbm.c",
+     "node_macro(c, f, x0 - 1, y, &rho_at, &ux_at, &uy_at);", "node_macro(c, f, x0, y, &rho_at, &ux_at, &uy_at);",
+     "observables on constructed fields"),
+    ("central-moment bulk/shear coupling with the wrong sign", "lbm.c",
+     "Om[3][4] = Om[4][3] = 0.5 * (wb - ws);", "Om[3][4] = Om[4][3] = 0.5 * (ws - wb);",
+     "central moments relax at their rates"),
     ("OU noise doubled in the GKTL process", "ou.c",
      "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
      "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),
