@@ -42,6 +42,10 @@ def ou_normaliser(orc):
     T_sel.test_ou_gktl_normaliser_matches_scgf(orc, 1.0)
 
 
+def guo_moments(orc):
+    T_lbm.test_guo_source_moments(orc, 0.04, -0.03, 2e-4, -5e-4)
+
+
 PINS = {
     "momentum balance": momentum_balance,
     "equilibrium moments": equilibrium_moments,
@@ -61,6 +65,8 @@ PINS = {
     "OU GKTL normaliser": ou_normaliser,
     "draws use their documented counters": T_rng.test_draws_of_the_method_use_their_documented_counters,
     "integer weights copied exactly": T_sel.test_integer_weights_are_copied_exactly,
+    "Guo source moments": guo_moments,
+    "initial state": T_lbm.test_init_is_equilibrium_with_bounded_velocity,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -133,6 +139,14 @@ MUTANTS = [
     ("central-moment bulk/shear coupling with the wrong sign", "lbm.c",
      "Om[3][4] = Om[4][3] = 0.5 * (wb - ws);", "Om[3][4] = Om[4][3] = 0.5 * (ws - wb);",
      "central moments relax at their rates"),
+    ("Guo source without the -u term", "lbm.c",
+     "double ax = (CX[i] - ux) / CS2 + cu * CX[i] / (CS2 * CS2);", "double ax = CX[i] / CS2 + cu * CX[i] / (CS2 * CS2);",
+     "Guo source moments"),
+    ("solid nodes initialised empty", "lbm.c",
+     "for (int i = 0; i < 9; ++i) feq[i] = W[i];", "for (int i = 0; i < 9; ++i) feq[i] = 0.0;", "initial state"),
+    ("base pressure from the square's last column", "lbm.c",
+     "node_macro(c, f, x1, y, &rho_at, &ux_at, &uy_at);", "node_macro(c, f, x1 - 1, y, &rho_at, &ux_at, &uy_at);",
+     "observables on constructed fields"),
     ("OU noise doubled in the GKTL process", "ou.c",
      "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
      "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),
