@@ -70,3 +70,27 @@ def test_product_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "oracle.h" not in src, f
+
+
+def test_every_entry_point_rejects_null_handles_and_empty_sizes(L):
+    """Every exported function that takes a handle, an output pointer or a
+    count returns LBM_ERR_ARG with a message for a NULL handle (or a zero
+    count, or variant index -1), before it touches the GPU; the functions
+    without arguments and the destructors (NULL is a no-op) are left out."""
+    lib = L.lib()
+    skip = {"lbm_last_error", "lbm_launch_count", "lbm_step_variant_count", "lbm_ensemble_destroy", "cnn_destroy",
+            "cnn_param_count"}
+    special = {"lbm_step_variant_info": (-1, None, None, None), "lbm_step_variant_kind": (-1,)}
+    tried = 0
+    for name in L.EXPORTS:
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        args = special.get(name) or tuple(
+            None if t is C.c_void_p else (0.0 if t in (C.c_double, C.c_float) else 0) for t in fn.argtypes)
+        assert fn(*args) == L.LBM_ERR_ARG, name
+        assert lib.lbm_last_error(), name
+        tried += 1
+    assert tried == len(L.EXPORTS) - len(skip)
+    assert lib.lbm_ensemble_destroy(None) == L.LBM_OK and lib.cnn_destroy(None) == L.LBM_OK
+    assert lib.cnn_param_count(None) == -1
