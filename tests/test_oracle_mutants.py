@@ -67,6 +67,7 @@ PINS = {
     "integer weights copied exactly": T_sel.test_integer_weights_are_copied_exactly,
     "Guo source moments": guo_moments,
     "initial state": T_lbm.test_init_is_equilibrium_with_bounded_velocity,
+    "opposite shears in a symmetric flow": T_obs.test_symmetric_flow_has_opposite_shears,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -147,6 +148,10 @@ MUTANTS = [
     ("base pressure from the square's last column", "lbm.c",
      "node_macro(c, f, x1, y, &rho_at, &ux_at, &uy_at);", "node_macro(c, f, x1 - 1, y, &rho_at, &ux_at, &uy_at);",
      "observables on constructed fields"),
+    ("bottom-wall shear without its sign flip", "lbm.c",
+     "gb -= (9.0 * u1 - u2) / 3.0;", "gb += (9.0 * u1 - u2) / 3.0;", "opposite shears in a symmetric flow"),
+    ("forebody pressure without cs2", "lbm.c",
+     "pfb += CS2 * rho_at;", "pfb += rho_at;", "observables on constructed fields"),
     ("OU noise doubled in the GKTL process", "ou.c",
      "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
      "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),
