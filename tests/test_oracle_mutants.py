@@ -68,6 +68,7 @@ PINS = {
     "Guo source moments": guo_moments,
     "initial state": T_lbm.test_init_is_equilibrium_with_bounded_velocity,
     "opposite shears in a symmetric flow": T_obs.test_symmetric_flow_has_opposite_shears,
+    "OU AMS against direct sampling": T_sel.test_ou_ams_matches_direct_sampling,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -152,6 +153,10 @@ MUTANTS = [
      "gb -= (9.0 * u1 - u2) / 3.0;", "gb += (9.0 * u1 - u2) / 3.0;", "opposite shears in a symmetric flow"),
     ("forebody pressure without cs2", "lbm.c",
      "pfb += CS2 * rho_at;", "pfb += rho_at;", "observables on constructed fields"),
+    ("AMS estimator without its weight", "ou.c",
+     "logw += log1p(-(double)nk / (double)n);", "/* no weight */", "OU AMS against direct sampling"),
+    ("AMS branch re-simulated from the start instead of the level crossing", "ou.c",
+     "while (tb <= n_steps && !(xs[tb] > z)) tb++;", "/* branch at t = 0 */", "OU AMS against direct sampling"),
     ("OU noise doubled in the GKTL process", "ou.c",
      "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
      "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),
