@@ -248,6 +248,17 @@ def oracle_rate(steps_per_proc: int, procs: int, w):
     return updates / wall / 1e9, wall, sum(times)
 
 
+def cpu_baseline(w, cores: int) -> dict:
+    """the oracle as it stands, timed on `cores` host cores over a bounded
+    sample of the workload (each process one clone, about 20 steps of a
+    1024 x 256 lattice's worth of sites): aggregate and single-process rates"""
+    spp = max(1, int(20 * 1024 * 256 / (w["nx"] * w["ny"])))
+    v, wall, cpu_s = oracle_rate(spp, cores, w)
+    return {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle", "per_core": v * wall / cpu_s,
+            "sample": f"{cores} single-threaded oracle processes, each one clone of {w['nx']}x{w['ny']} for "
+                      f"{spp} steps ({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)"}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -262,13 +273,14 @@ def run_reference(args):
     cores = cpu_cores()
     w = workload(args)
     steps_per_proc = max(1, int(20 * 1024 * 256 / (w["nx"] * w["ny"])))
-    vals, walls = [], []
+    vals, walls, per_core = [], [], []
     for _ in range(args.warmup):
         oracle_rate(1, 1, w)
     for _ in range(args.steps):
-        v, wall, _ = oracle_rate(steps_per_proc, cores, w)
+        v, wall, cpu_s = oracle_rate(steps_per_proc, cores, w)
         vals.append(v)
         walls.append(wall)
+        per_core.append(v * wall / cpu_s)  # one process: updates per second of its own time
     value = statistics.median(vals)
     sample = (f"{cores} processes x 1 clone of {w['nx']}x{w['ny']} x {steps_per_proc} steps per step "
               f"(of {w['clones']} clones x {PERIOD} steps per workload step)")
@@ -277,7 +289,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
-        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": cores, "kind": "oracle", "sample": sample,
+                         "per_core": statistics.median(per_core)},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -325,12 +338,7 @@ def run_ours(args):
     w = workload(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cores = cpu_cores()
-        spp = max(1, int(20 * 1024 * 256 / (w["nx"] * w["ny"])))
-        v, wall, cpu_s = oracle_rate(spp, cores, w)
-        cpu = {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"{cores} single-threaded oracle processes, each one clone of {w['nx']}x{w['ny']} for "
-                         f"{spp} steps ({cpu_s:.1f} s of CPU work, {wall:.1f} s wall)"}
+        cpu = cpu_baseline(w, cpu_cores())
 
     stream = torch.cuda.current_stream()
     total_periods = args.warmup + args.steps + 2 * (args.warmup + args.steps) + 2

@@ -88,3 +88,13 @@ def test_solid_cells_of_the_workloads():
     # ..., 120-127 of 129) over the grid's 8 columns
     opn = bench.workload(argparse.Namespace(workload="open", clones=None))
     assert bench.solid_cells(opn) == 16 * 16 + 8 * 64
+
+
+def test_cpu_baseline_record_of_the_gpu_arm():
+    """the CPU-baseline object of the GPU arm's line: the oracle on two host
+    processes over the bounded sample"""
+    import argparse
+    w = bench.workload(argparse.Namespace(workload="gktl", clones=None))
+    cb = bench.cpu_baseline(w, 2)
+    assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["unit"] == "GLUPS"
+    assert 0 < cb["per_core"] <= 1.2 * cb["value"] and "1024x256" in cb["sample"]

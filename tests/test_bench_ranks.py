@@ -87,5 +87,7 @@ def test_reference_arm_prints_its_contract_line_on_rank_zero():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["n_gpus"] == 1
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    # the single-threaded rate of one process, at most the aggregate (within timing noise)
+    assert 0 < cb["per_core"] <= 1.2 * cb["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("GKTL batched ensemble")
