@@ -98,3 +98,26 @@ def test_cpu_baseline_record_of_the_gpu_arm():
     cb = bench.cpu_baseline(w, 2)
     assert cb["kind"] == "oracle" and cb["cores"] == 2 and cb["unit"] == "GLUPS"
     assert 0 < cb["per_core"] <= 1.2 * cb["value"] and "1024x256" in cb["sample"]
+
+
+def test_open_workload_is_the_paper_channel():
+    """the open-channel workload takes its numbers from Sec. 2
+    (tests/golden/paper_channel_sec2.txt); tau follows from Re_grid on the
+    bar size R/2 and the lattice viscosity nu = (tau - 1/2)/3 of App. A"""
+    import argparse
+    g = {}
+    with open(os.path.join(ROOT, "tests", "golden", "paper_channel_sec2.txt")) as fh:
+        for line in fh:
+            if "=" in line and not line.startswith("#"):
+                k, v = (s.strip() for s in line.split("="))
+                g[k] = float(v)
+    w = bench.workload(argparse.Namespace(workload="open", clones=None))
+    assert (w["nx"], w["ny"], w["side"]) == (g["nx"], g["ny"], g["R"])
+    x0, y0, sx, sy = w["obst"]
+    assert (sx, sy) == (g["R"], g["R"])
+    assert abs((x0 + sx / 2) - w["nx"] / 2) <= 0.5 and abs((y0 + sy / 2) - w["ny"] / 2) <= 0.5  # centred
+    _, _, bar, gap = bench.OPEN_GRID
+    assert (bar, gap) == (g["grid_bar"], g["grid_spacing"])
+    assert bench.OPEN_UC == g["u_centre"]
+    nu = g["u_centre"] * (g["R"] / 2) / g["Re_grid"]
+    assert abs(bench.OPEN_TAU - (0.5 + 3 * nu)) < 1e-15
