@@ -121,3 +121,15 @@ def test_open_workload_is_the_paper_channel():
     assert bench.OPEN_UC == g["u_centre"]
     nu = g["u_centre"] * (g["R"] / 2) / g["Re_grid"]
     assert abs(bench.OPEN_TAU - (0.5 + 3 * nu)) < 1e-15
+
+
+def test_perturbation_parameters_are_the_papers():
+    """every bench workload perturbs with App. D's epsilon and snapshot count
+    (tests/golden/perturbation_app_d.txt)"""
+    g = {}
+    with open(os.path.join(ROOT, "tests", "golden", "perturbation_app_d.txt")) as fh:
+        for line in fh:
+            if "=" in line and not line.startswith("#"):
+                k, v = (s.strip() for s in line.split("="))
+                g[k] = float(v)
+    assert bench.EPS == g["epsilon"] and bench.N_SNAP == g["N_s"]
