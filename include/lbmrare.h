@@ -466,9 +466,11 @@ int lbm_ensemble_fields(lbm_ensemble* e, const int32_t* clones, int32_t n, int32
  *     (FP32 f, or 16-bit (f - w_q) * 2^shift_exp), pitch = nx rounded up to a
  *     multiple of 256 elements, 16-byte aligned, distinct; padding columns are
  *     read but never written.  f_out_dev receives the state one step later.
- *   drag_dev: device double[n_clones], the momentum-exchange drag of the new
- *     state (eq. (drag_definition)).
+ *   drag_dev: device double[n_clones], 8-byte aligned: the momentum-exchange
+ *     drag of the new state, as lbm_ensemble_drag reports it.
  *   cfg: the flow (max_steps, ckpt_stride and n_snapshots are ignored).
+ * Misaligned buffers, a non-finite force and shift_exp outside [-20, 20] are
+ * rejected with LBM_ERR_ARG before anything is enqueued.
  * The call allocates nothing: its scratch (the per-warp drag partials and two
  * index tables) is a fixed 1 MiB device array inside the library, which every
  * device that loads the library holds until the process exits.  Sizes whose

@@ -10,6 +10,7 @@
 // scratch the step needs - the per-warp drag partials and two small index
 // tables - in a fixed device array that is part of the library image.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "internal.h"
@@ -53,12 +54,19 @@ extern "C" int lbm_step_noalloc(const lbm_config* cfg, int32_t n_clones, const v
                                 double* drag_dev, void* stream)
 {
     if (!cfg || !f_in_dev || !f_out_dev || !drag_dev) return fail(LBM_ERR_ARG, "lbm_step_noalloc: null argument");
+    // the step moves populations in 16-byte vectors and writes the drag as doubles
+    if (reinterpret_cast<uintptr_t>(f_in_dev) % 16 != 0 || reinterpret_cast<uintptr_t>(f_out_dev) % 16 != 0)
+        return fail(LBM_ERR_ARG, "lbm_step_noalloc: population buffers must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(drag_dev) % 8 != 0)
+        return fail(LBM_ERR_ARG, "lbm_step_noalloc: drag_dev must be 8-byte aligned");
     const lbm_config c = *cfg;
     if (c.nx < 8 || c.nx % 8 != 0) return fail(LBM_ERR_ARG, "lbm_step_noalloc: nx must be a positive multiple of 8");
     if (c.ny < 2) return fail(LBM_ERR_ARG, "lbm_step_noalloc: ny must be at least 2");
     if (n_clones < 1 || n_clones > 65535) return fail(LBM_ERR_ARG, "lbm_step_noalloc: clone count must be in [1, 65535]");
     if (!(c.tau > 0.5) || !std::isfinite(c.tau)) return fail(LBM_ERR_ARG, "lbm_step_noalloc: tau must exceed 1/2");
+    if (!std::isfinite(c.gx) || !std::isfinite(c.gy)) return fail(LBM_ERR_ARG, "lbm_step_noalloc: force must be finite");
     if (c.storage < 0 || c.storage > 2) return fail(LBM_ERR_ARG, "lbm_step_noalloc: unknown storage");
+    if (c.shift_exp < -20 || c.shift_exp > 20) return fail(LBM_ERR_ARG, "lbm_step_noalloc: shift_exp out of range");
     if (c.obs_w < 0 || c.obs_h < 0 || (c.obs_w > 0) != (c.obs_h > 0))
         return fail(LBM_ERR_ARG, "lbm_step_noalloc: obstacle size");
     if (c.obs_w > 0 && (c.obs_x0 < 1 || c.obs_x0 + c.obs_w > c.nx - 1 || c.obs_y0 < 0 || c.obs_y0 + c.obs_h > c.ny))

@@ -594,9 +594,15 @@ def lbm_step_noalloc(cfg: lbm_config, n_clones: int, f_in_dev, f_out_dev, drag_d
     """One fused step over caller-owned buffers [n_clones][9][ny][pitch] (torch
     CUDA tensors of the storage dtype); drag_dev: float64 [n_clones]."""
     import torch
+    want = {0: torch.float32, 1: torch.float16, 2: torch.bfloat16}.get(cfg.storage)
+    need = n_clones * 9 * cfg.ny * noalloc_pitch(cfg.nx)
     for t in (f_in_dev, f_out_dev):
         if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
             raise TypeError("population buffers must be contiguous torch CUDA tensors")
+        if want is not None and t.dtype != want:
+            raise TypeError(f"population buffers of this storage are {want}, got {t.dtype}")
+        _need(t, need, "population buffer")
+    _need(drag_dev, n_clones, "drag_dev")
     _check(lib().lbm_step_noalloc(C.byref(cfg), n_clones, C.c_void_p(f_in_dev.data_ptr()),
                                   C.c_void_p(f_out_dev.data_ptr()), _dev(drag_dev, torch.float64), _stream(stream)))
 

@@ -94,3 +94,23 @@ def test_every_entry_point_rejects_null_handles_and_empty_sizes(L):
     assert tried == len(L.EXPORTS) - len(skip)
     assert lib.lbm_ensemble_destroy(None) == L.LBM_OK and lib.cnn_destroy(None) == L.LBM_OK
     assert lib.cnn_param_count(None) == -1
+
+
+def test_noalloc_rejects_misaligned_or_invalid_arguments_before_the_gpu(L):
+    """lbm_step_noalloc checks the alignment of the caller's buffers (16 bytes
+    for the populations, 8 for the drag), the force and the 16-bit scale
+    exponent on the host; the pointers below are never dereferenced."""
+    lib = L.lib()
+    good = L.config(64, 16, tau=0.6, max_steps=1)
+    fin, fout, drag = C.c_void_p(0x10000), C.c_void_p(0x20000), C.c_void_p(0x30000)
+    cases = [
+        (good, C.c_void_p(0x10004), fout, drag, b"16-byte aligned"),
+        (good, fin, C.c_void_p(0x20008), drag, b"16-byte aligned"),
+        (good, fin, fout, C.c_void_p(0x30004), b"8-byte aligned"),
+        (L.config(64, 16, tau=0.6, gx=float("inf"), max_steps=1), fin, fout, drag, b"force"),
+        (L.config(64, 16, tau=0.6, gy=float("nan"), max_steps=1), fin, fout, drag, b"force"),
+        (L.config(64, 16, tau=0.6, max_steps=1, storage="fp16", shift_exp=40), fin, fout, drag, b"shift_exp"),
+    ]
+    for cfg, a, b, d, msg in cases:
+        assert lib.lbm_step_noalloc(C.byref(cfg), 1, a, b, d, None) == L.LBM_ERR_ARG
+        assert msg in lib.lbm_last_error()

@@ -44,10 +44,12 @@ def unpack(buf, c, storage, nx):
     return a if storage == "fp32" else a + w
 
 
-@pytest.mark.parametrize("storage", ["fp32", "bf16"])
-def test_noalloc_two_steps_match_ensemble(L, storage):
+@pytest.mark.parametrize("storage,obstacle", [("fp32", (50, 14, 9, 7)), ("fp16", (50, 14, 9, 7)),
+                                              ("bf16", (50, 14, 9, 7)), ("fp32", (0, 0, 0, 0)),
+                                              ("fp16", (0, 0, 0, 0))])
+def test_noalloc_two_steps_match_ensemble(L, storage, obstacle):
     nx, ny, n = 200, 37, 3
-    kw = dict(nx=nx, ny=ny, obstacle=(50, 14, 9, 7), tau=0.6, gx=2e-5, gy=-5e-6, max_steps=8, storage=storage)
+    kw = dict(nx=nx, ny=ny, obstacle=obstacle, tau=0.6, gx=2e-5, gy=-5e-6, max_steps=8, storage=storage)
     cfg = L.config(**kw)
     stream = torch.cuda.current_stream()
     e = L.lbm_ensemble_create(cfg, n, 5, stream)
@@ -70,14 +72,39 @@ def test_noalloc_two_steps_match_ensemble(L, storage):
         got = unpack(a, c, storage, nx)
         assert np.abs(got - ref[c]).max() <= POP_TOL * np.abs(ref[c]).max()
     drag = torch.stack([d1, d2], dim=1).cpu().numpy()
-    assert np.abs(drag - ref_drag).max() <= DRAG_TOL * np.abs(ref_drag).max()
+    if obstacle[2] == 0:  # no obstacle, no drag
+        assert np.all(drag == 0.0) and np.all(ref_drag == 0.0)
+    else:
+        assert np.abs(drag - ref_drag).max() <= DRAG_TOL * np.abs(ref_drag).max()
 
 
 def test_noalloc_rejects_oversized_scratch(L):
-    cfg = L.config(1024, 256, obstacle=(240, 112, 32, 32), tau=0.6, max_steps=1)
-    a = torch.zeros(1, dtype=torch.float32, device="cuda")
-    d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    """Buffers of the right size and type, so that only the scratch limit can
+    reject the call: 1200 clones of 256 x 128 with a 60 x 124 obstacle that
+    spans two 128-site row segments need 1200 x (126 rows x 2 segments) drag
+    slots x 4 bytes, more than the fixed 1 MiB."""
+    n, nx, ny = 1200, 256, 128
+    cfg = L.config(nx, ny, obstacle=(100, 2, 60, 124), tau=0.6, max_steps=1)
+    a = torch.zeros((n, 9, ny, L.noalloc_pitch(nx)), dtype=torch.float32, device="cuda")
+    b = torch.zeros_like(a)
+    d = torch.zeros(n, dtype=torch.float64, device="cuda")
     with pytest.raises(L.LbmError) as ei:
-        L.lbm_step_noalloc(cfg, 60000, a, a.clone(), d)
+        L.lbm_step_noalloc(cfg, n, a, b, d)
     assert ei.value.status == L.LBM_ERR_ARG
     assert "1048576" in str(ei.value)
+    del a, b
+    torch.cuda.empty_cache()
+
+
+def test_noalloc_wrapper_rejects_short_or_mistyped_buffers(L):
+    nx, ny, n = 64, 16, 2
+    cfg = L.config(nx, ny, tau=0.6, max_steps=1, storage="fp16")
+    shape = (n, 9, ny, L.noalloc_pitch(nx))
+    a = torch.zeros(shape, dtype=torch.float16, device="cuda")
+    d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):  # FP32 buffers for 16-bit storage
+        L.lbm_step_noalloc(cfg, n, a.float(), a.float().clone(), d)
+    with pytest.raises(TypeError):  # one clone short
+        L.lbm_step_noalloc(cfg, n, a[:1].contiguous(), a.clone(), d)
+    with pytest.raises(TypeError):  # drag for one clone only
+        L.lbm_step_noalloc(cfg, n, a, a.clone(), d[:1])
