@@ -94,9 +94,11 @@ def _load(path: str):
     L.orc_gktl_select.argtypes = [i32, p, u64, u64, p]; L.orc_gktl_select.restype = C.c_int
     L.orc_ams_select.argtypes = [i32, p, u64, u64, p, p, p, p]; L.orc_ams_select.restype = C.c_int
     L.orc_ou_noise.argtypes = [u64, u64, u64, u64]; L.orc_ou_noise.restype = d
-    L.orc_ou_gktl.argtypes = [i32, i32, i32, d, d, u64, p, i32, p]; L.orc_ou_gktl.restype = d
+    L.orc_ou_gktl.argtypes = [i32, i32, i32, d, d, d, u64, p, i32, p, p, p, p]; L.orc_ou_gktl.restype = d
     L.orc_ou_direct_max.argtypes = [i64, i32, d, u64, i32, p, p]
     L.orc_ou_ams.argtypes = [i32, i32, d, d, i32, u64, p]; L.orc_ou_ams.restype = d
+    L.orc_ou_ams_score.argtypes = [i32, i32, d, i32, i32, d, d, i32, u64, p, p, p, i32, p, p, p]
+    L.orc_ou_ams_score.restype = d
     return L
 
 
@@ -274,11 +276,23 @@ def ams_select(Q, seed, it):
 
 
 # ---------------------------------------------------------------- OU test process
-def ou_gktl(n, n_periods, steps_per_period, dt, k, seed, window_steps=0):
+def ou_gktl(n, n_periods, steps_per_period, dt, k, seed, window_steps=0, kappa=0.0, full=False):
+    """GKTL on the OU process (orc_ou_gktl).  Returns (log Z, final integrals,
+    final max of the window mean or None); with full=True a dict that adds the
+    final histories [N][M + 1], the potential's corrections
+    kappa (V(x_{T_a}) - V(x_0)) and log R of each cloning step."""
+    M = n_periods * steps_per_period
     fi = np.zeros(n)
     mm = np.zeros(n)
-    logZ = lib().orc_ou_gktl(n, n_periods, steps_per_period, dt, k, seed, _ptr(fi), window_steps,
-                             _ptr(mm) if window_steps > 0 else None)
+    hist = np.zeros((n, M + 1)) if full else None
+    corr = np.zeros(n)
+    logR = np.zeros(n_periods)
+    logZ = lib().orc_ou_gktl(n, n_periods, steps_per_period, dt, k, kappa, seed, _ptr(fi), window_steps,
+                             _ptr(mm) if window_steps > 0 else None, _ptr(hist) if full else None, _ptr(corr),
+                             _ptr(logR))
+    if full:
+        return dict(log_z=logZ, integrals=fi, max_mean=(mm if window_steps > 0 else None), hist=hist,
+                    correction=corr, log_r=logR)
     return logZ, fi, (mm if window_steps > 0 else None)
 
 
@@ -293,6 +307,21 @@ def ou_ams(n, n_steps, dt, a, j_max, seed):
     it = C.c_int32()
     p = lib().orc_ou_ams(n, n_steps, dt, a, j_max, seed, C.byref(it))
     return p, it.value
+
+
+def ou_ams_score(n, n_steps, dt, stride, score_window, score_level, a, j_max, seed):
+    """AMS on the OU process with a trailing-mean score seen every stride steps
+    (orc_ou_ams_score).  Returns (estimate, iterations, log weight, event
+    maxima[N], killed records (log weight before the kill, event maximum))."""
+    it = C.c_int32()
+    lw = C.c_double()
+    nr = C.c_int32()
+    mx = np.zeros(n)
+    cap = j_max * n
+    rl, rm = np.zeros(max(cap, 1)), np.zeros(max(cap, 1))
+    p = lib().orc_ou_ams_score(n, n_steps, dt, stride, score_window, score_level, a, j_max, seed, C.byref(it),
+                               C.byref(lw), _ptr(mx), cap, C.byref(nr), _ptr(rl), _ptr(rm))
+    return p, it.value, lw.value, mx, (rl[:nr.value].copy(), rm[:nr.value].copy())
 
 
 # ---------------------------------------------------------------- observables & estimators
@@ -313,22 +342,25 @@ def trailing_mean_max(drag: np.ndarray, window: int, t_end: int | None = None, t
     if t_end is None:
         t_end = d.shape[1]
     out = np.full(d.shape[0], -np.inf)
-    for n in range(d.shape[0]):
-        for t in range(t_begin + window, t_end + 1):
-            m = np.sum(d[n, t - window:t]) / window
-            if m > out[n]:
-                out[n] = m
-    return out
+    if t_end < t_begin + window:
+        return out
+    # the window ending after step t holds drag[:, t - window:t]; t runs over
+    # [t_begin + window, t_end], so the windows start at t_begin .. t_end - window
+    windows = np.lib.stride_tricks.sliding_window_view(d[:, t_begin:t_end], window, axis=1)
+    return np.max(np.sum(windows, axis=2) / window, axis=1)
 
 
 def gktl_probability(log_z: float, k: float, integrals: np.ndarray, maxima: np.ndarray,
-                     levels: np.ndarray) -> np.ndarray:
+                     levels: np.ndarray, correction: np.ndarray | None = None) -> np.ndarray:
     """App. C.2: P(F_T >= a) ~ (1/N) sum_j Z e^{-k int_0^{T_a} A_j} 1{max F_T^(j) >= a},
     the biased path measure of eq. (Biased_Path_Approximation) inverted (the
-    printed exponent's sign is read as the inversion requires)."""
+    printed exponent's sign is read as the inversion requires).  With a
+    potential in the exponents, correction[j] = kappa (V_j(T_a) - V_j(0)) of
+    each final trajectory divides its weight by e^{correction[j]}."""
     integrals = np.asarray(integrals, dtype=np.float64)
     maxima = np.asarray(maxima, dtype=np.float64)
-    w = np.exp(log_z - k * integrals)
+    corr = np.zeros_like(integrals) if correction is None else np.asarray(correction, dtype=np.float64)
+    w = np.exp(log_z - k * integrals - corr)
     return np.array([np.sum(w * (maxima >= a)) / len(w) for a in np.atleast_1d(levels)])
 
 
@@ -339,11 +371,22 @@ def return_time(p: np.ndarray, t_a: float, t_window: float) -> np.ndarray:
         return -(t_a - t_window) / np.log1p(-p)
 
 
-def ams_probability(log_weight: float, maxima: np.ndarray, level: float) -> float:
-    """Generalised AMS estimator: prod_j (1 - |K_j|/N) times the fraction of the
-    final ensemble whose maximum reaches the level."""
+def ams_probability(log_weight: float, maxima: np.ndarray, level: float, killed=None) -> float:
+    """Generalised AMS estimator (Brehier, Lelievre & Rousset 2016) of the
+    probability that the event maximum reaches the level: every trajectory the
+    run has seen counts with its weight over N.  The final ensemble's weight is
+    prod_j (1 - |K_j|/N) = e^{log_weight}; killed = (log weights before each
+    kill, event maxima of the killed trajectories) adds those killed at
+    iteration j with weight prod_{i<j} (1 - |K_i|/N).  With the event's own
+    observable as the score no killed trajectory reaches a level above the
+    last killed one, and the final ensemble alone gives the estimate."""
     maxima = np.asarray(maxima, dtype=np.float64)
-    return float(np.exp(log_weight) * np.mean(maxima >= level))
+    n = len(maxima)
+    p = np.exp(log_weight) * np.sum(maxima >= level) / n
+    if killed is not None:
+        lw_k, mx_k = (np.asarray(a, dtype=np.float64) for a in killed)
+        p += np.sum(np.exp(lw_k) * (mx_k >= level)) / n
+    return float(p)
 
 
 # ---------------------------------------------------------------- direct sampling (Sec. 3)

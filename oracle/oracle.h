@@ -145,11 +145,17 @@ int orc_ams_select(int32_t n, const double* Q, uint64_t seed, uint64_t iter,
 /* ---------------- Ornstein-Uhlenbeck test process (App. B.2) ---------- */
 /* exact AR(1) discretisation of dx = -x dt + dW with <dW dW> = dt */
 double orc_ou_noise(uint64_t seed, uint64_t a, uint64_t b, uint64_t c);
-/* GKTL on the OU process with observable A = x.  Returns log Z = sum_i log R_i;
- * final_int[N] = time integral over [0, T_a] of each final trajectory;
- * final_max_mean (may be NULL) with window T: max over t of (1/T) int_{t-T}^t x. */
-double orc_ou_gktl(int32_t n, int32_t n_periods, int32_t steps_per_period, double dt, double k,
-                   uint64_t seed, double* final_int, int32_t window_steps, double* final_max_mean);
+/* GKTL on the OU process with observable A = x and potential kappa V, V = x
+ * (kappa = 0: the plain algorithm).  Returns log Z = sum_i log R_i; every
+ * output may be NULL:
+ *   final_int[N]    time integral over [0, T_a] of each final trajectory;
+ *   final_max_mean  with window T: max over t of (1/T) int_{t-T}^t x;
+ *   final_hist      [N][M + 1] each final trajectory x_0..x_M (its genealogy);
+ *   final_corr[N]   kappa (V(x_{T_a}) - V(x_0)) of each final trajectory;
+ *   logR_out        [n_periods] log R_i of each cloning step. */
+double orc_ou_gktl(int32_t n, int32_t n_periods, int32_t steps_per_period, double dt, double k, double kappa,
+                   uint64_t seed, double* final_int, int32_t window_steps, double* final_max_mean,
+                   double* final_hist, double* final_corr, double* logR_out);
 /* direct sampling: fraction of n trajectories (stationary start) whose max over
  * steps 0..n_steps of x reaches each level a[j] */
 void orc_ou_direct_max(int64_t n, int32_t n_steps, double dt, uint64_t seed,
@@ -159,6 +165,18 @@ void orc_ou_direct_max(int64_t n, int32_t n_steps, double dt, uint64_t seed,
  * P(max x >= a); *iters receives the number of iterations. */
 double orc_ou_ams(int32_t n, int32_t n_steps, double dt, double a, int32_t j_max,
                   uint64_t seed, int32_t* iters);
+/* AMS on the OU process with the trailing mean of x over score_window steps,
+ * taken at every stride-th step, as score; stops when the killed level reaches
+ * score_level or after j_max iterations.  Returns the estimate of
+ * P(max_t x >= a), the killed trajectories included; *out_logw =
+ * sum_j ln(1 - |K_j|/N) and out_event_max[N] = max_t x of each final
+ * trajectory; one record per killed trajectory, in kill order, of the log
+ * weight before its iteration (rec_logw) and its max_t x (rec_max), the first
+ * rec_cap of them stored, their number in *n_rec (outputs may be NULL). */
+double orc_ou_ams_score(int32_t n, int32_t n_steps, double dt, int32_t stride, int32_t score_window,
+                        double score_level, double a, int32_t j_max, uint64_t seed, int32_t* iters,
+                        double* out_logw, double* out_event_max, int32_t rec_cap, int32_t* n_rec,
+                        double* rec_logw, double* rec_max);
 
 #ifdef __cplusplus
 }

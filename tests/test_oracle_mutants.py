@@ -16,6 +16,7 @@ from tests import test_oracle_mrt as T_mrt
 from tests import test_oracle_observables as T_obs
 from tests import test_oracle_open as T_open
 from tests import test_oracle_rng as T_rng
+from tests import test_oracle_estimators as T_est
 from tests import test_oracle_select as T_sel
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -46,6 +47,26 @@ def guo_moments(orc):
     T_lbm.test_guo_source_moments(orc, 0.04, -0.03, 2e-4, -5e-4)
 
 
+_DIRECT_WINDOW = []
+
+
+def direct_window():
+    """the brute-force tail probabilities of the estimator pins, computed once"""
+    if not _DIRECT_WINDOW:
+        mx = T_est.ou_direct_window_max(200000, T_est.PERIODS * T_est.STEPS_PER_PERIOD, T_est.WINDOW, T_est.DT, 2024)
+        p = T_est.np.array([(mx >= a).mean() for a in T_est.LEVELS])
+        _DIRECT_WINDOW.append((p, T_est.np.sqrt(p * (1 - p) / mx.size)))
+    return _DIRECT_WINDOW[0]
+
+
+def gktl_estimator(orc):
+    T_est.test_gktl_estimator_matches_direct_sampling(orc, direct_window(), 0.5)
+
+
+def gktl_potential(orc):
+    T_est.test_gktl_with_potential_matches_direct_sampling(orc, direct_window())
+
+
 PINS = {
     "momentum balance": momentum_balance,
     "equilibrium moments": equilibrium_moments,
@@ -69,6 +90,10 @@ PINS = {
     "initial state": T_lbm.test_init_is_equilibrium_with_bounded_velocity,
     "opposite shears in a symmetric flow": T_obs.test_symmetric_flow_has_opposite_shears,
     "OU AMS against direct sampling": T_sel.test_ou_ams_matches_direct_sampling,
+    "GKTL estimator against direct sampling": gktl_estimator,
+    "GKTL with a potential against direct sampling": gktl_potential,
+    "GKTL potential bookkeeping": T_est.test_gktl_potential_bookkeeping,
+    "AMS with another score against direct sampling": T_est.test_ams_estimator_with_another_score_matches_direct_sampling,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -156,10 +181,21 @@ MUTANTS = [
     ("AMS estimator without its weight", "ou.c",
      "logw += log1p(-(double)nk / (double)n);", "/* no weight */", "OU AMS against direct sampling"),
     ("AMS branch re-simulated from the start instead of the level crossing", "ou.c",
-     "while (tb <= n_steps && !(xs[tb] > z)) tb++;", "/* branch at t = 0 */", "OU AMS against direct sampling"),
+     "while (tb <= n_steps && !(ams_score_at(xs, tb, score_window) > z)) tb += stride;", "/* branch at t = 0 */",
+     "OU AMS against direct sampling"),
     ("OU noise doubled in the GKTL process", "ou.c",
      "x[i] = a * x[i] + sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);",
      "x[i] = a * x[i] + 2.0 * sig * orc_ou_noise(seed, (uint64_t)step, (uint64_t)i, 0u);", "OU GKTL normaliser"),
+    ("potential's start value not carried through the genealogy", "ou.c",
+     "v0n[i] = v0[parent[i]];", "v0n[i] = v0[i];", "GKTL potential bookkeeping"),
+    ("potential added with the wrong sign", "ou.c",
+     "s[i] = k * acc + kappa * (x[i] - vprev[i]);", "s[i] = k * acc - kappa * (x[i] - vprev[i]);",
+     "GKTL with a potential against direct sampling"),
+    ("potential's previous value left at the start", "ou.c",
+     "memcpy(vprev, xn, sizeof(double) * n);", "/* vprev kept */", "GKTL with a potential against direct sampling"),
+    ("AMS killed trajectories left out of the estimate", "ou.c",
+     "if (mk >= alev) p_killed += exp(logw) / (double)n;", "/* killed left out */",
+     "AMS with another score against direct sampling"),
 ]
 
 
@@ -297,3 +333,56 @@ def test_direct_statistics_pin_catches_planted_mistake(orc, case, old, new, pin)
     copy = oracle_copy(old, new)
     with pytest.raises(AssertionError):
         DIRECT_PINS[pin](copy)
+
+
+# ---------------------------------------------------------------- estimator helpers (oracle/__init__.py)
+ESTIMATOR_PINS = {
+    "window sum hand computed": T_est.test_window_sum_hand_computed,
+    "trailing mean max hand computed": T_est.test_trailing_mean_max_hand_computed,
+    "return time of a Poisson process": T_est.test_return_time_of_a_poisson_process,
+    "GKTL estimator against direct sampling": gktl_estimator,
+    "GKTL with a potential against direct sampling": gktl_potential,
+    "AMS estimator hand computed": T_est.test_ams_probability_hand_computed,
+    "AMS with another score against direct sampling": T_est.test_ams_estimator_with_another_score_matches_direct_sampling,
+}
+
+ESTIMATOR_MUTANTS = [
+    ("GKTL exponent's sign flipped (the printed e^{+kI})",
+     "w = np.exp(log_z - k * integrals - corr)", "w = np.exp(log_z + k * integrals - corr)",
+     "GKTL estimator against direct sampling"),
+    ("potential's correction left out",
+     "w = np.exp(log_z - k * integrals - corr)", "w = np.exp(log_z - k * integrals)",
+     "GKTL with a potential against direct sampling"),
+    ("time-averaged drag window one step late",
+     "sliding_window_view(d[:, t_begin:t_end], window, axis=1)",
+     "sliding_window_view(d[:, t_begin + 1:t_end + 1], window, axis=1)", "trailing mean max hand computed"),
+    ("time-averaged drag window one step early",
+     "sliding_window_view(d[:, t_begin:t_end], window, axis=1)",
+     "sliding_window_view(d[:, max(t_begin - 1, 0):t_end - 1], window, axis=1)", "trailing mean max hand computed"),
+    ("GKTL window sum one step late",
+     "return k * np.sum(np.asarray(drag, dtype=np.float64)[:, t0:t1], axis=1)",
+     "return k * np.sum(np.asarray(drag, dtype=np.float64)[:, t0 + 1:t1 + 1], axis=1)", "window sum hand computed"),
+    ("return time over T_a instead of T_a - T",
+     "return -(t_a - t_window) / np.log1p(-p)", "return -t_a / np.log1p(-p)", "return time of a Poisson process"),
+    ("return time to first order in P",
+     "return -(t_a - t_window) / np.log1p(-p)", "return (t_a - t_window) / p", "return time of a Poisson process"),
+    ("AMS estimator without its weight",
+     "p = np.exp(log_weight) * np.sum(maxima >= level) / n", "p = np.sum(maxima >= level) / n",
+     "AMS estimator hand computed"),
+    ("AMS killed records left out",
+     "p += np.sum(np.exp(lw_k) * (mx_k >= level)) / n", "p += 0.0",
+     "AMS with another score against direct sampling"),
+]
+
+
+def test_estimator_control_copy_passes_every_pin(orc):
+    copy = oracle_copy()
+    for pin in ESTIMATOR_PINS.values():
+        pin(copy)
+
+
+@pytest.mark.parametrize("case,old,new,pin", ESTIMATOR_MUTANTS, ids=[m[0] for m in ESTIMATOR_MUTANTS])
+def test_estimator_pin_catches_planted_mistake(orc, case, old, new, pin):
+    copy = oracle_copy(old, new)
+    with pytest.raises(AssertionError):
+        ESTIMATOR_PINS[pin](copy)
