@@ -341,7 +341,12 @@ int gktl_probability(int32_t n, double k, const double* logR_dev, int32_t n_peri
  * and re-simulate it to t0 + t_a.  Outputs: *iterations (kills done),
  * *log_weight = sum_j ln(1 - |K_j|/N), Q_dev[N] the final score maxima, and
  * on the host levels[j-1] = z_j and n_killed[j-1] = |K_j| (either may be NULL;
- * max_iter entries; ties at the minimum are killed together).  Waits. */
+ * max_iter entries; ties at the minimum are killed together), and
+ * killed_max[(j-1) * N + i] (may be NULL; max_iter * N entries) the event
+ * maximum - the time-averaged drag over window, maximised over the run - of the
+ * i-th trajectory killed at iteration j, taken before it is replaced.  The
+ * generalised AMS estimator counts these killed trajectories (ams_probability);
+ * with the drag as score each one's maximum is z_j.  Waits. */
 typedef struct {
     int32_t t_a;          /* trajectory duration, steps */
     int32_t window;       /* score window T, steps */
@@ -356,12 +361,20 @@ typedef struct {
                              evenly spaced trajectories at the branching checkpoint */
 } lbm_ams_params;
 int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* p, int32_t* iterations, double* log_weight, double* Q_dev,
-                double* levels, int32_t* n_killed);
+                double* levels, int32_t* n_killed, double* killed_max);
 
 /* AMS estimator (generalised AMS, Brehier-Lelievre-Rousset 2016; the paper
- * states none): p_dev[j] = exp(log_weight) * (1/N) #{n : Q_n >= a_j}. */
-int ams_probability(int32_t n, double log_weight, const double* Q_dev, int32_t n_levels, const double* levels_dev,
-                    double* p_dev, void* stream);
+ * states none): every trajectory the run has seen counts with its weight,
+ * p_dev[l] = (exp(log_weight) #{n : Q_n >= a_l}
+ *            + sum_r exp(rec_logw_dev[r]) 1{rec_max_dev[r] >= a_l}) / N,
+ * with Q_dev[N] the final ensemble's event maxima and one record r per killed
+ * trajectory: the log weight before its iteration, sum_{i<j} ln(1 - |K_i|/N),
+ * and its event maximum (lbm_ams_run's killed_max).  n_records = 0 counts the
+ * final ensemble only, which is exact when the score is the event's own
+ * observable and a_l lies above the last killed level.  FP64, fixed-order sums. */
+int ams_probability(int32_t n, double log_weight, const double* Q_dev, int32_t n_records, const double* rec_logw_dev,
+                    const double* rec_max_dev, int32_t n_levels, const double* levels_dev, double* p_dev,
+                    void* stream);
 
 /* ---------------------------------------------------------------- learned score */
 

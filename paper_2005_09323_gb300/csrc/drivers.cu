@@ -5,9 +5,12 @@
 //   log R_i.  Estimator (App. C.2): P(F_T >= a) = (1/N) sum_j Z e^{-k I_j}
 //   1{max F_T^(j) >= a}, r(a) = -(T_a - T) / ln(1 - P).
 //   AMS (App. B.1): trajectories of fixed duration T_a, score = time-averaged
-//   drag over a window; kill the minimum maximum, branch a survivor at the
-//   killed level, re-simulate.  Estimator: prod_j (1 - |K_j|/N) times the
-//   fraction of the final ensemble whose maximum reaches a.
+//   drag over a window (or a learned score); kill the minimum maximum, branch a
+//   survivor at the killed level, re-simulate.  Estimator (generalised AMS):
+//   every trajectory the run has seen counts with its weight over N - a killed
+//   one with prod_{i<j} (1 - |K_i|/N), a final one with prod_j (1 - |K_j|/N) -
+//   times 1{its time-averaged drag maximum >= a}.  With the drag as score the
+//   killed ones all lie below the levels above the last killed one.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -50,20 +53,31 @@ __global__ void gktl_probability_kernel(int32_t n, double k, const double* logR,
     }
 }
 
-__global__ void ams_probability_kernel(int32_t n, double log_weight, const double* Q, const double* levels,
+// one block per level: the final ensemble's count and the killed records'
+// weighted sum, fixed-order reductions
+__global__ void ams_probability_kernel(int32_t n, double log_weight, const double* Q, int32_t n_rec,
+                                       const double* rec_logw, const double* rec_max, const double* levels,
                                        double* p_out)
 {
     __shared__ int sh[kEstThreads];
+    __shared__ double shr[kEstThreads];
     const double a = levels[blockIdx.x];
     int cnt = 0;
     for (int j = threadIdx.x; j < n; j += kEstThreads) cnt += Q[j] >= a ? 1 : 0;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < n_rec; r += kEstThreads)
+        if (rec_max[r] >= a) acc += exp(rec_logw[r]);
     sh[threadIdx.x] = cnt;
+    shr[threadIdx.x] = acc;
     __syncthreads();
     for (int off = kEstThreads / 2; off > 0; off >>= 1) {
-        if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+        if ((int)threadIdx.x < off) {
+            sh[threadIdx.x] += sh[threadIdx.x + off];
+            shr[threadIdx.x] += shr[threadIdx.x + off];
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) p_out[blockIdx.x] = exp(log_weight) * (double)sh[0] / (double)n;
+    if (threadIdx.x == 0) p_out[blockIdx.x] = (exp(log_weight) * (double)sh[0] + shr[0]) / (double)n;
 }
 
 // s_n += kappa (V_now - V_prev): the telescoping potential of the exponent
@@ -122,13 +136,15 @@ int gktl_probability(int32_t n, double k, const double* logR_dev, int32_t n_peri
     return LBM_OK;
 }
 
-int ams_probability(int32_t n, double log_weight, const double* Q_dev, int32_t n_levels, const double* levels_dev,
-                    double* p_dev, void* stream)
+int ams_probability(int32_t n, double log_weight, const double* Q_dev, int32_t n_records, const double* rec_logw_dev,
+                    const double* rec_max_dev, int32_t n_levels, const double* levels_dev, double* p_dev, void* stream)
 {
-    if (n < 1 || n_levels < 1 || n_levels > 65535) return fail(LBM_ERR_ARG, "ams_probability: sizes");
+    if (n < 1 || n_levels < 1 || n_levels > 65535 || n_records < 0) return fail(LBM_ERR_ARG, "ams_probability: sizes");
     if (!Q_dev || !levels_dev || !p_dev) return fail(LBM_ERR_ARG, "ams_probability: null pointer");
-    ams_probability_kernel<<<n_levels, kEstThreads, 0, static_cast<cudaStream_t>(stream)>>>(n, log_weight, Q_dev,
-                                                                                           levels_dev, p_dev);
+    if (n_records > 0 && (!rec_logw_dev || !rec_max_dev))
+        return fail(LBM_ERR_ARG, "ams_probability: null killed records");
+    ams_probability_kernel<<<n_levels, kEstThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        n, log_weight, Q_dev, n_records, rec_logw_dev, rec_max_dev, levels_dev, p_dev);
     LBM_CUDA(cudaGetLastError());
     count_launches(1);
     return LBM_OK;
@@ -217,7 +233,7 @@ int lbm_gktl_run(lbm_ensemble* e, const lbm_gktl_params* prm, double* logR_dev, 
 }
 
 int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* prm, int32_t* iterations, double* log_weight, double* Q_dev,
-                double* levels, int32_t* n_killed)
+                double* levels, int32_t* n_killed, double* killed_max)
 {
     if (!e || !prm || !iterations || !log_weight || !Q_dev) return fail(LBM_ERR_ARG, "lbm_ams_run: null argument");
     const lbm_ams_params p = *prm;
@@ -274,7 +290,9 @@ int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* prm, int32_t* iterations,
     int32_t* surv = killed + e->n;
     int32_t* nk_dev = surv + e->n;
     double* z_dev = e->red_partials + 2 * (size_t)e->n;  // after the two int tables (2n ints = n doubles)
+    double* ev_dev = e->red_partials + 3 * (size_t)e->n;  // event maxima before a kill (learned score)
     std::vector<int32_t> hk(e->n), hs(e->n);
+    std::vector<double> ev(learned ? e->n : 0);
     double lw = 0.0;
     int32_t done = 0;
     for (int32_t j = 1; j <= p.max_iter; ++j) {
@@ -288,7 +306,13 @@ int lbm_ams_run(lbm_ensemble* e, const lbm_ams_params* prm, int32_t* iterations,
         if (z >= p.level || nk >= e->n) break;
         LBM_CUDA(cudaMemcpyAsync(hk.data(), killed, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, e->stream));
         LBM_CUDA(cudaMemcpyAsync(hs.data(), surv, sizeof(int32_t) * nk, cudaMemcpyDeviceToHost, e->stream));
+        if (learned && killed_max) {  // the killed trajectories' own event maxima, before they are replaced
+            if ((rc = lbm_ensemble_scores(e, p.window, t0, t_end, ev_dev))) return rc;
+            LBM_CUDA(cudaMemcpyAsync(ev.data(), ev_dev, sizeof(double) * e->n, cudaMemcpyDeviceToHost, e->stream));
+        }
         LBM_CUDA(cudaStreamSynchronize(e->stream));
+        if (killed_max)  // with the drag as score a killed trajectory's maximum is the level itself
+            for (int32_t i = 0; i < nk; ++i) killed_max[(int64_t)(j - 1) * e->n + i] = learned ? ev[hk[i]] : z;
         // branching times from the scores of the survivors (not modified here)
         std::vector<int32_t> tb(nk);
         for (int32_t i = 0; i < nk; ++i) {

@@ -136,8 +136,8 @@ def lib():
             "lbm_step_noalloc": ([p, i32, p, p, p, p], C.c_int),
             "lbm_gktl_run": ([p, p, p, p, p, p, p], C.c_int),
             "gktl_probability": ([i32, d, p, i32, p, p, p, i32, p, d, d, p, p, p], C.c_int),
-            "lbm_ams_run": ([p, p, p, p, p, p, p], C.c_int),
-            "ams_probability": ([i32, d, p, i32, p, p, p], C.c_int),
+            "lbm_ams_run": ([p, p, p, p, p, p, p, p], C.c_int),
+            "ams_probability": ([i32, d, p, i32, p, p, i32, p, p, p], C.c_int),
             "cnn_create": ([i32, i32, i32, u64, p], C.c_int),
             "cnn_destroy": ([p], C.c_int),
             "cnn_param_count": ([p], i64),
@@ -388,18 +388,32 @@ def gktl_probability(k: float, logR_dev, integral_dev, maxima_dev, levels_dev, t
 
 
 def lbm_ams_run(e, t_a: int, window: int, max_iter: int, level: float, eps: float, seed: int, Q_dev,
-                with_kills: bool = False, score_kind: int = 0, refresh_snapshots: bool = False):
-    """returns (iterations, log_weight, levels z_1..z_iterations[, kills per iteration])"""
+                with_kills: bool = False, score_kind: int = 0, refresh_snapshots: bool = False,
+                with_records: bool = False):
+    """returns (iterations, log_weight, levels z_1..z_iterations[, kills per
+    iteration][, killed records (log weights before each kill, event maxima)])"""
     import torch
     prm = lbm_ams_params(t_a, window, max_iter, level, eps, seed, score_kind, int(refresh_snapshots))
     it = C.c_int32()
     lw = C.c_double()
+    n = Q_dev.numel()
     levels = np.zeros(max(max_iter, 1))
     kills = np.zeros(max(max_iter, 1), dtype=np.int32)
+    kmax = np.full(max(max_iter, 1) * n, np.nan) if with_records else None
     _check(lib().lbm_ams_run(e, C.byref(prm), C.byref(it), C.byref(lw), _dev(Q_dev, torch.float64), _host(levels),
-                             _host(kills)))
+                             _host(kills), _host(kmax) if with_records else None))
     out = (it.value, lw.value, levels[:it.value].copy())
-    return out + (kills[:it.value].copy(),) if with_kills else out
+    if with_kills:
+        out = out + (kills[:it.value].copy(),)
+    if with_records:
+        rec_lw, rec_mx, w = [], [], 0.0
+        for j in range(it.value):
+            for i in range(kills[j]):
+                rec_lw.append(w)
+                rec_mx.append(kmax[j * n + i])
+            w += np.log1p(-kills[j] / n)
+        out = out + ((np.array(rec_lw), np.array(rec_mx)),)
+    return out
 
 
 def lbm_drag_autocorrelation(e, t0: int, t1: int, max_lag: int, c_dev):
@@ -420,10 +434,18 @@ def lbm_drag_return_times(e, t0: int, t1: int, levels_dev, gap: int):
     return ev, r
 
 
-def ams_probability(log_weight: float, Q_dev, levels_dev, p_dev, stream=None):
+def ams_probability(log_weight: float, Q_dev, levels_dev, p_dev, records=None, stream=None):
+    """records: None (final ensemble only) or (log weights, event maxima) of the
+    killed trajectories, float64 CUDA tensors of one length"""
     import torch
-    _check(lib().ams_probability(Q_dev.numel(), log_weight, _dev(Q_dev, torch.float64), levels_dev.numel(),
-                                 _dev(levels_dev, torch.float64), _dev(p_dev, torch.float64), _stream(stream)))
+    nr = 0 if records is None else records[0].numel()
+    if records is not None and records[1].numel() != nr:
+        raise TypeError("killed records: log weights and maxima differ in length")
+    rl = None if records is None else _dev(records[0], torch.float64)
+    rm = None if records is None else _dev(records[1], torch.float64)
+    _check(lib().ams_probability(Q_dev.numel(), log_weight, _dev(Q_dev, torch.float64), nr, rl, rm,
+                                 levels_dev.numel(), _dev(levels_dev, torch.float64), _dev(p_dev, torch.float64),
+                                 _stream(stream)))
 
 
 # ---------------------------------------------------------------- learned score

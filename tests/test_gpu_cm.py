@@ -51,6 +51,12 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+def rel_pop(a, b):
+    """largest relative error of any single population (the populations are
+    positive): |f_gpu - f_oracle| <= tol |f_oracle| element by element"""
+    return (np.abs(a - b) / np.abs(b)).max()
+
+
 def ocfg(orc, kw, rates):
     return orc.cfg(kw["nx"], kw["ny"], obstacle=kw.get("obstacle", (0, 0, 0, 0)), tau=kw["tau"],
                    gx=kw.get("gx", 0.0), gy=kw.get("gy", 0.0), collision=1, **rates)
@@ -62,7 +68,7 @@ def test_cm_cfg1_200_steps_match_oracle(L, orc, rates):
         L.lbm_ensemble_step(e.h, 200)
         oc = ocfg(orc, CFG1, rates)
         f_ref, d_ref = orc.run(oc, orc.init(oc, 0, 0, 0.01), 200)
-        assert rel(e.pops(0), f_ref) < POP_TOL
+        assert rel_pop(e.pops(0), f_ref) < POP_TOL
         assert rel(e.drag(0, 200)[0], d_ref) < DRAG_TOL
 
 
@@ -79,7 +85,7 @@ def test_cm_every_fp32_variant_on_ragged_grid(L, orc):
             L.lbm_ensemble_step(e.h, 60)
             d = e.drag(0, 60)
             for c in range(3):
-                assert rel(e.pops(c), refs[c][0]) < POP_TOL, (vec, warps, c)
+                assert rel_pop(e.pops(c), refs[c][0]) < POP_TOL, (vec, warps, c)
                 assert rel(d[c], refs[c][1]) < DRAG_TOL, (vec, warps, c)
         tried += 1
     assert tried >= 3
@@ -141,7 +147,7 @@ def test_cm_noalloc_step_matches_ensemble(L):
     L.lbm_step_noalloc(e.cfg, n, a, b, d, torch.cuda.current_stream())
     torch.cuda.synchronize()
     for c in range(n):
-        assert rel(b[c, :, :, :nx].double().cpu().numpy(), ref[c]) < POP_TOL
+        assert rel_pop(b[c, :, :, :nx].double().cpu().numpy(), ref[c]) < POP_TOL
 
 
 def test_cm_argument_errors(L):

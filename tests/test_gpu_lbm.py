@@ -56,6 +56,12 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+def rel_pop(a, b):
+    """largest relative error of any single population (the populations are
+    positive): |f_gpu - f_oracle| <= tol |f_oracle| element by element"""
+    return (np.abs(a - b) / np.abs(b)).max()
+
+
 def oracle_cfg(orc, kw):
     return orc.cfg(kw["nx"], kw["ny"], obstacle=kw.get("obstacle", (0, 0, 0, 0)), tau=kw.get("tau", 0.6),
                    gx=kw.get("gx", 0.0), gy=kw.get("gy", 0.0))
@@ -81,7 +87,7 @@ def test_cfg1_200_steps_match_oracle(L, orc, seed):
         L.lbm_ensemble_step(e.h, 200)
         oc = oracle_cfg(orc, CFG1)
         f_ref, d_ref = orc.run(oc, orc.init(oc, seed, 0, 0.01), 200)
-        assert rel(e.pops(0), f_ref) < POP_TOL
+        assert rel_pop(e.pops(0), f_ref) < POP_TOL
         assert rel(e.drag(0, 200)[0], d_ref) < DRAG_TOL
 
 
@@ -102,7 +108,7 @@ def test_every_variant_on_ragged_grid(L, orc):
             L.lbm_ensemble_step(e.h, 60)
             d = e.drag(0, 60)
             for c in range(3):
-                assert rel(e.pops(c), refs[c][0]) < POP_TOL, (vec, warps, c)
+                assert rel_pop(e.pops(c), refs[c][0]) < POP_TOL, (vec, warps, c)
                 assert rel(d[c], refs[c][1]) < DRAG_TOL, (vec, warps, c)
         tried += 1
     assert tried >= 3
@@ -166,7 +172,7 @@ def test_no_obstacle_and_obstacle_on_wall(L, orc):
         with Ens(L, 1, seed=4, **kw) as e:
             L.lbm_ensemble_step(e.h, 40)
             f_ref, d_ref = orc.run(oc, orc.init(oc, 4, 0, 0.01), 40)
-            assert rel(e.pops(0), f_ref) < POP_TOL
+            assert rel_pop(e.pops(0), f_ref) < POP_TOL
             if obst[2]:
                 assert rel(e.drag(0, 40)[0], d_ref) < DRAG_TOL
             else:
@@ -179,7 +185,7 @@ def test_minimum_width_channel(L, orc):
     with Ens(L, 1, seed=2, **kw) as e:
         L.lbm_ensemble_step(e.h, 30)
         f_ref, _ = orc.run(oc, orc.init(oc, 2, 0, 0.01), 30)
-        assert rel(e.pops(0), f_ref) < POP_TOL
+        assert rel_pop(e.pops(0), f_ref) < POP_TOL
 
 
 def test_mass_conserved_and_moments(L, orc):
@@ -365,6 +371,36 @@ def test_branch_replays_across_step_variants(L):
         assert np.abs(d[1, 63:] - d[2, 63:]).max() <= 1e-5 * np.abs(d[2]).max()
 
 
+def test_perturbed_branch_matches_oracle(L, orc):
+    """App. B.1's branch with App. D's perturbation against the oracle: the
+    source's state at t_b (the oracle runs the source from its seeded start),
+    perturbed with the bank of states at t = 120 and the weights of counter
+    (4, iter, dst, n), then 150 further steps; the branch's state and its drag
+    after t_b match element by element at the FP32 tolerances, and its drag up
+    to t_b is the source's"""
+    kw = dict(RAGGED, max_steps=300, ckpt_stride=25, n_snapshots=2)
+    oc = oracle_cfg(orc, kw)
+    t_b, seed, it, eps, after = 63, 11, 4, 0.05, 150  # eps above App. D's 0.002 so that it shows
+    with Ens(L, 3, seed=8, **kw) as e:
+        L.lbm_ensemble_step(e.h, 120)
+        L.lbm_ensemble_set_snapshots(e.h, [0, 2])
+        L.lbm_ensemble_branch(e.h, 1, 2, t_b, eps, seed, it)
+        L.lbm_ensemble_step_clones(e.h, after, [1])
+        got = e.pops(1)
+        d = np.zeros((3, t_b + after))
+        L.lbm_ensemble_drag(e.h, 0, t_b + after, d)
+    snaps = np.stack([orc.run(oc, orc.init(oc, 8, c, 0.01), 120)[0] for c in (0, 2)])
+    f_src, d_src = orc.run(oc, orc.init(oc, 8, 2, 0.01), t_b)
+    f_b = orc.perturb(oc, f_src, snaps, orc.perturb_alphas(seed, it, 1, 2), eps)
+    f_ref, d_ref = orc.run(oc, f_b, after)
+    assert rel_pop(got, f_ref) < POP_TOL
+    assert rel(d[1, t_b:], d_ref) < DRAG_TOL
+    assert rel(d[1, :t_b], d_src) < DRAG_TOL
+    # the perturbation is not negligible at these tolerances
+    f_plain, _ = orc.run(oc, f_src, after)
+    assert rel_pop(f_plain, f_ref) > 20 * POP_TOL
+
+
 def test_nonfinite_state_is_reported(L):
     kw = dict(nx=64, ny=16, obstacle=(20, 5, 6, 6), tau=0.6, max_steps=20)
     with Ens(L, 2, **kw) as e:
@@ -412,7 +448,7 @@ def test_ams_workload_full_size_sampled_parity(L, orc):
         oc = oracle_cfg(orc, kw)
         for c in (0, 137, 255):
             f_ref, d_ref = orc.run(oc, orc.init(oc, 21, c, 0.01), 20)
-            assert rel(e.pops(c), f_ref) < POP_TOL
+            assert rel_pop(e.pops(c), f_ref) < POP_TOL
             assert rel(d[c], d_ref) < DRAG_TOL
 
 
@@ -486,5 +522,5 @@ def test_full_size_sampled_parity(L, orc):
         oc = oracle_cfg(orc, kw)
         for c in (0, 63):
             f_ref, d_ref = orc.run(oc, orc.init(oc, 12, c, 0.01), 20)
-            assert rel(e.pops(c), f_ref) < POP_TOL
+            assert rel_pop(e.pops(c), f_ref) < POP_TOL
             assert rel(d[c], d_ref) < DRAG_TOL

@@ -57,6 +57,12 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+def rel_pop(a, b):
+    """largest relative error of any single population (the populations are
+    positive): |f_gpu - f_oracle| <= tol |f_oracle| element by element"""
+    return (np.abs(a - b) / np.abs(b)).max()
+
+
 def ocfg(orc, kw):
     coll = kw.get("collision", "bgk")
     rates = {k: kw[k] for k in ("omega_bulk", "omega_3", "omega_4") if k in kw}
@@ -92,7 +98,7 @@ def test_open_channel_matches_oracle(L, orc, coll):
         d = e.drag(0, 200)
         for c in range(2):
             f_ref, d_ref = orc.run(oc, orc.init(oc, 4, c, 0.01), 200)
-            assert rel(e.pops(c), f_ref) < POP_TOL, c
+            assert rel_pop(e.pops(c), f_ref) < POP_TOL, c
             assert rel(d[c], d_ref) < DRAG_TOL, c
 
 
@@ -110,7 +116,7 @@ def test_every_open_variant_matches_oracle_and_each_other(L, orc):
             got = [e.pops(c) for c in range(2)]
             d = e.drag(0, 60)
         for c in range(2):
-            assert rel(got[c], ref[c][0]) < POP_TOL, (v, c)
+            assert rel_pop(got[c], ref[c][0]) < POP_TOL, (v, c)
             assert rel(d[c], ref[c][1]) < DRAG_TOL, (v, c)
         if first is None:
             first = got
@@ -197,7 +203,7 @@ def test_paper_channel_matches_oracle(L, orc):
     f_ref, d_ref = orc.run(oc, orc.init(oc, 0, 0, 0.0), 100)
     with Ens(L, 1, seed=0, **PAPER) as e:
         L.lbm_ensemble_step(e.h, 100)
-        assert rel(e.pops(0), f_ref) < POP_TOL
+        assert rel_pop(e.pops(0), f_ref) < POP_TOL
         assert rel(e.drag(0, 100)[0], d_ref) < DRAG_TOL
 
 

@@ -107,14 +107,53 @@ def test_gktl_probability_matches_oracle(L, orc):
     assert np.isinf(got[-1]) and got[-1] > 0  # P = 0 above every maximum
 
 
+def test_gktl_probability_with_potential_on_an_oracle_run(L, orc):
+    """App. C.2 with a potential in the exponents: the estimator kernel, given
+    the per-period log R, integrals, window maxima and corrections of an oracle
+    GKTL run on the OU process (k = 0.5, kappa = 1, V = x), equals the
+    oracle's estimator (pinned against brute-force sampling on the CPU)"""
+    o = orc.ou_gktl(1024, 20, 10, 0.05, 0.5, 501, kappa=1.0, full=True)
+    maxima = orc.trailing_mean_max(o["hist"][:, 1:], 40)
+    levels = np.array([0.5, 1.0, 1.25, 1.5, 1.75, 5.0])
+    dev = {k: torch.tensor(v, device="cuda") for k, v in
+           dict(logR=o["log_r"], integ=o["integrals"], maxima=maxima, corr=o["correction"], levels=levels).items()}
+    p, r = zeros(len(levels)), zeros(len(levels))
+    L.gktl_probability(0.5, dev["logR"], dev["integ"], dev["maxima"], dev["levels"], 10.0, 2.0, p, r,
+                       correction_dev=dev["corr"])
+    p_ref = orc.gktl_probability(o["log_z"], 0.5, o["integrals"], maxima, levels, o["correction"])
+    assert np.allclose(p.cpu().numpy(), p_ref, rtol=1e-12, atol=0)
+    assert np.allclose(r.cpu().numpy()[:-1], orc.return_time(p_ref, 10.0, 2.0)[:-1], rtol=1e-12)
+    p_raw = zeros(len(levels))  # without the correction the kernel gives the oracle's uncorrected sum
+    L.gktl_probability(0.5, dev["logR"], dev["integ"], dev["maxima"], dev["levels"], 10.0, 2.0, p_raw)
+    assert np.allclose(p_raw.cpu().numpy(), orc.gktl_probability(o["log_z"], 0.5, o["integrals"], maxima, levels),
+                       rtol=1e-12, atol=0)
+
+
+def test_ams_probability_with_killed_records_on_an_oracle_run(L, orc):
+    """Generalised AMS with a score other than the event (App. B.1): the
+    estimator kernel, given the final maxima and the killed records of an
+    oracle AMS run on the OU process, equals the oracle's estimator"""
+    p_orc, it, lw, mx, (rl, rm) = orc.ou_ams_score(32, 100, 0.05, 5, 10, np.inf, 1.5, 60, 3007)
+    levels = np.array([0.5, 1.0, 1.5, 2.0, 2.5])
+    p = zeros(len(levels))
+    L.ams_probability(lw, torch.tensor(mx, device="cuda"), torch.tensor(levels, device="cuda"), p,
+                      records=(torch.tensor(rl, device="cuda"), torch.tensor(rm, device="cuda")))
+    ref = [orc.ams_probability(lw, mx, a, (rl, rm)) for a in levels]
+    assert np.allclose(p.cpu().numpy(), ref, rtol=1e-13, atol=0)
+    assert abs(p.cpu().numpy()[2] - p_orc) <= 1e-13 * p_orc
+
+
 def test_ams_run_invariants(L, orc):
     n, t_a, window, J = 8, 240, 40, 12
     e, cfg = make(L, n, 21, max_steps=t_a, ckpt_stride=30, n_snapshots=2)
     try:
         L.lbm_ensemble_set_snapshots(e, [0, 1])
         Q = zeros(n)
-        it, lw, levels, kills = L.lbm_ams_run(e, t_a, window, J, float("inf"), 0.002, 13, Q, with_kills=True)
+        it, lw, levels, kills, (rec_lw, rec_mx) = L.lbm_ams_run(e, t_a, window, J, float("inf"), 0.002, 13, Q,
+                                                               with_kills=True, with_records=True)
         assert it == J
+        # with the drag as score a killed trajectory's event maximum is its level
+        assert np.array_equal(rec_mx, np.repeat(levels, kills))
         assert np.all(np.diff(levels) > 0)  # every kill removes the minimum: the level rises
         q = Q.cpu().numpy()
         assert np.all(q > levels[-1])
@@ -131,6 +170,11 @@ def test_ams_run_invariants(L, orc):
         L.ams_probability(lw, Q, lv, p)
         ref = [orc.ams_probability(lw, q, a) for a in lv.cpu().numpy()]
         assert np.allclose(p.cpu().numpy(), ref, rtol=1e-14)
+        # above the last killed level the killed records add nothing
+        L.ams_probability(lw, Q, lv, p, records=(torch.tensor(rec_lw, device="cuda"),
+                                                 torch.tensor(rec_mx, device="cuda")))
+        assert np.allclose(p.cpu().numpy()[1:], ref[1:], rtol=1e-14)
+        assert p.cpu().numpy()[0] > ref[0]  # at the last killed level its trajectories count
     finally:
         L.lbm_ensemble_destroy(e)
 

@@ -94,6 +94,38 @@ def test_ams_with_learned_score(L, model):
         assert np.array_equal(np.asarray(a), np.asarray(b))
 
 
+def test_ams_with_learned_score_records_the_killed_trajectories(L, orc, model):
+    """With the learned score the killed trajectories can hold the event
+    (their drag maximum) though their score was the lowest, so the generalised
+    AMS estimator counts them: the record of each trajectory killed at the last
+    iteration J is the time-averaged drag maximum that a run stopped after J - 1
+    iterations (deterministic) shows for the clones of minimum learned score"""
+    n, C, t_a, J, window = 8, 20, 200, 6, 40
+    out = {}
+    for iters in (J, J - 1):
+        e, cfg = ensemble(L, n, 9, max_steps=t_a, ckpt_stride=C, n_snapshots=2)
+        try:
+            L.lbm_ensemble_attach_score(e, model, F, 100.0, 50.0)
+            L.lbm_ensemble_set_snapshots(e, [0, 1])
+            Q = zeros(n)
+            res = L.lbm_ams_run(e, t_a, window, iters, float("inf"), 0.002, 5, Q, with_kills=True, score_kind=1,
+                                with_records=True)
+            d = np.zeros((n, t_a))
+            L.lbm_ensemble_drag(e, 0, t_a, d)
+            out[iters] = (res, Q.cpu().numpy(), d)
+        finally:
+            L.lbm_ensemble_destroy(e)
+    (it, lw, levels, kills, (rec_lw, rec_mx)), _, _ = out[J]
+    assert it == J and len(rec_mx) == kills.sum()
+    (it1, lw1, _, kills1, (rec_lw1, rec_mx1)), q_learned, drag = out[J - 1]
+    assert np.array_equal(rec_mx[:len(rec_mx1)], rec_mx1) and np.array_equal(rec_lw[:len(rec_lw1)], rec_lw1)
+    killed = np.nonzero(q_learned == q_learned.min())[0]
+    assert len(killed) == kills[-1]
+    ev = orc.trailing_mean_max(drag, window, t_a)
+    assert np.allclose(rec_mx[len(rec_mx1):], ev[killed], rtol=1e-11, atol=1e-14)
+    assert np.allclose(rec_lw[len(rec_lw1):], lw1, rtol=0, atol=1e-15)
+
+
 def test_gktl_with_learned_potential(L, model):
     n, period, periods = 12, 20, 4
     # kappa = 0 with a score attached is the plain run, bit for bit
