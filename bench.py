@@ -569,6 +569,92 @@ def run_precision_report(args):
                       "report": report}))
 
 
+# chaotic small open channel of the long-run comparisons: 129 x 33, square of
+# side 8 at the centre, bars of 4 rows every 8 from x = 8, 32-column sponge to
+# tau = 1, central moments, tau = 0.5015, u_c = 0.08 (drag correlation time
+# about 340 steps; a 1e-6 change of one population grows to the drag's
+# fluctuation size within about 4000 steps)
+CHAOTIC = dict(nx=129, ny=33, obstacle=(60, 12, 8, 8), tau=0.5015, open_x=1, u_in=0.08, grid=(8, 4, 4, 4),
+               sponge_len=32, sponge_tau=1.0)
+
+
+def _chaotic_oracle_drag(job):
+    """one oracle trajectory of the chaotic channel: (seed, clone, steps) -> drag"""
+    import oracle
+    seed, clone, steps = job
+    kw = dict(CHAOTIC)
+    c = oracle.cfg(kw.pop("nx"), kw.pop("ny"), obstacle=kw.pop("obstacle"), collision=1, **kw)
+    return oracle.run(c, oracle.init(c, seed, clone, 0.01), steps)[1]
+
+
+def run_long_run_precision(args):
+    """Long-run drag statistics past the predictability horizon in the chaotic
+    small open channel: shifted FP16 and BF16 storage against FP32 on a large
+    GPU ensemble (default 2048 trajectories; the sampling error of a 2% check),
+    and FP32 against the FP64 oracle on the oracle's 32 trajectories (same seeds;
+    all host cores).  Steps [4000, 8000) of each trajectory; standard errors
+    from the spread of per-trajectory values."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    n = args.clones or 2048
+    steps, t0, seed = 8000, 4000, 21
+    n_orc = 0 if args.no_cpu else 32
+    pool, orc_async = None, None
+    if n_orc:  # spawned before the first GPU call
+        pool = mp.get_context("spawn").Pool(min(len(os.sched_getaffinity(0)), n_orc))
+        orc_async = pool.map_async(_chaotic_oracle_drag, [(seed, c, steps) for c in range(n_orc)])
+    torch.cuda.set_device(0)
+    L.lib()
+    series = {}
+    for st in ("fp32", "fp16", "bf16"):
+        cfg = L.config(**CHAOTIC, collision="cm", storage=st, max_steps=steps, init_amp=0.01)
+        e = L.lbm_ensemble_create(cfg, n, seed, torch.cuda.current_stream())
+        t = time.time()
+        L.lbm_ensemble_step(e, steps)
+        d = np.zeros((n, steps))
+        L.lbm_ensemble_drag(e, 0, steps, d)
+        series[st] = (d[:, t0:], time.time() - t)
+        L.lbm_ensemble_destroy(e)
+
+    def ks(a, b):
+        a, b = np.sort(a.ravel()), np.sort(b.ravel())
+        x = np.concatenate([a, b])
+        return float(np.abs(np.searchsorted(a, x, side="right") / a.size
+                            - np.searchsorted(b, x, side="right") / b.size).max())
+
+    def compare(d, ref):
+        out = {}
+        for name, stat in (("mean", np.mean), ("std", np.std)):
+            pa, pb = stat(d, axis=1), stat(ref, axis=1)
+            se = float(np.sqrt(pa.var(ddof=1) / pa.size + pb.var(ddof=1) / pb.size))
+            out[name] = float(stat(d))
+            out[f"{name}_rel_dev"] = float((stat(d) - stat(ref)) / abs(stat(ref)))
+            out[f"{name}_rel_se"] = se / abs(float(stat(ref)))
+        out["ks"] = ks(d, ref)
+        for q in (0.99, 0.999):
+            out[f"exceed_q{q}"] = float((d > np.quantile(ref, q)).mean())
+        return out
+
+    ref = series["fp32"][0]
+    report = {st: dict(compare(d, ref), seconds=round(sec, 3)) for st, (d, sec) in series.items()}
+    if n_orc:
+        o = np.stack(orc_async.get())[:, t0:]
+        pool.close()
+        half = np.random.default_rng(0).permutation(n_orc)
+        report["fp32_vs_fp64_oracle"] = dict(
+            compare(ref[:n_orc], o), trajectories=n_orc,
+            ks_null_two_oracle_halves=ks(o[half[:n_orc // 2]], o[half[n_orc // 2:]]))
+    print(json.dumps({"metric": "long-run drag statistics of the storage formats", "trajectories": n,
+                      "steps": steps, "window": [t0, steps],
+                      "config": {"workload": "chaotic open channel 129x33, square R=8, bars R/2 every R, sponge 32, "
+                                             "central moments, tau=0.5015, u_c=0.08"},
+                      "report": report}))
+
+
 # ---------------------------------------------------------------- time to return time
 def run_return_time(args):
     """Wall time for a return-time estimate of extreme time-averaged drag at 20%
@@ -1206,7 +1292,7 @@ def main():
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
     ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run", "ams-estimate",
-                                              "perturb-check"])
+                                              "perturb-check", "long-run-precision"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--collision", default=None, choices=["bgk", "cm"],
                     help="BGK or the central-moment collision (default: central moments for the open "
@@ -1229,6 +1315,8 @@ def main():
         run_return_time(args)
     elif args.workload == "precision-report":
         run_precision_report(args)
+    elif args.workload == "long-run-precision":
+        run_long_run_precision(args)
     elif args.workload == "ams-branch":
         run_ams_branch(args)
     elif args.workload == "ams-estimate":
