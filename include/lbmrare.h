@@ -423,6 +423,14 @@ int cnn_set_conv_path(cnn_model* m, int32_t path);
  * records it and returns; the context stays usable), else LBM_OK.  cnn_fit
  * checks the same flag after every minibatch. */
 int cnn_status(cnn_model* m, void* stream);
+/* Which hidden-layer kernels a step of this batch size runs: *conv_tc = 1 if
+ * the 32 -> 32 forward and data-gradient convolutions run on the tcgen05
+ * kernels (else mma.sync), *wgrad_tc = 1 likewise for their weight gradient.
+ * The tensor-core path needs a width that is a multiple of 128, or a divisor
+ * of 128 for the forward kernels; a width of exactly 128 with more than 148
+ * output rows (batch x height) stays on mma.sync, because a GPU fault of
+ * unknown cause was once recorded at 32 x 128 with batch 64.  No GPU work. */
+int cnn_tensor_core_paths(const cnn_model* m, int32_t batch, int32_t* conv_tc, int32_t* wgrad_tc);
 /* predictions for n inputs (any n; evaluated in batches of max_batch) */
 int cnn_predict(cnn_model* m, const void* x_dev, int64_t n, float* pred_dev, void* stream);
 /* epochs of minibatch Adam over a data set x_dev [n][H][W][8], y_dev[n] (FP32):

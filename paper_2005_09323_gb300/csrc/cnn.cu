@@ -836,6 +836,15 @@ int cnn_set_conv_path(cnn_model* m, int32_t path)
     return LBM_OK;
 }
 
+int cnn_tensor_core_paths(const cnn_model* m, int32_t batch, int32_t* conv_tc, int32_t* wgrad_tc)
+{
+    if (int rc = cnn_check(m, batch)) return rc;
+    if (!conv_tc || !wgrad_tc) return fail(LBM_ERR_ARG, "cnn_tensor_core_paths: null output");
+    *conv_tc = use_tc(m, batch) ? 1 : 0;
+    *wgrad_tc = (m->conv_path == 0 && conv3x3_wgrad_tc_supported(batch, m->H, m->W)) ? 1 : 0;
+    return LBM_OK;
+}
+
 int cnn_status(cnn_model* m, void* stream)
 {
     if (!m) return fail(LBM_ERR_ARG, "cnn_status: null model");

@@ -27,7 +27,7 @@ EXPORTS = [
     "lbm_ensemble_branch", "lbm_ensemble_moments", "lbm_ensemble_get_populations",
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
     "lbm_step_variant_info", "lbm_step_variant_count", "lbm_ensemble_set_timing", "lbm_ensemble_kernel_time",
-    "lbm_ensemble_set_graphs", "lbm_step_variant_kind", "cnn_set_conv_path", "cnn_status",
+    "lbm_ensemble_set_graphs", "lbm_step_variant_kind", "cnn_set_conv_path", "cnn_status", "cnn_tensor_core_paths",
     "lbm_drag_autocorrelation", "lbm_drag_return_times",
     "gktl_weights", "gktl_select", "ams_select", "lbm_step_noalloc",
     "lbm_gktl_run", "gktl_probability", "lbm_ams_run", "ams_probability",
@@ -157,6 +157,7 @@ def lib():
             "lbm_ensemble_set_observables": ([p, i32], C.c_int),
             "lbm_ensemble_observables": ([p, i32, i32, p, i32], C.c_int),
             "cnn_status": ([p, p], C.c_int),
+            "cnn_tensor_core_paths": ([p, i32, p, p], C.c_int),
             "cnn_predict": ([p, p, i64, p, p], C.c_int),
             "cnn_fit": ([p, p, p, i64, i32, i32, C.c_float, u64, p, p], C.c_int),
             "lbm_ensemble_attach_score": ([p, p, i32, C.c_float, C.c_float], C.c_int),
@@ -563,6 +564,13 @@ def cnn_set_conv_path(m, path: int):
 
 def cnn_status(m, stream=None):
     _check(lib().cnn_status(m, _stream(stream)))
+
+
+def cnn_tensor_core_paths(m, batch: int):
+    """(hidden convolutions on tcgen05, their weight gradient on tcgen05) for a batch"""
+    a, b = C.c_int32(), C.c_int32()
+    _check(lib().cnn_tensor_core_paths(m, batch, C.byref(a), C.byref(b)))
+    return bool(a.value), bool(b.value)
 
 
 def cnn_predict(m, x_dev, pred_dev, stream=None):

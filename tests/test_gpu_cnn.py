@@ -125,6 +125,50 @@ def test_tensor_core_gradient_at_full_size_matches_oracle(L, orc):
         for l in range(4):
             sl = slice(off[l], off[l + 1])
             assert np.linalg.norm(g[sl] - ref16[sl]) < 1.5e-2 * np.linalg.norm(ref16[sl]), l
+        check_taps_and_biases(g, ref16)
+    finally:
+        L.cnn_destroy(m)
+
+
+def check_taps_and_biases(g, ref, tol=3e-2):
+    """each tap (ky, kx) of each layer's weight gradient and each layer's bias
+    gradient within tol in relative L2 norm: an error confined to one tap or
+    to the bias column cannot hide under the layer's norm"""
+    from oracle import cnn
+    off, _ = cnn.offsets()
+    for l, (cin, kp) in enumerate(zip(cnn.CIN, cnn.KPAD)):
+        G = g[off[l]:off[l + 1]].reshape(32, kp)
+        R = ref[off[l]:off[l + 1]].reshape(32, kp)
+        for tap in range(9):
+            a, b = G[:, tap * cin:(tap + 1) * cin], R[:, tap * cin:(tap + 1) * cin]
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), (l, tap)
+        assert np.linalg.norm(G[:, 9 * cin] - R[:, 9 * cin]) <= tol * np.linalg.norm(R[:, 9 * cin]), (l, "bias")
+        assert np.all(G[:, 9 * cin + 1:] == 0.0), (l, "padding")
+
+
+def test_w128_with_several_rows_per_cta_runs_on_mma_sync(L, orc):
+    """A 128-pixel-wide input with more output rows than one per CTA (the
+    shape of the one recorded GPU fault: 32 x 128, here batch 8) is routed to
+    the mma.sync kernels; one output row per CTA (batch 4) keeps tcgen05.  The
+    routed gradient matches the oracle, per layer, per tap and per bias"""
+    from oracle import cnn
+    m = L.cnn_create(32, 128, 8, 5)
+    try:
+        assert L.cnn_tensor_core_paths(m, 8) == (False, False)
+        assert L.cnn_tensor_core_paths(m, 4) == (True, True)
+        xt, x = inputs(8, 32, 128, 12)
+        y = np.linspace(-0.6, 0.9, 8).astype(np.float32)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        L.cnn_gradient(m, xt, torch.tensor(y, device="cuda"), loss)
+        L.cnn_status(m)
+        g = L.cnn_get_gradient(m).astype(np.float64)
+        p = conv_layers_bf16(L.cnn_get_params(m))
+        _, ref16 = cnn.loss_and_grad(p, x, y.astype(np.float64), store=bf16_round)
+        off, _ = cnn.offsets()
+        for l in range(4):
+            sl = slice(off[l], off[l + 1])
+            assert np.linalg.norm(g[sl] - ref16[sl]) < 1.5e-2 * np.linalg.norm(ref16[sl]), l
+        check_taps_and_biases(g, ref16)
     finally:
         L.cnn_destroy(m)
 
