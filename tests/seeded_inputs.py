@@ -42,3 +42,22 @@ def channel(nx: int, ny: int, side: int, cx: int | None = None):
     if side <= 0:
         return (0, 0, 0, 0)
     return (cx - side // 2, ny // 2 - side // 2, side, side)
+
+
+def cnn_params(seed: int) -> np.ndarray:
+    """A parameter vector of the learned-score network in its documented flat
+    layout (FP32 values): for conv layer l (input channels 8, then 32) a
+    [32][80] or [32][304] block, 9 * C_in tap weights drawn uniformly within
+    the He bound sqrt(6 / (9 * C_in)), then a bias drawn in [-0.1, 0.1], then
+    zero padding; then 32 head weights within 1/sqrt(32) and a zero head bias."""
+    g = rng(seed)
+    out = []
+    for cin, kpad in ((8, 80), (32, 304), (32, 304), (32, 304)):
+        block = np.zeros((32, kpad))
+        a = np.sqrt(6.0 / (9 * cin))
+        block[:, :9 * cin] = g.uniform(-a, a, (32, 9 * cin))
+        block[:, 9 * cin] = g.uniform(-0.1, 0.1, 32)
+        out.append(block.ravel())
+    out.append(g.uniform(-1, 1, 32) / np.sqrt(32.0))
+    out.append(np.zeros(1))
+    return np.concatenate(out).astype(np.float32)

@@ -9,6 +9,8 @@ import numpy as np
 import pytest
 import torch
 
+from tests import seeded_inputs as si
+
 pytestmark = pytest.mark.gpu
 
 
@@ -22,6 +24,13 @@ def L():
 
 def bf16_round(a):
     return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def seeded(L, m, seed):
+    """load seeded parameters into the model; returns them (FP64) for the oracle"""
+    p = si.cnn_params(seed)
+    L.cnn_set_params(m, p)
+    return p.astype(np.float64)
 
 
 def conv_layers_bf16(p):
@@ -47,6 +56,7 @@ def model(L, request):
     (128-pixel blocks of 4 rows x 32) or on the mma.sync path"""
     m = L.cnn_create(16, 32, 8, 42)
     L.cnn_set_conv_path(m, request.param)
+    m.seeded_params = seeded(L, m, 42)
     yield m
     L.cnn_status(m)
     L.cnn_destroy(m)
@@ -92,11 +102,11 @@ def test_tensor_core_forward_at_full_size_matches_oracle(L, orc):
     from oracle import cnn
     m = L.cnn_create(64, 256, 2, 5)
     try:
+        p = conv_layers_bf16(seeded(L, m, 5))
         xt, x = inputs(2, 64, 256, 9)
         pred = torch.zeros(2, dtype=torch.float32, device="cuda")
         L.cnn_forward(m, xt, pred)
         L.cnn_status(m)
-        p = conv_layers_bf16(L.cnn_get_params(m))
         ref, _ = cnn.forward(p, x, store=bf16_round)
         got = pred.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-2 * (np.abs(ref).max() + 1e-3), (got, ref)
@@ -113,13 +123,13 @@ def test_tensor_core_gradient_at_full_size_matches_oracle(L, orc):
     from oracle import cnn
     m = L.cnn_create(64, 256, 2, 5)
     try:
+        p = conv_layers_bf16(seeded(L, m, 6))
         xt, x = inputs(2, 64, 256, 4)
         y = np.array([0.7, -0.4], dtype=np.float32)
         loss = torch.zeros(1, dtype=torch.float32, device="cuda")
         L.cnn_gradient(m, xt, torch.tensor(y, device="cuda"), loss)
         L.cnn_status(m)
         g = L.cnn_get_gradient(m).astype(np.float64)
-        p = conv_layers_bf16(L.cnn_get_params(m))
         _, ref16 = cnn.loss_and_grad(p, x, y.astype(np.float64), store=bf16_round)
         off, _ = cnn.offsets()
         for l in range(4):
@@ -156,13 +166,13 @@ def test_w128_with_several_rows_per_cta_runs_on_mma_sync(L, orc):
     try:
         assert L.cnn_tensor_core_paths(m, 8) == (False, False)
         assert L.cnn_tensor_core_paths(m, 4) == (True, True)
+        p = conv_layers_bf16(seeded(L, m, 7))
         xt, x = inputs(8, 32, 128, 12)
         y = np.linspace(-0.6, 0.9, 8).astype(np.float32)
         loss = torch.zeros(1, dtype=torch.float32, device="cuda")
         L.cnn_gradient(m, xt, torch.tensor(y, device="cuda"), loss)
         L.cnn_status(m)
         g = L.cnn_get_gradient(m).astype(np.float64)
-        p = conv_layers_bf16(L.cnn_get_params(m))
         _, ref16 = cnn.loss_and_grad(p, x, y.astype(np.float64), store=bf16_round)
         off, _ = cnn.offsets()
         for l in range(4):
@@ -178,7 +188,7 @@ def test_forward_matches_oracle(L, orc, model):
     xt, x = inputs(6, 16, 32, 1)
     pred = torch.zeros(6, dtype=torch.float32, device="cuda")
     L.cnn_forward(model, xt, pred)
-    p = conv_layers_bf16(L.cnn_get_params(model))
+    p = conv_layers_bf16(model.seeded_params)
     ref, _ = cnn.forward(p, x)
     got = pred.cpu().numpy()
     scale = np.abs(ref).max() + np.abs(ref - ref.mean()).max()
@@ -199,7 +209,7 @@ def test_gradient_matches_oracle(L, orc, model):
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     L.cnn_gradient(model, xt, torch.tensor(y, device="cuda"), loss)
     g = L.cnn_get_gradient(model).astype(np.float64)
-    p = conv_layers_bf16(L.cnn_get_params(model))
+    p = conv_layers_bf16(model.seeded_params)
     ref_loss, ref = cnn.loss_and_grad(p, x, y.astype(np.float64))
     _, ref16 = cnn.loss_and_grad(p, x, y.astype(np.float64), store=bf16_round)
     assert abs(loss.item() - ref_loss) <= 2e-2 * ref_loss
@@ -218,7 +228,7 @@ def test_adam_step_matches_oracle(L, model):
     from oracle import cnn
     xt, _ = inputs(4, 16, 32, 3)
     y = torch.tensor([0.5, 0.0, -0.5, 1.0], device="cuda")
-    p0 = L.cnn_get_params(model).astype(np.float64)
+    p0 = model.seeded_params
     L.cnn_gradient(model, xt, y)
     g = L.cnn_get_gradient(model).astype(np.float64)
     L.cnn_adam_step(model, 1e-3)
@@ -258,7 +268,7 @@ def test_fields_match_oracle(L, orc, nx, ny, factor):
         L.lbm_ensemble_fields(e, [2, 0], factor, 1000.0, 50.0, dst, nx, ny)
         oc = orc.cfg(nx, ny, obstacle=(30, 12, 8, 8), tau=0.6, gx=2e-5)
         for i, c in enumerate([2, 0]):
-            f = L.lbm_ensemble_get_populations(e, c, nx, ny)
+            f, _ = orc.run(oc, orc.init(oc, 5, c, 0.01), 15)  # the oracle's own state of clone c
             ref = cnn.fields(oc, f, factor, 1000.0, 50.0)
             got = dst[i].float().cpu().numpy()
             for ch in range(3):
@@ -280,7 +290,7 @@ def test_cnn_argument_errors(L, model):
                       torch.zeros(2, device="cuda"))
     with pytest.raises(L.LbmError):
         L.cnn_set_conv_path(model, 2)
-    bad = L.cnn_get_params(model)
+    bad = si.cnn_params(1)
     bad[5] = np.nan
     with pytest.raises(L.LbmError):
         L.cnn_set_params(model, bad)

@@ -6,6 +6,8 @@ import numpy as np
 import pytest
 import torch
 
+from tests import seeded_inputs as si
+
 pytestmark = pytest.mark.gpu
 
 NX, NY, F = 128, 32, 4
@@ -165,6 +167,65 @@ def test_gktl_with_learned_potential(L, model):
         assert np.all(np.isfinite(logR.cpu().numpy()))
     finally:
         L.lbm_ensemble_destroy(e)
+
+
+def test_gktl_with_learned_potential_matches_oracle(L, orc):
+    """App. C.1 with the learned potential against an oracle composition of the
+    same steps: the oracle runs every clone (FP64 LBM), scores each state with
+    the FP64 network on its own block means (activations rounded to BF16 as the
+    GPU stores them), adds kappa (V(t_i) - V(t_{i-1})) to k sum D, weights,
+    resamples, and carries V(t_i) and the ancestor's V(0) along the
+    genealogy.  Seeded network parameters on both sides; eps = 0.  The
+    parents agree exactly, log R and the correction kappa (V(T_a) - V(0)) to
+    the network's BF16 precision."""
+    from oracle import cnn
+
+    def bf16_round(a):
+        return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+    n, period, periods, k, kappa, sel_seed, seed = 6, 20, 3, 200.0, 0.7, 4, 2
+    m = L.cnn_create(NY // F, NX // F, 16, 3)
+    p = si.cnn_params(31)
+    L.cnn_set_params(m, p)
+    pq = p.astype(np.float64)
+    off, _ = cnn.offsets()
+    pq[:off[4]] = bf16_round(pq[:off[4]])  # the GPU multiplies BF16 copies of the conv weights
+    e, cfg = ensemble(L, n, seed, max_steps=period * periods)
+    try:
+        L.lbm_ensemble_attach_score(e, m, F, 100.0, 50.0)
+        logR, parent, corr = zeros(periods), zeros(periods * n, torch.int32), zeros(n)
+        L.lbm_gktl_run(e, period, periods, k, 0.0, sel_seed, 0, logR, parent, kappa=kappa, correction_dev=corr)
+        got_logR, got_parent, got_corr = logR.cpu().numpy(), parent.cpu().numpy().reshape(periods, n), corr.cpu().numpy()
+    finally:
+        L.lbm_ensemble_destroy(e)
+        L.cnn_destroy(m)
+    oc = orc.cfg(NX, NY, obstacle=KW["obstacle"], tau=KW["tau"], gx=KW["gx"])
+
+    def V(f):
+        x = bf16_round(cnn.fields(oc, f, F, 100.0, 50.0))[None]
+        return float(cnn.forward(pq, x, store=bf16_round)[0][0])
+    f = [orc.init(oc, seed, c, 0.01) for c in range(n)]
+    v0 = np.array([V(fc) for fc in f])
+    vprev = v0.copy()
+    ref_logR, ref_parent, v_scale = [], [], np.abs(v0).max()
+    for i in range(periods):
+        runs = [orc.run(oc, fc, period) for fc in f]
+        f = [r[0] for r in runs]
+        vnow = np.array([V(fc) for fc in f])
+        v_scale = max(v_scale, np.abs(vnow).max())
+        s_ = np.array([k * r[1].sum() for r in runs]) + kappa * (vnow - vprev)
+        W, lr = orc.gktl_weights(s_)
+        par = orc.gktl_select(W, sel_seed, i)
+        ref_logR.append(lr)
+        ref_parent.append(par)
+        f = [f[q].copy() for q in par]
+        v0, vprev = v0[par], vnow[par]
+    ref_corr = kappa * (vprev - v0)
+    assert np.array_equal(got_parent, np.array(ref_parent))
+    assert (got_parent != np.arange(n)).any()  # the selection cloned
+    tol = 2e-2 * kappa * v_scale  # the network's BF16 precision, carried into s
+    assert np.abs(got_logR - np.array(ref_logR)).max() <= tol
+    assert np.abs(got_corr - ref_corr).max() <= tol
 
 
 def test_dataset_labels_are_future_drag_means(L):
