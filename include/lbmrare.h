@@ -146,6 +146,13 @@ int lbm_ensemble_time(lbm_ensemble* e, int32_t* t);
  * LBM_ERR_NONFINITE (a recorded drag value was not finite). */
 int lbm_ensemble_drag(lbm_ensemble* e, int32_t t0, int32_t t1, double* dst, int32_t dst_on_device);
 
+/* Overwrite the drag history D(t), t0 < t <= t1, of every clone with
+ * src[N][t1-t0] (host, FP64, finite; t1 at most the latest clone time), for
+ * the statistics, window sums, scores and estimators that read it: a run
+ * restored from saved state, or a given series to evaluate them on.  The
+ * populations are untouched.  Waits.  Errors: LBM_ERR_ARG. */
+int lbm_ensemble_set_drag(lbm_ensemble* e, int32_t t0, int32_t t1, const double* src);
+
 /* GKTL exponent of eq. (Weight): out_dev[n] = k * sum_{t0 < t <= t1} D_n(t)
  * (dt = one lattice step), FP64, fixed summation order. */
 int lbm_ensemble_window_sum(lbm_ensemble* e, int32_t t0, int32_t t1, double k, double* out_dev);

@@ -999,6 +999,21 @@ int lbm_ensemble_drag(lbm_ensemble* e, int32_t t0, int32_t t1, double* dst, int3
     return LBM_OK;
 }
 
+int lbm_ensemble_set_drag(lbm_ensemble* e, int32_t t0, int32_t t1, const double* src)
+{
+    if (!e || !src) return fail(LBM_ERR_ARG, "null argument");
+    const int32_t tmax = *std::max_element(e->t_host.begin(), e->t_host.end());
+    if (t0 < 0 || t1 < t0 || t1 > tmax) return fail(LBM_ERR_ARG, "drag window outside the recorded history");
+    const int32_t w = t1 - t0;
+    for (int64_t i = 0; i < (int64_t)w * e->n; ++i)
+        if (!std::isfinite(src[i])) return fail(LBM_ERR_ARG, "drag values must be finite");
+    if (w == 0) return LBM_OK;
+    LBM_CUDA(cudaMemcpy2DAsync(e->drag + t0, sizeof(double) * e->cfg.max_steps, src, sizeof(double) * w,
+                               sizeof(double) * w, e->n, cudaMemcpyHostToDevice, e->stream));
+    LBM_CUDA(cudaStreamSynchronize(e->stream));
+    return LBM_OK;
+}
+
 int lbm_ensemble_window_sum(lbm_ensemble* e, int32_t t0, int32_t t1, double k, double* out_dev)
 {
     if (!e || !out_dev) return fail(LBM_ERR_ARG, "null argument");

@@ -22,7 +22,7 @@ STORAGE_NAMES = tuple(STORAGE)
 
 EXPORTS = [
     "lbm_last_error", "lbm_launch_count", "lbm_ensemble_create", "lbm_ensemble_destroy", "lbm_ensemble_step",
-    "lbm_ensemble_step_clones", "lbm_ensemble_time", "lbm_ensemble_drag", "lbm_ensemble_window_sum",
+    "lbm_ensemble_step_clones", "lbm_ensemble_time", "lbm_ensemble_drag", "lbm_ensemble_window_sum", "lbm_ensemble_set_drag",
     "lbm_ensemble_scores", "lbm_ensemble_first_crossing", "lbm_ensemble_set_snapshots", "lbm_ensemble_clone",
     "lbm_ensemble_branch", "lbm_ensemble_moments", "lbm_ensemble_get_populations",
     "lbm_ensemble_set_populations", "lbm_ensemble_autotune", "lbm_ensemble_set_variant",
@@ -114,6 +114,7 @@ def lib():
             "lbm_ensemble_time": ([p, p], C.c_int),
             "lbm_ensemble_drag": ([p, i32, i32, p, i32], C.c_int),
             "lbm_ensemble_window_sum": ([p, i32, i32, d, p], C.c_int),
+            "lbm_ensemble_set_drag": ([p, i32, i32, p], C.c_int),
             "lbm_ensemble_scores": ([p, i32, i32, i32, p], C.c_int),
             "lbm_ensemble_first_crossing": ([p, i32, d, p], C.c_int),
             "lbm_ensemble_set_snapshots": ([p, i32, p], C.c_int),
@@ -265,6 +266,12 @@ def lbm_ensemble_drag(e, t0: int, t1: int, dst):
         import torch
         _check(lib().lbm_ensemble_drag(e, t0, t1, _dev(dst, torch.float64), 1))
     return dst
+
+
+def lbm_ensemble_set_drag(e, t0: int, t1: int, src: np.ndarray):
+    """overwrite the drag history of steps t0 < t <= t1 with src [N, t1 - t0] (waits)"""
+    a = np.ascontiguousarray(src, dtype=np.float64)
+    _check(lib().lbm_ensemble_set_drag(e, t0, t1, _host(a)))
 
 
 def lbm_ensemble_window_sum(e, t0: int, t1: int, k: float, out_dev):

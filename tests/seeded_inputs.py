@@ -61,3 +61,17 @@ def cnn_params(seed: int) -> np.ndarray:
     out.append(g.uniform(-1, 1, 32) / np.sqrt(32.0))
     out.append(np.zeros(1))
     return np.concatenate(out).astype(np.float32)
+
+
+def drag_series(n: int, steps: int, seed: int, mean: float = 1e-3, sd: float = 2e-3, rho: float = 0.9) -> np.ndarray:
+    """n independent synthetic drag series [n, steps]: a stationary Gaussian
+    AR(1) sequence with the given mean, standard deviation and lag-1
+    correlation (the structure the statistics read: fluctuations, a
+    correlation time, excursions above levels)"""
+    g = rng(seed)
+    x = np.zeros((n, steps))
+    x[:, 0] = g.normal(0.0, 1.0, n)
+    e = g.normal(0.0, np.sqrt(1.0 - rho * rho), (n, steps))
+    for t in range(1, steps):
+        x[:, t] = rho * x[:, t - 1] + e[:, t]
+    return mean + sd * x

@@ -1,10 +1,13 @@
 """Direct-sampling statistics on the GPU (Sec. 3) against the oracle on the
-same drag series: the pooled autocorrelation and correlation time (FP64 sums
-in another order: 1e-10 relative) and the waiting-time return times (event
-counts are integers: exact)."""
+same drag series (a seeded synthetic series written into the ensemble's
+history, so that both sides read one input): the pooled autocorrelation and
+correlation time (FP64 sums in another order: 1e-10 relative) and the
+waiting-time return times (event counts are integers: exact)."""
 import numpy as np
 import pytest
 import torch
+
+from tests import seeded_inputs as si
 
 pytestmark = pytest.mark.gpu
 
@@ -25,8 +28,11 @@ def run(L):
     cfg = L.config(**KW)
     e = L.lbm_ensemble_create(cfg, n, 4, torch.cuda.current_stream())
     L.lbm_ensemble_step(e, steps)
-    d = np.zeros((n, steps))
-    L.lbm_ensemble_drag(e, 0, steps, d)
+    d = si.drag_series(n, steps, 4, rho=0.95)
+    L.lbm_ensemble_set_drag(e, 0, steps, d)
+    back = np.zeros((n, steps))
+    L.lbm_ensemble_drag(e, 0, steps, back)
+    assert np.array_equal(back, d)
     yield e, d
     L.lbm_ensemble_destroy(e)
 

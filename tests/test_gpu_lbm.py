@@ -207,7 +207,10 @@ def test_window_sum_and_scores_match_oracle(L, orc):
     kw = dict(RAGGED, max_steps=300)
     with Ens(L, 4, seed=3, **kw) as e:
         L.lbm_ensemble_step(e.h, 300)
-        d = e.drag(0, 300)
+        d = si.drag_series(4, 300, 11)  # one seeded series for both sides
+        L.lbm_ensemble_set_drag(e.h, 0, 300, d)
+        with pytest.raises(L.LbmError):  # beyond the clones' time
+            L.lbm_ensemble_set_drag(e.h, 0, 301, np.zeros((4, 301)))
         out = torch.zeros(4, dtype=torch.float64, device="cuda")
         L.lbm_ensemble_window_sum(e.h, 100, 250, 3.5, out)
         ref = orc.window_sum(d, 100, 250, 3.5)
@@ -279,16 +282,18 @@ def test_clone_exact_copy_and_perturbation(L, orc):
         assert np.array_equal(e.pops(4), before[4])
         h2 = e.drag(0, 20)
         assert np.array_equal(h2[1], hist[0]) and np.array_equal(h2[3], hist[2])
-        # App. D perturbation with a snapshot bank of three states
+        # App. D perturbation with a snapshot bank of three states; the oracle
+        # perturbs its own states of the same clones at step 20
         L.lbm_ensemble_set_snapshots(e.h, [4, 2, 0])
-        snaps = np.stack([before[4], before[2], before[0]])
+        at20 = {c: orc.run(oc, orc.init(oc, 2, c, 0.01), 20)[0] for c in (0, 2, 4)}
+        snaps = np.stack([at20[4], at20[2], at20[0]])
         parent = torch.tensor([0, 4, 2, 3, 4], dtype=torch.int32, device="cuda")
         L.lbm_ensemble_clone(e.h, parent, 0.002, 77, 5)
         alpha = orc.perturb_alphas(77, 5, 1, 3)
-        ref = orc.perturb(oc, before[4], snaps, alpha, 0.002)
+        ref = orc.perturb(oc, at20[4], snaps, alpha, 0.002)
         got = e.pops(1)
         assert rel(got, ref) < 1e-6
-        m_ref, _, _ = orc.moments(oc, before[4])
+        m_ref, _, _ = orc.moments(oc, at20[4])
         m_got, _, _ = orc.moments(oc, got)
         assert abs(m_got - m_ref) / m_ref < 1e-6
         assert np.array_equal(e.pops(3), before[2])  # kept its own slot (a copy of 2 since the first call)
@@ -316,15 +321,16 @@ def test_snapshot_bank_from_checkpoints(L, orc):
     kw = dict(RAGGED, max_steps=100, ckpt_stride=20, n_snapshots=2)
     oc = oracle_cfg(orc, kw)
     with Ens(L, 4, seed=3, **kw) as e:
-        L.lbm_ensemble_step(e.h, 40)
-        at40 = [e.pops(c) for c in range(4)]
-        L.lbm_ensemble_step(e.h, 25)
+        L.lbm_ensemble_step(e.h, 65)
         L.lbm_ensemble_set_snapshots_from_checkpoint(e.h, [3, 1], 2)
         before = e.pops(2)
         parent = torch.tensor([0, 1, 0, 3], dtype=torch.int32, device="cuda")
         L.lbm_ensemble_clone(e.h, parent, 0.002, 5, 9)
         alpha = orc.perturb_alphas(5, 9, 2, 2)
-        ref = orc.perturb(oc, e.pops(0), np.stack([at40[3], at40[1]]), alpha, 0.002)
+        # the oracle's own states: the bank at step 40, the parent at step 65
+        at40 = {c: orc.run(oc, orc.init(oc, 3, c, 0.01), 40)[0] for c in (1, 3)}
+        parent0 = orc.run(oc, orc.init(oc, 3, 0, 0.01), 65)[0]
+        ref = orc.perturb(oc, parent0, np.stack([at40[3], at40[1]]), alpha, 0.002)
         assert rel(e.pops(2), ref) < 1e-6
         assert not np.array_equal(e.pops(2), before)
         with pytest.raises(L.LbmError):

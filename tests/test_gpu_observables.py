@@ -129,16 +129,17 @@ def test_perturb_in_place_matches_oracle(L, orc, kw):
         L.lbm_ensemble_step(e.h, 20)
         L.lbm_ensemble_set_snapshots(e.h, [3, 0, 2])
         before = [e.pops(c) for c in range(n)]
-        snaps = np.stack([before[3], before[0], before[2]])
+        at20 = [orc.run(oc, orc.init(oc, 7, c, kw["init_amp"]), 20)[0] for c in range(n)]  # the oracle's own states
+        snaps = np.stack([at20[3], at20[0], at20[2]])
         L.lbm_ensemble_perturb(e.h, [1, 3], 0.002, 99, 4)
         for c in (0, 2):
             assert np.array_equal(e.pops(c), before[c])
         for c in (1, 3):
-            ref = orc.perturb(oc, before[c], snaps, orc.perturb_alphas(99, 4, c, 3), 0.002)
+            ref = orc.perturb(oc, at20[c], snaps, orc.perturb_alphas(99, 4, c, 3), 0.002)
             got = e.pops(c)
             assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-6
             assert np.abs(got - before[c]).max() > 1e-6
-            m_ref, _, _ = orc.moments(oc, before[c])
+            m_ref, _, _ = orc.moments(oc, at20[c])
             m_got, _, _ = orc.moments(oc, got)
             assert abs(m_got - m_ref) / m_ref < 1e-6
         L.lbm_ensemble_perturb(e.h, [0], 0.0, 1, 1)  # eps = 0: nothing
