@@ -107,7 +107,7 @@ struct lbm_ensemble {
     double* mass_dev;         // [N]
     float* om_col;            // open channel: [nx] relaxation rate of each column
     float* inlet_g;           // open channel: [9][ny] inlet populations minus w_q
-    float* open_u;            // open channel: [N][4][ny] velocities of columns nx-2, nx-3
+    float* open_u;            // open channel: [2][N][4][ny] velocities of columns nx-2, nx-3, per step parity
     double* scores;           // [N][max_steps] trailing means
     int32_t score_window, score_t_begin, score_t_end;  // arguments of the last lbm_ensemble_scores
     int32_t* fields_list_dev; // clone list of field extractions

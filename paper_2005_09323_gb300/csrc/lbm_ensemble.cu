@@ -492,7 +492,12 @@ int variant_for(const lbm_ensemble* e, int n_list)
     return (int64_t)n_list * e->cfg.nx * e->cfg.ny <= kSmallSites ? e->variant_small : e->variant;
 }
 
-StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_list, int vec, int step, int kind = 0)
+// parameters of step `step` (0-based) of a chunk of `chunk` steps (chunk 0: a
+// single step); an open channel's chunk writes its outlet column after the last
+// step only, and the steps after the first pull from the outlet of the
+// previous step's velocities
+StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_list, int vec, int step, int kind = 0,
+                       int chunk = 0)
 {
     const lbm_config& c = e->cfg;
     StepParams p{};
@@ -546,7 +551,11 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
         if (c.sponge_len > 0) p.sx0 = c.nx - c.sponge_len;
         p.om_col = e->om_col;
         p.inlet_g = e->inlet_g;
-        p.open_u = e->open_u;
+        const int64_t u_buf = (int64_t)4 * c.ny * e->n;  // one velocity buffer per step parity
+        p.open_u = e->open_u + (step & 1) * u_buf;
+        p.open_u_prev = e->open_u + ((step + 1) & 1) * u_buf;
+        p.outlet_from_u = step > 0 ? 1 : 0;
+        p.write_outlet = step + 1 >= chunk ? 1 : 0;
         // the outlet column is the boundary kernel's: a row segment that would
         // hold it alone is not launched
         p.nseg = std::max(1, (c.nx - 1 + 32 * vec - 1) / (32 * vec));
@@ -588,16 +597,16 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
     const StepVariant& v = step_variants()[vi];
     const StepVariant::Launch launch = launcher(e, v);
     if (!launch) return fail(LBM_ERR_ARG, "the step variant has no open-channel instantiation");
-    // an open channel adds the outlet kernel, observables their own kernel
-    const int per_step = (e->cfg.open_x ? 2 : 1) + (e->observe ? 1 : 0);
+    // an open channel adds the outlet kernel once per chunk, observables their own kernel per step
+    const int launches = chunk * (1 + (e->observe ? 1 : 0)) + (e->cfg.open_x ? 1 : 0);
     if (!e->use_graphs) {
         for (int s = 0; s < chunk; ++s) {
-            cudaError_t err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->stream);
+            cudaError_t err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind, chunk), e->stream);
             if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
             if (e->observe && observables_launch(e, list_dev, n_list, s, e->stream))
                 return cuda_fail(cudaGetLastError(), "observables kernel launch");
         }
-        count_launches(chunk * per_step);
+        count_launches(launches);
         return LBM_OK;
     }
     lbm_ensemble::StepGraph* hit = nullptr;
@@ -608,7 +617,7 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
         LBM_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed));
         cudaError_t launch_err = cudaSuccess;
         for (int s = 0; s < chunk && launch_err == cudaSuccess; ++s) {
-            launch_err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind), e->cap_stream);
+            launch_err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind, chunk), e->cap_stream);
             if (launch_err == cudaSuccess && e->observe && observables_launch(e, list_dev, n_list, s, e->cap_stream))
                 launch_err = cudaGetLastError();
         }
@@ -634,7 +643,7 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
     }
     hit->used = ++e->graph_clock;
     LBM_CUDA(cudaGraphLaunch(hit->exec, e->stream));
-    count_launches(chunk * per_step);
+    count_launches(launches);
     return LBM_OK;
 }
 
@@ -864,7 +873,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     if (c.open_x) {
         ALLOC(e->om_col, sizeof(float) * c.nx);
         ALLOC(e->inlet_g, sizeof(float) * 9 * c.ny);
-        ALLOC(e->open_u, sizeof(float) * 4 * c.ny * (size_t)n_clones);
+        ALLOC(e->open_u, sizeof(float) * 2 * 4 * c.ny * (size_t)n_clones);
     }
 #undef ALLOC
     std::vector<int32_t> iota(n_clones);

@@ -234,6 +234,53 @@ __device__ __forceinline__ void open_velocity9(const float (&g)[9], float& ux, f
     uy = jy * inv;
 }
 
+// carried value g_q = f_q - w_q of the open channel's outlet column (x = nx - 1)
+// at row y, regularized (Latt et al. 2008) from the velocities of columns nx-2
+// and nx-3 in u = [ux(nx-2), uy(nx-2), ux(nx-3), uy(nx-3)][ny]:
+//   rho = 1,  u = 2 u(nx-2) - u(nx-3),
+//   f_q = f_q^eq(1, u) + w_q / (2 cs2^2) Q_q : Pi,  Q_q = c_q c_q - cs2 I,
+//   Pi = bc_pre S,  bc_pre = -2 cs2 (tau(nx-1) - 1),
+// S the strain rate by finite differences: x one-sided from the two upstream
+// columns, y central on the extrapolated column (one-sided on the wall rows).
+// Every operation is rounded explicitly (no contraction), so that the kernel
+// that stores the column and a step that pulls from it without the stored
+// column (outlet_from_u) compute the same value bit for bit.
+__device__ __forceinline__ float outlet_g(const float* __restrict__ u, int ny, int y, int q, float bc_pre)
+{
+    const int ym = y > 0 ? y - 1 : y, yp = y < ny - 1 ? y + 1 : y;
+    // written by the step kernel just before (L2 loads)
+    const float u2 = __ldcg(u + y), v2 = __ldcg(u + ny + y), u3 = __ldcg(u + 2 * ny + y), v3 = __ldcg(u + 3 * ny + y);
+    const float exm = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + ym)), __ldcg(u + 2 * ny + ym));
+    const float exp_ = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + yp)), __ldcg(u + 2 * ny + yp));
+    const float eym = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + ny + ym)), __ldcg(u + 3 * ny + ym));
+    const float eyp = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + ny + yp)), __ldcg(u + 3 * ny + yp));
+    const float inv_dy = yp - ym == 2 ? 0.5f : 1.0f;
+    const float dxux = __fsub_rn(u2, u3), dxuy = __fsub_rn(v2, v3);
+    const float dyux = __fmul_rn(__fsub_rn(exp_, exm), inv_dy), dyuy = __fmul_rn(__fsub_rn(eyp, eym), inv_dy);
+    const float pxx = __fmul_rn(bc_pre, dxux), pyy = __fmul_rn(bc_pre, dyuy);
+    const float pxy = __fmul_rn(__fmul_rn(bc_pre, 0.5f), __fadd_rn(dyux, dxuy));
+    const float ux = __fsub_rn(__fmul_rn(2.0f, u2), u3), uy = __fsub_rn(__fmul_rn(2.0f, v2), v3);
+    const float usq = __fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy));
+    const float cxq = (float)cx(q), cyq = (float)cy(q);
+    const float cu = __fadd_rn(__fmul_rn(cxq, ux), __fmul_rn(cyq, uy));
+    const float qp = __fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(__fmul_rn(cxq, cxq), 1.0f / 3.0f), pxx),
+                                         __fmul_rn(__fmul_rn(2.0f * cxq, cyq), pxy)),
+                               __fmul_rn(__fsub_rn(__fmul_rn(cyq, cyq), 1.0f / 3.0f), pyy));
+    const float t = __fadd_rn(__fsub_rn(__fadd_rn(__fmul_rn(3.0f, cu), __fmul_rn(__fmul_rn(4.5f, cu), cu)),
+                                        __fmul_rn(1.5f, usq)),
+                              __fmul_rn(4.5f, qp));
+    return __fmul_rn(wf(q), t);
+}
+
+// the outlet value of direction q at row y as a pull would load it: stored in
+// the storage format, then decoded
+template <int S, bool SCALED>
+__device__ __noinline__ float outlet_pulled(const StepParams& p, const float* __restrict__ u, int y, int q)
+{
+    using K = Carry<S, SCALED>;
+    return K::in(K::out(outlet_g(u, p.ny, y, q, p.bc_pre), wf(q), p.scale), wf(q), p.inv_scale);
+}
+
 template <int S, int V, bool GENERAL, bool SCALED, int COLL, bool OPEN>
 __device__ __forceinline__ void step_warp(const StepParams& p, const typename Codec<S>::T* __restrict__ src,
                                           typename Codec<S>::T* __restrict__ dst, int c, int y, int seg, int lane,
@@ -370,6 +417,23 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
         }
     }
 
+    if constexpr (OPEN) {
+        // the previous step of this chunk left the outlet column unwritten: the
+        // pulls from it (directions 3, 6 and 7 at column nx - 2, from rows y,
+        // y - 1 and y + 1) take the outlet that step's velocities give, as the
+        // stored column would hold it; a wall row keeps its bounce-back
+        if (p.outlet_from_u && x0 <= p.nx - 2 && x0 + V > p.nx - 2) {
+            const float* u = p.open_u_prev + (int64_t)blockIdx.z * 4 * p.ny;
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if (x0 + j == p.nx - 2) {
+                    g[3][j] = outlet_pulled<S, SCALED>(p, u, y, 3);
+                    if (y > 0) g[6][j] = outlet_pulled<S, SCALED>(p, u, y - 1, 6);
+                    if (y + 1 < p.ny) g[7][j] = outlet_pulled<S, SCALED>(p, u, y + 1, 7);
+                }
+        }
+    }
+
     // ---- phase 3: BGK collision with Guo forcing
     if constexpr (OPEN) {
         // one collision body per site: the rate of a sponge column, else 1/tau
@@ -499,10 +563,13 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
 //                      the two upstream columns, y central on the extrapolated
 //                      column (one-sided on the wall rows).
 // The threads that own columns nx-2 and nx-3 leave their velocities (as
-// stored) in p.open_u ([list index][ux(nx-2), uy(nx-2), ux(nx-3), uy(nx-3)][ny]),
-// and open_bc_kernel, launched after the step on the same stream, writes the
-// outlet column from them: four coalesced floats per row.  A row segment that
-// would hold column nx-1 alone is not launched.  (Writing the outlet from the
+// stored) in p.open_u ([list index][ux(nx-2), uy(nx-2), ux(nx-3), uy(nx-3)][ny],
+// one buffer per step parity).  Within a chunk of steps the outlet column is
+// not written: the next step's thread of column nx-2 computes the three outlet
+// populations it pulls from those velocities (outlet_from_u).  After the
+// chunk's last step open_bc_kernel writes the column from them, so that every
+// state seen outside a chunk (checkpoints, copies, reads) is whole.  A row
+// segment that would hold column nx-1 alone is not launched.  (Writing the outlet from the
 // block that finishes last for each clone instead, with an arrival counter,
 // measured slower: every block waits at a barrier before it can retire, and
 // the last clone's outlet lands on the kernel's tail.)
@@ -513,29 +580,9 @@ __device__ __forceinline__ void open_outlet_row(const StepParams& p, typename Co
 {
     using K = Carry<S, SCALED>;
     const float* u = p.open_u + (int64_t)li * 4 * p.ny;
-    const int ym = y > 0 ? y - 1 : y, yp = y < p.ny - 1 ? y + 1 : y;
-    // written by the step kernel just before (L2 loads)
-    const float u2 = __ldcg(u + y), v2 = __ldcg(u + p.ny + y), u3 = __ldcg(u + 2 * p.ny + y),
-                v3 = __ldcg(u + 3 * p.ny + y);
-    const float exm = 2.0f * __ldcg(u + ym) - __ldcg(u + 2 * p.ny + ym);
-    const float exp_ = 2.0f * __ldcg(u + yp) - __ldcg(u + 2 * p.ny + yp);
-    const float eym = 2.0f * __ldcg(u + p.ny + ym) - __ldcg(u + 3 * p.ny + ym);
-    const float eyp = 2.0f * __ldcg(u + p.ny + yp) - __ldcg(u + 3 * p.ny + yp);
-    const float inv_dy = 1.0f / (float)(yp - ym);
-    const float dxux = u2 - u3, dxuy = v2 - v3;
-    const float dyux = (exp_ - exm) * inv_dy, dyuy = (eyp - eym) * inv_dy;
-    const float pxx = p.bc_pre * dxux, pyy = p.bc_pre * dyuy, pxy = p.bc_pre * 0.5f * (dyux + dxuy);
-    const float ux = 2.0f * u2 - u3, uy = 2.0f * v2 - v3;
-    const float usq = ux * ux + uy * uy;
     typename Codec<S>::T* o = st + (int64_t)y * p.pitch + (p.nx - 1);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        const float cxq = (float)cx(q), cyq = (float)cy(q);
-        const float cu = cxq * ux + cyq * uy;
-        const float qp = (cxq * cxq - (1.0f / 3.0f)) * pxx + 2.0f * cxq * cyq * pxy + (cyq * cyq - (1.0f / 3.0f)) * pyy;
-        const float gq = wf(q) * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq + 4.5f * qp);
-        o[q * p.plane] = K::out(gq, wf(q), p.scale);
-    }
+    for (int q = 0; q < 9; ++q) o[q * p.plane] = K::out(outlet_g(u, p.ny, y, q, p.bc_pre), wf(q), p.scale);
 }
 
 template <int S, int V, int WARPS, bool SCALED, int COLL, bool OPEN = false>
@@ -614,7 +661,8 @@ cudaError_t launch_step(const StepParams& p, cudaStream_t s)
 }
 
 // one step of an open channel: the fused step's open-channel instantiation
-// (which also writes the inlet column), then the outlet column.  (Launching
+// (which also writes the inlet column), then, after a chunk's last step, the
+// outlet column.  (Launching
 // the outlet kernel as a programmatic dependent of the step measured slower:
 // its waiting blocks hold SM slots during the step's tail.)
 template <int S, int V, int WARPS>
@@ -627,7 +675,7 @@ cudaError_t launch_step_open(const StepParams& p, cudaStream_t s)
         constexpr int C = decltype(coll)::value;
         constexpr bool SC = decltype(scaled)::value;
         step_kernel<S, V, WARPS, SC, C, true><<<grid, block, 0, s>>>(p);
-        open_bc_kernel<S, SC><<<bc_grid, kBcThreads, 0, s>>>(p);
+        if (p.write_outlet) open_bc_kernel<S, SC><<<bc_grid, kBcThreads, 0, s>>>(p);
     };
     auto by_scale = [&](auto coll) {
         if constexpr (S == kFP32) {

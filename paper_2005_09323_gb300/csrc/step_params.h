@@ -108,7 +108,11 @@ struct StepParams {
     const float* om_col;        // [nx] relaxation rate 1/tau(x) of each column
     const float* inlet_g;       // [9][ny] inlet populations minus w_q (FP32 of the FP64 values)
     float bc_pre;               // outlet stress factor -2 cs2 (tau(nx-1) - 1)
-    float* open_u;              // [list index][4][ny] velocities of columns nx-2, nx-3
+    float* open_u;              // [list index][4][ny] velocities of columns nx-2, nx-3 (this step writes)
+    const float* open_u_prev;   // the same, written by the previous step of the chunk
+    int32_t outlet_from_u;      // 1: the pulls from the outlet column use the outlet computed from
+                                // open_u_prev (the previous step left that column unwritten)
+    int32_t write_outlet;       // 1: the launch also writes the outlet column (the chunk's last step)
 };
 
 // consumer warps of the row-staged step kernel; each writes its own drag
