@@ -235,8 +235,8 @@ __device__ __forceinline__ void open_velocity9(const float (&g)[9], float& ux, f
 }
 
 // carried value g_q = f_q - w_q of the open channel's outlet column (x = nx - 1)
-// at row y, regularized (Latt et al. 2008) from the velocities of columns nx-2
-// and nx-3 in u = [ux(nx-2), uy(nx-2), ux(nx-3), uy(nx-3)][ny]:
+// at one row, regularized (Latt et al. 2008) from the velocities of columns
+// nx-2 and nx-3:
 //   rho = 1,  u = 2 u(nx-2) - u(nx-3),
 //   f_q = f_q^eq(1, u) + w_q / (2 cs2^2) Q_q : Pi,  Q_q = c_q c_q - cs2 I,
 //   Pi = bc_pre S,  bc_pre = -2 cs2 (tau(nx-1) - 1),
@@ -245,23 +245,29 @@ __device__ __forceinline__ void open_velocity9(const float (&g)[9], float& ux, f
 // Every operation is rounded explicitly (no contraction), so that the kernel
 // that stores the column and a step that pulls from it without the stored
 // column (outlet_from_u) compute the same value bit for bit.
-__device__ __forceinline__ float outlet_g(const float* __restrict__ u, int ny, int y, int q, float bc_pre)
+// the twelve velocity components one outlet row needs: columns nx-2 (2) and
+// nx-3 (3) at the row itself and at its neighbours ym, yp (the row itself on a
+// wall row), and whether the y difference spans two rows
+struct OutletU {
+    float u2, v2, u3, v3;          // row y
+    float u2m, u3m, v2m, v3m;      // row ym
+    float u2p, u3p, v2p, v3p;      // row yp
+    bool two;                      // yp - ym == 2
+};
+
+__device__ __forceinline__ float outlet_g(const OutletU& a, float cxq, float cyq, float wq, float bc_pre)
 {
-    const int ym = y > 0 ? y - 1 : y, yp = y < ny - 1 ? y + 1 : y;
-    // written by the step kernel just before (L2 loads)
-    const float u2 = __ldcg(u + y), v2 = __ldcg(u + ny + y), u3 = __ldcg(u + 2 * ny + y), v3 = __ldcg(u + 3 * ny + y);
-    const float exm = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + ym)), __ldcg(u + 2 * ny + ym));
-    const float exp_ = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + yp)), __ldcg(u + 2 * ny + yp));
-    const float eym = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + ny + ym)), __ldcg(u + 3 * ny + ym));
-    const float eyp = __fsub_rn(__fmul_rn(2.0f, __ldcg(u + ny + yp)), __ldcg(u + 3 * ny + yp));
-    const float inv_dy = yp - ym == 2 ? 0.5f : 1.0f;
-    const float dxux = __fsub_rn(u2, u3), dxuy = __fsub_rn(v2, v3);
+    const float exm = __fsub_rn(__fmul_rn(2.0f, a.u2m), a.u3m);
+    const float exp_ = __fsub_rn(__fmul_rn(2.0f, a.u2p), a.u3p);
+    const float eym = __fsub_rn(__fmul_rn(2.0f, a.v2m), a.v3m);
+    const float eyp = __fsub_rn(__fmul_rn(2.0f, a.v2p), a.v3p);
+    const float inv_dy = a.two ? 0.5f : 1.0f;
+    const float dxux = __fsub_rn(a.u2, a.u3), dxuy = __fsub_rn(a.v2, a.v3);
     const float dyux = __fmul_rn(__fsub_rn(exp_, exm), inv_dy), dyuy = __fmul_rn(__fsub_rn(eyp, eym), inv_dy);
     const float pxx = __fmul_rn(bc_pre, dxux), pyy = __fmul_rn(bc_pre, dyuy);
     const float pxy = __fmul_rn(__fmul_rn(bc_pre, 0.5f), __fadd_rn(dyux, dxuy));
-    const float ux = __fsub_rn(__fmul_rn(2.0f, u2), u3), uy = __fsub_rn(__fmul_rn(2.0f, v2), v3);
+    const float ux = __fsub_rn(__fmul_rn(2.0f, a.u2), a.u3), uy = __fsub_rn(__fmul_rn(2.0f, a.v2), a.v3);
     const float usq = __fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy));
-    const float cxq = (float)cx(q), cyq = (float)cy(q);
     const float cu = __fadd_rn(__fmul_rn(cxq, ux), __fmul_rn(cyq, uy));
     const float qp = __fadd_rn(__fadd_rn(__fmul_rn(__fsub_rn(__fmul_rn(cxq, cxq), 1.0f / 3.0f), pxx),
                                          __fmul_rn(__fmul_rn(2.0f * cxq, cyq), pxy)),
@@ -269,16 +275,89 @@ __device__ __forceinline__ float outlet_g(const float* __restrict__ u, int ny, i
     const float t = __fadd_rn(__fsub_rn(__fadd_rn(__fmul_rn(3.0f, cu), __fmul_rn(__fmul_rn(4.5f, cu), cu)),
                                         __fmul_rn(1.5f, usq)),
                               __fmul_rn(4.5f, qp));
-    return __fmul_rn(wf(q), t);
+    return __fmul_rn(wq, t);
 }
 
-// the outlet value of direction q at row y as a pull would load it: stored in
-// the storage format, then decoded
+// the velocities of outlet row y from the buffer the step kernel writes
+__device__ __forceinline__ OutletU outlet_u_at(const float* __restrict__ u, int ny, int y)
+{
+    const int ym = y > 0 ? y - 1 : y, yp = y < ny - 1 ? y + 1 : y;
+    OutletU a;
+    // written by the step kernel just before (L2 loads)
+    a.u2 = __ldcg(u + y);
+    a.v2 = __ldcg(u + ny + y);
+    a.u3 = __ldcg(u + 2 * ny + y);
+    a.v3 = __ldcg(u + 3 * ny + y);
+    a.u2m = __ldcg(u + ym);
+    a.u3m = __ldcg(u + 2 * ny + ym);
+    a.v2m = __ldcg(u + ny + ym);
+    a.v3m = __ldcg(u + 3 * ny + ym);
+    a.u2p = __ldcg(u + yp);
+    a.u3p = __ldcg(u + 2 * ny + yp);
+    a.v2p = __ldcg(u + ny + yp);
+    a.v3p = __ldcg(u + 3 * ny + yp);
+    a.two = yp - ym == 2;
+    return a;
+}
+
+// The pulls of a step whose previous step (in the same chunk) left the outlet
+// column unwritten: directions 3, 6 and 7 at column nx - 2 come from the outlet
+// at rows y, y - 1 and y + 1.  The warp holding column nx - 2 loads the twenty
+// velocity values of rows y - 2 .. y + 2 (clamped to the channel) in phase 1,
+// one per lane; lanes 0, 1 and 2 gather by shuffles what their outlet row
+// needs and compute one direction each, in the storage format and back (as a
+// pull from the stored column would load it); the owner of column nx - 2 takes
+// the three values by shuffles.
+struct OutletPrefetch {
+    float v;    // lane l < 20: component l / 5 at row clamp(y - 2 + l % 5)
+};
+
+__device__ __forceinline__ OutletPrefetch outlet_prefetch(const StepParams& p, int y, int lane)
+{
+    OutletPrefetch f{0.f};
+    if (lane < 20) {
+        int r = y - 2 + lane % 5;
+        r = r < 0 ? 0 : (r >= p.ny ? p.ny - 1 : r);
+        f.v = __ldcg(p.open_u_prev + ((int64_t)blockIdx.z * 4 + lane / 5) * p.ny + r);
+    }
+    return f;
+}
+
 template <int S, bool SCALED>
-__device__ __noinline__ float outlet_pulled(const StepParams& p, const float* __restrict__ u, int y, int q)
+__device__ __forceinline__ void outlet_pulls(const StepParams& p, const OutletPrefetch& f, int y, int lane,
+                                             float& g3, float& g6, float& g7)
 {
     using K = Carry<S, SCALED>;
-    return K::in(K::out(outlet_g(u, p.ny, y, q, p.bc_pre), wf(q), p.scale), wf(q), p.inv_scale);
+    // lane 0: direction 3 from row y; lane 1: 6 from row y - 1; lane 2: 7 from row y + 1
+    const int k = lane < 3 ? lane : 0;
+    const int yo_raw = y + (k == 1 ? -1 : (k == 2 ? 1 : 0));
+    const int yo = yo_raw < 0 ? 0 : (yo_raw >= p.ny ? p.ny - 1 : yo_raw);
+    const int ym = yo > 0 ? yo - 1 : yo, yp = yo < p.ny - 1 ? yo + 1 : yo;
+    // rows yo, ym, yp lie within y - 2 .. y + 2: index component * 5 + (row - y + 2)
+    auto at = [&](int comp, int row) { return __shfl_sync(0xffffffffu, f.v, comp * 5 + (row - y + 2)); };
+    OutletU a;
+    a.u2 = at(0, yo);
+    a.v2 = at(1, yo);
+    a.u3 = at(2, yo);
+    a.v3 = at(3, yo);
+    a.u2m = at(0, ym);
+    a.v2m = at(1, ym);
+    a.u3m = at(2, ym);
+    a.v3m = at(3, ym);
+    a.u2p = at(0, yp);
+    a.v2p = at(1, yp);
+    a.u3p = at(2, yp);
+    a.v3p = at(3, yp);
+    a.two = yp - ym == 2;
+    const int q = k == 0 ? 3 : (k == 1 ? 6 : 7);
+    const float wq = k == 0 ? wf(3) : wf(6);
+    const float r = K::in(K::out(outlet_g(a, -1.0f, k == 0 ? 0.0f : (k == 1 ? 1.0f : -1.0f), wq, p.bc_pre), wq,
+                                 p.scale),
+                          wq, p.inv_scale);
+    (void)q;
+    g3 = __shfl_sync(0xffffffffu, r, 0);
+    g6 = __shfl_sync(0xffffffffu, r, 1);
+    g7 = __shfl_sync(0xffffffffu, r, 2);
 }
 
 template <int S, int V, bool GENERAL, bool SCALED, int COLL, bool OPEN>
@@ -325,6 +404,14 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
             const int xs = x0 + V >= p.nx ? 0 : x0 + V;
             if (lane == 31 || x0 + V >= p.nx) edge[q] = ld_one(rp + xs);
         }
+    }
+
+    // the warp holding column nx - 2 of an open channel, inside a chunk: the
+    // velocities for the outlet it pulls from, loaded with the populations
+    const bool outlet_warp = OPEN && p.outlet_from_u && seg * 32 * V <= p.nx - 2 && p.nx - 2 < (seg + 1) * 32 * V;
+    OutletPrefetch opf{0.f};
+    if constexpr (OPEN) {
+        if (outlet_warp) opf = outlet_prefetch(p, y, lane);
     }
 
     // ---- phase 2: assemble the pulled values of the V sites
@@ -422,14 +509,15 @@ __device__ __forceinline__ void step_warp(const StepParams& p, const typename Co
         // pulls from it (directions 3, 6 and 7 at column nx - 2, from rows y,
         // y - 1 and y + 1) take the outlet that step's velocities give, as the
         // stored column would hold it; a wall row keeps its bounce-back
-        if (p.outlet_from_u && x0 <= p.nx - 2 && x0 + V > p.nx - 2) {
-            const float* u = p.open_u_prev + (int64_t)blockIdx.z * 4 * p.ny;
+        if (outlet_warp) {
+            float o3, o6, o7;
+            outlet_pulls<S, SCALED>(p, opf, y, lane, o3, o6, o7);
 #pragma unroll
             for (int j = 0; j < V; ++j)
                 if (x0 + j == p.nx - 2) {
-                    g[3][j] = outlet_pulled<S, SCALED>(p, u, y, 3);
-                    if (y > 0) g[6][j] = outlet_pulled<S, SCALED>(p, u, y - 1, 6);
-                    if (y + 1 < p.ny) g[7][j] = outlet_pulled<S, SCALED>(p, u, y + 1, 7);
+                    g[3][j] = o3;
+                    if (y > 0) g[6][j] = o6;
+                    if (y + 1 < p.ny) g[7][j] = o7;
                 }
         }
     }
@@ -581,12 +669,18 @@ __device__ __forceinline__ void open_outlet_row(const StepParams& p, typename Co
     using K = Carry<S, SCALED>;
     const float* u = p.open_u + (int64_t)li * 4 * p.ny;
     typename Codec<S>::T* o = st + (int64_t)y * p.pitch + (p.nx - 1);
+    const OutletU a = outlet_u_at(u, p.ny, y);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) o[q * p.plane] = K::out(outlet_g(u, p.ny, y, q, p.bc_pre), wf(q), p.scale);
+    for (int q = 0; q < 9; ++q)
+        o[q * p.plane] = K::out(outlet_g(a, (float)cx(q), (float)cy(q), wf(q), p.bc_pre), wf(q), p.scale);
 }
 
+// open-channel instantiations of up to 4 sites per thread are held to 64
+// registers (32 resident warps per SM instead of 24): latency-bound, they gain
+// more from the warps in flight than they lose to a few spilled bytes
 template <int S, int V, int WARPS, bool SCALED, int COLL, bool OPEN = false>
-__global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
+__global__ void __launch_bounds__(WARPS * 32, (OPEN && V <= 4) ? 1024 / (WARPS * 32) : 1)
+    step_kernel(const StepParams p)
 {
     using T = typename Codec<S>::T;
     const int lane = threadIdx.x;
