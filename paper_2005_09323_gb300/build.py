@@ -19,7 +19,7 @@ BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liblbmrare.so")
 
 SOURCES = ["lbm_ensemble.cu", "selection.cu", "step_fp32.cu", "step_fp16.cu", "step_bf16.cu", "step_open_fp32.cu", "step_open_16.cu", "noalloc.cu", "drivers.cu", "cnn.cu", "conv_tc.cu", "surrogate.cu", "stats.cu", "observables.cu"]
-HEADERS = ["lbm_device.cuh", "lbm_step.cuh", "lbm_step_rows.cuh", "async_copy.cuh", "internal.h", "step_params.h"]
+HEADERS = ["lbm_device.cuh", "lbm_step.cuh", "lbm_step_rows.cuh", "lbm_step_tb.cuh", "async_copy.cuh", "internal.h", "step_params.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

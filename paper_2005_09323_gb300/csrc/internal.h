@@ -29,11 +29,13 @@ struct StepVariant {
     int vec;    // sites per thread
     int warps;  // warps per block
     cudaError_t (*launch)(const StepParams&, cudaStream_t);
-    int kind;   // 0: register-staged row segments per warp; 1: whole rows staged by bulk copies
+    int kind;   // 0: register-staged row segments per warp; 1: whole rows staged by bulk copies;
+                // 2: tiles in shared memory, several steps per launch (temporal blocking)
     bool (*supports)(const StepParams&);  // null: every shape
     // the open channel's step (fused step + boundary columns); null: this
     // variant has no open-channel instantiation
     Launch launch_open = nullptr;
+    int multi = 1;  // most steps one launch runs (kind 2; an odd number per launch)
 };
 
 // LBM_ERR_ARG unless the collision fields of c are valid (lbm_ensemble.cu)

@@ -447,14 +447,22 @@ StepVariant::Launch launcher(const lbm_ensemble* e, const StepVariant& v)
     return e->cfg.open_x ? v.launch_open : v.launch;
 }
 
-// vec = 0: row-staged kernels, one slot per consumer warp in each ring row
-Ring ring_for(const lbm_config& c, int vec)
+// drag slots of a variant: kind 0, one per warp segment of vec sites in each
+// ring row; kind 1 (row-staged), one per consumer warp in each ring row; kind 2
+// (tiles), one per tile that holds part of the ring (rs0, rs1: tile columns)
+Ring ring_for(const lbm_config& c, int vec, int kind)
 {
     Ring r{0, -1, 0, -1, 0};
     if (c.obs_w <= 0) return r;
     r.ry0 = std::max(c.obs_y0 - 1, 0);
     r.ry1 = std::min(c.obs_y0 + c.obs_h, c.ny - 1);
-    if (vec > 0) {
+    if (kind == 2) {
+        r.rs0 = (c.obs_x0 - 1) / kTbTx;
+        r.rs1 = (c.obs_x0 + c.obs_w) / kTbTx;
+        r.n_slots = (r.ry1 / kTbTy - r.ry0 / kTbTy + 1) * (r.rs1 - r.rs0 + 1);
+        return r;
+    }
+    if (kind == 0) {
         const int seg_w = 32 * vec;
         r.rs0 = (c.obs_x0 - 1) / seg_w;
         r.rs1 = (c.obs_x0 + c.obs_w) / seg_w;
@@ -517,7 +525,7 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
     p.ox1 = c.obs_w > 0 ? c.obs_x0 + c.obs_w : c.obs_x0;
     p.oy0 = c.obs_y0;
     p.oy1 = c.obs_w > 0 ? c.obs_y0 + c.obs_h : c.obs_y0;
-    const Ring r = ring_for(c, kind == 1 ? 0 : vec);
+    const Ring r = ring_for(c, vec, kind);
     p.ry0 = r.ry0;
     p.ry1 = r.ry1;
     p.rs0 = r.rs0;
@@ -534,6 +542,7 @@ StepParams make_params(const lbm_ensemble* e, const int32_t* list, int32_t n_lis
     p.scale = e->scale;
     p.inv_scale = e->inv_scale;
     p.step_in_batch = step;
+    p.tb_steps = 1;
     const Solids sol = solids_of(c);
     p.open = c.open_x;
     p.gx0 = sol.gx0;
@@ -597,13 +606,28 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
     const StepVariant& v = step_variants()[vi];
     const StepVariant::Launch launch = launcher(e, v);
     if (!launch) return fail(LBM_ERR_ARG, "the step variant has no open-channel instantiation");
+    // the steps of each launch: one, or for a multi-step variant an odd number
+    // of at most v.multi (observables need the state after every step: one)
+    std::vector<int> first, count;
+    for (int s = 0; s < chunk;) {
+        int k = (v.multi > 1 && !e->observe) ? std::min(v.multi, chunk - s) : 1;
+        if (k % 2 == 0) k -= 1;
+        first.push_back(s);
+        count.push_back(k);
+        s += k;
+    }
+    auto params = [&](size_t i) {
+        StepParams p = make_params(e, list_dev, n_list, v.vec, first[i], v.kind, chunk);
+        p.tb_steps = count[i];
+        return p;
+    };
     // an open channel adds the outlet kernel once per chunk, observables their own kernel per step
-    const int launches = chunk * (1 + (e->observe ? 1 : 0)) + (e->cfg.open_x ? 1 : 0);
+    const int launches = (int)first.size() + (e->observe ? chunk : 0) + (e->cfg.open_x ? 1 : 0);
     if (!e->use_graphs) {
-        for (int s = 0; s < chunk; ++s) {
-            cudaError_t err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind, chunk), e->stream);
+        for (size_t i = 0; i < first.size(); ++i) {
+            cudaError_t err = launch(params(i), e->stream);
             if (err != cudaSuccess) return cuda_fail(err, "step kernel launch");
-            if (e->observe && observables_launch(e, list_dev, n_list, s, e->stream))
+            if (e->observe && observables_launch(e, list_dev, n_list, first[i], e->stream))
                 return cuda_fail(cudaGetLastError(), "observables kernel launch");
         }
         count_launches(launches);
@@ -616,9 +640,10 @@ int launch_chunk(lbm_ensemble* e, int vi, const int32_t* list_dev, int n_list, i
         if (!e->cap_stream) LBM_CUDA(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
         LBM_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeRelaxed));
         cudaError_t launch_err = cudaSuccess;
-        for (int s = 0; s < chunk && launch_err == cudaSuccess; ++s) {
-            launch_err = launch(make_params(e, list_dev, n_list, v.vec, s, v.kind, chunk), e->cap_stream);
-            if (launch_err == cudaSuccess && e->observe && observables_launch(e, list_dev, n_list, s, e->cap_stream))
+        for (size_t i = 0; i < first.size() && launch_err == cudaSuccess; ++i) {
+            launch_err = launch(params(i), e->cap_stream);
+            if (launch_err == cudaSuccess && e->observe &&
+                observables_launch(e, list_dev, n_list, first[i], e->cap_stream))
                 launch_err = cudaGetLastError();
         }
         cudaGraph_t graph = nullptr;
@@ -655,7 +680,7 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
     const int n_list = (int)list.size();
     const int vi = variant_for(e, n_list);
     const StepVariant& v = vars[vi];
-    const Ring r = ring_for(e->cfg, v.kind == 1 ? 0 : v.vec);
+    const Ring r = ring_for(e->cfg, v.vec, v.kind);
     int32_t t = e->t_host[list[0]];
     int32_t left = n_steps;
     while (left > 0) {
@@ -837,7 +862,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     // partial slots: enough for the narrowest segments of any variant
     int max_slots = 1;
     for (const auto& v : step_variants())
-        if (v.storage == c.storage) max_slots = std::max(max_slots, ring_for(c, v.kind == 1 ? 0 : v.vec).n_slots);
+        if (v.storage == c.storage) max_slots = std::max(max_slots, ring_for(c, v.vec, v.kind).n_slots);
     e->n_slots = max_slots;
     e->n_ckpt = c.ckpt_stride > 0 ? c.max_steps / c.ckpt_stride + 1 : 0;
     e->parity_host.assign(n_clones, 0);
@@ -1315,6 +1340,7 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
             const StepVariant::Launch launch = launcher(e, v);
             if (!launch) continue;
             StepParams p = make_params(e, e->all_dev, n_list, v.vec, 0, v.kind);
+            p.tb_steps = v.multi;  // a multi-step trial runs its steps: timed per step below
             if (v.supports && !v.supports(p)) continue;
             for (int r = 0; r < 2; ++r)
                 if (launch(p, e->stream) != cudaSuccess) return -1;
@@ -1326,6 +1352,7 @@ int lbm_ensemble_autotune(lbm_ensemble* e, int32_t* variant)
             if (cudaEventSynchronize(b) != cudaSuccess) return -1;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
+            ms /= (float)v.multi;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = (int)i;

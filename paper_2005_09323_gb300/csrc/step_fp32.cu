@@ -1,6 +1,7 @@
 // Instantiations of the fused step for fp32 population storage.
 #include "lbm_step.cuh"
 #include "lbm_step_rows.cuh"
+#include "lbm_step_tb.cuh"
 
 namespace lbm {
 
@@ -28,6 +29,9 @@ void register_step_fp32(std::vector<StepVariant>& out)
     out.push_back({kFP32, 4, 4, &launch_step<kFP32, 4, 4>, 0, nullptr});
     out.push_back({kFP32, 4, 8, &launch_step<kFP32, 4, 8>, 0, nullptr});
     out.push_back({kFP32, 4, kRowThreads / 32, &launch_rows<kFP32, 4>, 1, &rows_supported<kFP32, 4>});
+    // several steps per launch from shared memory: the small calls of one AMS branch
+    out.push_back({kFP32, 1, kTbThreads / 32, &launch_tb<kFP32>, 2, &tb_supported<kFP32>});
+    out.back().multi = kTbHalo;
 }
 
 }  // namespace lbm

@@ -113,10 +113,18 @@ struct StepParams {
     int32_t outlet_from_u;      // 1: the pulls from the outlet column use the outlet computed from
                                 // open_u_prev (the previous step left that column unwritten)
     int32_t write_outlet;       // 1: the launch also writes the outlet column (the chunk's last step)
+    int32_t tb_steps;           // steps of one launch of the temporally blocked kernel (odd)
 };
 
 // consumer warps of the row-staged step kernel; each writes its own drag
 // partial for every obstacle-ring row it computes
 constexpr int kRowWarps = 8;
+
+// the temporally blocked step kernel: tiles of kTbTx x kTbTy sites with a halo
+// of kTbHalo sites (a 32 x 16 region, one site per thread), at most kTbHalo
+// steps per launch; one drag partial per tile of the obstacle ring and step
+constexpr int kTbHalo = 3, kTbRw = 32, kTbRh = 16;
+constexpr int kTbTx = kTbRw - 2 * kTbHalo, kTbTy = kTbRh - 2 * kTbHalo;  // 26 x 10
+constexpr int kTbThreads = kTbRw * kTbRh;                              // 512
 
 }  // namespace lbm
