@@ -127,7 +127,9 @@ def test_cm_with_equal_rates_is_bgk(L):
         L.lbm_ensemble_step(b.h, 80)
         for c in range(2):
             assert rel(b.pops(c), a.pops(c)) < 1e-6
-        assert rel(b.drag(0, 80), a.drag(0, 80)) < 1e-5
+        # the drag (a few 1e-2) cancels some 60 link momenta of order 0.2: FP32
+        # differences of 1e-7 in the populations move it by a few 1e-7
+        assert rel(b.drag(0, 80), a.drag(0, 80)) < 5e-5
 
 
 def test_cm_noalloc_step_matches_ensemble(L):
