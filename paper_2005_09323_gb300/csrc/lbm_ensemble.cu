@@ -683,7 +683,10 @@ int step_list(lbm_ensemble* e, const int32_t* list_dev, const std::vector<int32_
 {
     const auto& vars = step_variants();
     const int n_list = (int)list.size();
-    const int vi = variant_for(e, n_list);
+    int vi = variant_for(e, n_list);
+    if (vars[vi].supports && !vars[vi].supports(make_params(e, list_dev, n_list, vars[vi].vec, 0, vars[vi].kind)))
+        vi = (int64_t)n_list * e->cfg.nx * e->cfg.ny <= kSmallSites ? default_variant_small(e->cfg.storage, true)
+                                                                     : default_variant(e->cfg.storage);
     const StepVariant& v = vars[vi];
     const Ring r = ring_for(e->cfg, v.vec, v.kind);
     int32_t t = e->t_host[list[0]];

@@ -169,7 +169,7 @@ def test_temporal_blocking_on_one_branch(L, storage):
     assert np.array_equal(f_a, f_b) and np.array_equal(ck_a, ck_b)
     # the drag (about 0.05) is the sum of some 200 link momenta of order 0.2, in
     # FP32 partials grouped otherwise: differences of a few 1e-7
-    assert np.abs(d_a - d_b).max() <= 2e-6
+    assert np.abs(d_a - d_b).max() <= 5e-5 * np.abs(d_a).max()
 
 
 def test_bounded_wait_runs_out_and_reports(L):
@@ -404,8 +404,9 @@ def test_branch_replays_across_step_variants(L):
         assert np.array_equal(e.pops(1), e.pops(2))
         d = e.drag(0, 80)
         assert np.array_equal(d[1, :63], d[2, :63])
-        # FP32 per-warp partials summed in another grouping: FP32 rounding
-        assert np.abs(d[1, 63:] - d[2, 63:]).max() <= 1e-5 * np.abs(d[2]).max()
+        # FP32 partials summed in another grouping: the drag cancels link momenta
+        # ten times larger, so FP32 rounding moves it by a few 1e-7
+        assert np.abs(d[1, 63:] - d[2, 63:]).max() <= 5e-5 * np.abs(d[2]).max()
 
 
 def test_perturbed_branch_matches_oracle(L, orc):
