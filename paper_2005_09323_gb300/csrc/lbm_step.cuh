@@ -675,12 +675,10 @@ __device__ __forceinline__ void open_outlet_row(const StepParams& p, typename Co
         o[q * p.plane] = K::out(outlet_g(a, (float)cx(q), (float)cy(q), wf(q), p.bc_pre), wf(q), p.scale);
 }
 
-// open-channel instantiations of up to 4 sites per thread are held to 64
-// registers (32 resident warps per SM instead of 24): latency-bound, they gain
-// more from the warps in flight than they lose to a few spilled bytes
-template <int S, int V, int WARPS, bool SCALED, int COLL, bool OPEN = false>
-__global__ void __launch_bounds__(WARPS * 32, (OPEN && V <= 4) ? 1024 / (WARPS * 32) : 1)
-    step_kernel(const StepParams p)
+// one warp's row segment of a fused-step launch (grid: segments, row blocks,
+// listed clones)
+template <int S, int V, int WARPS, bool SCALED, int COLL, bool OPEN>
+__device__ __forceinline__ void step_block(const StepParams& p)
 {
     using T = typename Codec<S>::T;
     const int lane = threadIdx.x;
@@ -713,6 +711,30 @@ __global__ void __launch_bounds__(WARPS * 32, (OPEN && V <= 4) ? 1024 / (WARPS *
         else
             step_warp<S, V, false, SCALED, COLL, false>(p, src, dst, c, y, seg, lane);
     }
+}
+
+// the periodic channel's fused step
+template <int S, int V, int WARPS, bool SCALED, int COLL>
+__global__ void __launch_bounds__(WARPS * 32) step_kernel(const StepParams p)
+{
+    step_block<S, V, WARPS, SCALED, COLL, false>(p);
+}
+
+// the open channel's fused step
+template <int S, int V, int WARPS, bool SCALED, int COLL>
+__global__ void __launch_bounds__(WARPS * 32) step_kernel_open(const StepParams p)
+{
+    step_block<S, V, WARPS, SCALED, COLL, true>(p);
+}
+
+// the same held to 64 registers, for 16-bit storage at up to 4 sites per
+// thread: 32 resident warps per SM instead of 24; issue-bound, it gains more
+// from the warps in flight than it loses to a few spilled bytes (FP32 storage
+// measured slower so)
+template <int S, int V, int WARPS, bool SCALED, int COLL>
+__global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32)) step_kernel_open64(const StepParams p)
+{
+    step_block<S, V, WARPS, SCALED, COLL, true>(p);
 }
 
 // the outlet column of an open channel, one thread per (row, listed clone),
@@ -768,7 +790,10 @@ cudaError_t launch_step_open(const StepParams& p, cudaStream_t s)
     auto go = [&](auto coll, auto scaled) {
         constexpr int C = decltype(coll)::value;
         constexpr bool SC = decltype(scaled)::value;
-        step_kernel<S, V, WARPS, SC, C, true><<<grid, block, 0, s>>>(p);
+        if constexpr (S != kFP32 && V <= 4)
+            step_kernel_open64<S, V, WARPS, SC, C><<<grid, block, 0, s>>>(p);
+        else
+            step_kernel_open<S, V, WARPS, SC, C><<<grid, block, 0, s>>>(p);
         if (p.write_outlet) open_bc_kernel<S, SC><<<bc_grid, kBcThreads, 0, s>>>(p);
     };
     auto by_scale = [&](auto coll) {
