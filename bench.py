@@ -93,15 +93,15 @@ METRIC = "Ensemble D2Q9 GLUPS & HBM-roofline fraction; time-to-return-time vs pl
 NCU_TRAFFIC = {
     ("gktl", "step_kernel<fp32, vec=4>"): {
         "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_fp32.cu"),
-        "sha": "c4516962776c0bb3", "bytes_per_site": 68.4735},
+        "sha": "241df406e4de695e", "bytes_per_site": 68.4597},
     ("precision", "step_rows_kernel<fp16, vec=4>"): {
         "files": ("lbm_step_rows.cuh", "async_copy.cuh", "lbm_step.cuh", "lbm_device.cuh", "step_params.h",
                   "step_fp16.cu"),
-        "sha": "4caf850e5db5f149", "bytes_per_site": 32.5056},
+        "sha": "9c24a2e7bd8f6b3e", "bytes_per_site": 32.5115},
     # both kernels of an open-channel step (the step kernel and the outlet kernel)
     ("open", "step_kernel<fp32, vec=4, open> + open_bc_kernel"): {
         "files": ("lbm_step.cuh", "lbm_device.cuh", "step_params.h", "step_open_fp32.cu"),
-        "sha": "ff6b9e0efa3adc0b", "bytes_per_site": 59.2802},
+        "sha": "3f91ba9496814b0e", "bytes_per_site": 59.1880},
 }
 
 
