@@ -52,13 +52,29 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
-// bounded by elapsed SM clock cycles instead of a poll count (the cycle
-// counter is a cheap register read, so a completed phase is seen promptly)
+// one try that suspends the thread in hardware until the phase completes or
+// about `ns` nanoseconds pass (the suspend-time hint of mbarrier.try_wait), so
+// that a waiting warp issues no instructions meanwhile
+__device__ inline bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded by elapsed SM clock cycles instead of a poll count.  After a first
+// plain try the thread waits in suspended tries: a warp that polled instead
+// would keep issuing barrier reads through the shared-memory pipe, which the
+// warps that issue the copies and the MMAs need as well.
 __device__ inline bool mbar_wait_cycles(uint32_t bar, uint32_t parity, long long limit_cycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait_suspend(bar, parity, 20000u))
         if (clock64() - t0 > limit_cycles) return false;
     return true;
 }

@@ -481,65 +481,81 @@ __global__ void __launch_bounds__(kRowThreads, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        // ---------------- TMA producer: input rows in the order the MMAs use them
+        // ---------------- TMA producer: input rows in the order the MMAs use them.
+        // The single thread's loop is the pipeline's pace, so its bookkeeping is
+        // 32-bit ring counters (slot, phase) rather than divisions of the row count.
         if (lane == 0) {
-            int64_t n = 0;
+            int n = 0, i = 0;
+            uint32_t par = 0;  // phase parity of the current pass over the slots
             auto load_row = [&](int b, int yr, int x0) -> bool {
-                const int i = (int)(n % kRowSlots);
-                if (n >= kRowSlots &&
-                    !mbar_wait_cycles(smem_addr(&empty[i]), (uint32_t)(((n / kRowSlots) - 1) & 1), kTcWaitCycles)) {
+                if (n >= kRowSlots && !mbar_wait_cycles(smem_addr(&empty[i]), par ^ 1u, kTcWaitCycles)) {
                     abort_flag = 1;
                     return false;
                 }
                 if (abort_flag) return false;
                 const uint32_t bar = smem_addr(&full[i]);
+                const uint32_t dst = ring_s + (uint32_t)i * kSlotBytes;
                 mbar_expect_tx(bar, kRowBoxBytes);
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    tma_load_4d(ring_s + i * kSlotBytes + c * kChunkBytes, &tmap, 8 * c, x0 - 1, yr, b, bar);
+                for (int c = 0; c < 4; ++c) tma_load_4d(dst + c * kChunkBytes, &tmap, 8 * c, x0 - 1, yr, b, bar);
                 ++n;
+                if (++i == kRowSlots) {
+                    i = 0;
+                    par ^= 1u;
+                }
                 return true;
             };
             walk_rows(sh, g0, g1, [&](int b, int y, int x0, int ya, int) {
                 if (y == ya && !(load_row(b, y - 1, x0) && load_row(b, y, x0))) return false;
                 return load_row(b, y + 1, x0);
             });
-            for (int64_t k = n - kRowSlots > 0 ? n - kRowSlots : 0; k < n; ++k)
+            for (int k = n - kRowSlots > 0 ? n - kRowSlots : 0; k < n; ++k)
                 mbar_wait_cycles(smem_addr(&full[k % kRowSlots]), (uint32_t)((k / kRowSlots) & 1), kTcWaitCycles);
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- MMA issuer: D_s for every input row s, in order
+        // ---------------- MMA issuer: D_s for every input row s, in order.  The
+        // input rows are the output rows plus two per run down a column; their
+        // MMAs do not depend on which output row they serve, so the loop is a
+        // plain count with ring counters, and the descriptors of slot i are those
+        // of slot 0 advanced by i slots (the start-address field holds address /
+        // 16 in 14 bits, which no shared-memory address overflows).
         if (lane == 0) {
-            int64_t n = 0;
-            auto compute = [&]() -> bool {
-                const int64_t sq = n++;
-                const int i = (int)(sq % kRowSlots), bi = (int)(sq % kRowBufs);
-                if (!mbar_wait_cycles(smem_addr(&full[i]), (uint32_t)((sq / kRowSlots) & 1), kTcWaitCycles) ||
-                    (sq >= kRowBufs && !mbar_wait_cycles(smem_addr(&dfree[bi]),
-                                                         (uint32_t)(((sq / kRowBufs) - 1) & 1), kTcWaitCycles))) {
-                    abort_flag = 1;
-                    return false;
+            const int n_in = g1 > g0 ? (int)(g1 - g0) + 2 * (int)((g1 - 1) / sh.H - g0 / sh.H + 1) : 0;
+            uint64_t ad[6], bd[6];
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    ad[2 * kx + ks] = interleave_desc(ring_s + 2 * ks * kChunkBytes + 16 * kx, kChunkBytes, 128);
+                    bd[2 * kx + ks] = sw64_desc(w_s + kx * kStackBytes + ks * 32);
                 }
-                if (abort_flag) return false;
+            int i = 0, bi = 0;
+            uint32_t fpar = 0, dround = 0;  // full's phase parity; passes over the accumulators
+            for (int sq = 0; sq < n_in; ++sq) {
+                if (!mbar_wait_cycles(smem_addr(&full[i]), fpar, kTcWaitCycles) ||
+                    (sq >= kRowBufs && !mbar_wait_cycles(smem_addr(&dfree[bi]), (dround - 1u) & 1u, kTcWaitCycles))) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
                 tc_fence_after();
-                const uint32_t rb = ring_s + (uint32_t)i * kSlotBytes;
+                const uint64_t so = (uint64_t)(((uint32_t)i * kSlotBytes) >> 4);
                 const uint32_t d = tmem + (uint32_t)(bi * 128);
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-                    for (int ks = 0; ks < 2; ++ks)
-                        umma_f16_n96(d, interleave_desc(rb + 2 * ks * kChunkBytes + 16 * kx, kChunkBytes, 128),
-                                     sw64_desc(w_s + kx * kStackBytes + ks * 32), (kx | ks) != 0);
+                for (int j = 0; j < 6; ++j) umma_f16_n96(d, ad[j] + so, bd[j], j != 0);
                 umma_commit(smem_addr(&dfull[bi]));  // D_s ready for the epilogue
                 umma_commit(smem_addr(&empty[i]));   // input slot free
-                return true;
-            };
-            walk_rows(sh, g0, g1, [&](int, int y, int, int ya, int) {
-                if (y == ya && !(compute() && compute())) return false;
-                return compute();
-            });
-            if (n > 0) {
+                if (++i == kRowSlots) {
+                    i = 0;
+                    fpar ^= 1u;
+                }
+                if (++bi == kRowBufs) {
+                    bi = 0;
+                    ++dround;
+                }
+            }
+            if (n_in > 0) {
                 umma_commit(smem_addr(&done));
                 mbar_wait_cycles(smem_addr(&done), 0, kTcWaitCycles);
             }
@@ -828,41 +844,60 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer.  Its loop sets the pipeline's pace, so the
+        // rings are followed with counters (slot, phase parity) and the operand
+        // descriptors are those of slot 0 advanced by the slot's offset (the
+        // start-address field holds address / 16 in 14 bits, which no shared-
+        // memory address overflows).
         if (lane == 0) {
-            int nin = 0, ndy = 0;  // input rows and stream rows consumed
+            uint64_t ad[8], bd[8];
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+                ad[ks] = sw64_mn_desc(in_s + ks * 1024, kWgCopy);
+                bd[ks] = sw64_mn_desc(dy_s + ks * 1024, kWgCopy);
+            }
+            int isl = 0, tm = 0, last = 0;  // input slot; stream row mod kWgDySlots; slot of the last row waited for
+            uint32_t ipar = 0, tpar = 0;
             bool first = true, ok = true;
             for (int u = blockIdx.x; u < sh.n_units && ok && !abort_flag; u += gridDim.x) {
                 int b, y0, y1, x0;
                 wg_unit(sh, u, b, y0, y1, x0);
-                const int n_out = y1 - y0, t0 = ndy;  // the unit's first stream row
+                const int n_out = y1 - y0;
                 for (int i = 0; i < n_out + 2 && ok; ++i) {
-                    for (int t = i == 0 ? t0 : t0 + i + 2; t <= t0 + i + 2 && ok; ++t)
-                        ok = mbar_wait_cycles(smem_addr(&dy_full[wg_dy_slot(t)]), (t / kWgDySlots) & 1, kTcWaitCycles);
-                    if (ok)
-                        ok = mbar_wait_cycles(smem_addr(&in_full[nin % kWgInSlots]), (nin / kWgInSlots) & 1,
-                                              kTcWaitCycles);
+                    // stream rows up to t0 + i + 2: three for the unit's first input row, then one
+                    for (int k = i == 0 ? 3 : 1; k > 0 && ok; --k) {
+                        last = kWgDySlots - 1 - tm;
+                        ok = mbar_wait_cycles(smem_addr(&dy_full[last]), tpar, kTcWaitCycles);
+                        if (++tm == kWgDySlots) {
+                            tm = 0;
+                            tpar ^= 1u;
+                        }
+                    }
+                    if (ok) ok = mbar_wait_cycles(smem_addr(&in_full[isl]), ipar, kTcWaitCycles);
                     if (!ok || abort_flag) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = in_s + (nin % kWgInSlots) * kWgSlot;
-                    const uint32_t b0 = dy_s + wg_dy_slot(t0 + i + 2) * kWgCopy;  // rows r + 1, r, r - 1
+                    // B: rows r + 1, r, r - 1 in slots last, last + 1, last + 2 (mirrored past the end)
+                    const uint64_t ao = (uint64_t)(((uint32_t)isl * kWgSlot) >> 4);
+                    const uint64_t bo = (uint64_t)(((uint32_t)last * kWgCopy) >> 4);
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks)
-                        umma_f16_mn(tmem, sw64_mn_desc(a0 + ks * 1024, kWgCopy), sw64_mn_desc(b0 + ks * 1024, kWgCopy),
-                                    (first && ks == 0) ? 0u : 1u);
+                        umma_f16_mn(tmem, ad[ks] + ao, bd[ks] + bo, (first && ks == 0) ? 0u : 1u);
                     first = false;
-                    umma_commit(smem_addr(&in_empty[nin % kWgInSlots]));
-                    ++nin;
-                    umma_commit(smem_addr(&dy_empty[wg_dy_slot(t0 + i)]));  // leaves the window
+                    umma_commit(smem_addr(&in_empty[isl]));
+                    if (++isl == kWgInSlots) {
+                        isl = 0;
+                        ipar ^= 1u;
+                    }
+                    // stream row t0 + i leaves the window: two rows behind the last
+                    umma_commit(smem_addr(&dy_empty[last + 2 < kWgDySlots ? last + 2 : last + 2 - kWgDySlots]));
                 }
                 if (!ok) break;
                 // the window's last two rows are free as well
-                umma_commit(smem_addr(&dy_empty[wg_dy_slot(t0 + n_out + 2)]));
-                umma_commit(smem_addr(&dy_empty[wg_dy_slot(t0 + n_out + 3)]));
-                ndy = t0 + n_out + 4;
+                umma_commit(smem_addr(&dy_empty[last]));
+                umma_commit(smem_addr(&dy_empty[last + 1 < kWgDySlots ? last + 1 : 0]));
             }
             if (!ok) abort_flag = 1;
             // every MMA issued completes before the epilogue reads or the memory is freed
