@@ -7,7 +7,7 @@
 
 namespace lbm {
 
-constexpr long long kWaitSpins = 1ll << 26;  // polls before a spin-bounded wait gives up
+constexpr long long kWaitCycles = 4000000000ll;  // SM clock cycles before a cycle-bounded wait gives up (about 2 s)
 
 __device__ inline uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -42,14 +42,6 @@ __device__ inline void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, u
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
-}
-
-// bounded wait; false on timeout
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity)
-{
-    for (long long i = 0; i < kWaitSpins; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
 }
 
 // one try that suspends the thread in hardware until the phase completes or

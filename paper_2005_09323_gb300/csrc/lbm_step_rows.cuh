@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) step_rows_kernel(const StepPar
         int k = 0, issued_last = -1;
         for (int item = blockIdx.x; item < items; item += gridDim.x, ++k) {
             const int s = k % stages;
-            if (k >= stages && !mbar_wait(smem_addr(&empty[s]), (uint32_t)(((k / stages) - 1) & 1))) {
+            if (k >= stages && !mbar_wait_cycles(smem_addr(&empty[s]), (uint32_t)(((k / stages) - 1) & 1), kWaitCycles)) {
                 if (p.err_flag) atomicExch(p.err_flag, 1);
                 abort_flag = 1;
                 break;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) step_rows_kernel(const StepPar
         }
         // the block's shared memory must outlive every copy issued into it
         for (int kk = issued_last - stages + 1 > 0 ? issued_last - stages + 1 : 0; kk <= issued_last; ++kk)
-            mbar_wait(smem_addr(&full[kk % stages]), (uint32_t)((kk / stages) & 1));
+            mbar_wait_cycles(smem_addr(&full[kk % stages]), (uint32_t)((kk / stages) & 1), kWaitCycles);
         return;
     }
 
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kRowThreads, 2) step_rows_kernel(const StepPar
     int k = 0;
     for (int item = blockIdx.x; item < items; item += gridDim.x, ++k) {
         const int s = k % stages;
-        if (!mbar_wait(smem_addr(&full[s]), (uint32_t)((k / stages) & 1))) {
+        if (!mbar_wait_cycles(smem_addr(&full[s]), (uint32_t)((k / stages) & 1), kWaitCycles)) {
             if (p.err_flag) atomicExch(p.err_flag, 1);
             abort_flag = 1;
         }
