@@ -533,19 +533,20 @@ __global__ void __launch_bounds__(kRowThreads, 1)
             int i = 0, bi = 0;
             uint32_t fpar = 0, dround = 0;  // full's phase parity; passes over the accumulators
             for (int sq = 0; sq < n_in; ++sq) {
+                // a failed wait elsewhere ends this loop through a failed wait here
                 if (!mbar_wait_cycles(smem_addr(&full[i]), fpar, kTcWaitCycles) ||
                     (sq >= kRowBufs && !mbar_wait_cycles(smem_addr(&dfree[bi]), (dround - 1u) & 1u, kTcWaitCycles))) {
                     abort_flag = 1;
                     break;
                 }
-                if (abort_flag) break;
                 tc_fence_after();
                 const uint64_t so = (uint64_t)(((uint32_t)i * kSlotBytes) >> 4);
                 const uint32_t d = tmem + (uint32_t)(bi * 128);
 #pragma unroll
                 for (int j = 0; j < 6; ++j) umma_f16_n96(d, ad[j] + so, bd[j], j != 0);
-                umma_commit(smem_addr(&dfull[bi]));  // D_s ready for the epilogue
-                umma_commit(smem_addr(&empty[i]));   // input slot free
+                // D_s ready for the epilogue, which also frees the input slot: a
+                // commit costs the issuing thread about as much as two MMAs
+                umma_commit(smem_addr(&dfull[bi]));
                 if (++i == kRowSlots) {
                     i = 0;
                     fpar ^= 1u;
@@ -583,6 +584,16 @@ __global__ void __launch_bounds__(kRowThreads, 1)
                 }
             if (abort_flag) return false;
             tc_fence_after();
+            // the MMAs of input rows sq[0..2] are complete: free the input slot of
+            // the last (each input row is some output row's sq[2], but for the
+            // two rows before a run's first, which its first output row frees)
+            if (q == 0 && lane == 0) {
+                mbar_arrive(smem_addr(&empty[(int)(sq[2] % kRowSlots)]));
+                if (y == ya) {
+                    mbar_arrive(smem_addr(&empty[(int)(sq[0] % kRowSlots)]));
+                    mbar_arrive(smem_addr(&empty[(int)(sq[1] % kRowSlots)]));
+                }
+            }
             uint32_t r[32], t[32];
             tmem_ld32(lane_addr + (uint32_t)((sq[0] % kRowBufs) * 128), r);
 #pragma unroll
@@ -695,6 +706,7 @@ constexpr int kWgDySlots = 6;               // output-gradient ring (plus two mi
 constexpr uint32_t kWgCopy = 128 * 64;      // one 128-pixel row of 32 channels
 constexpr uint32_t kWgSlot = 4 * kWgCopy;   // three x-shifted copies and the constant plane
 constexpr uint32_t kWgCols = 128;           // tensor-memory columns (power of 2; 96 used)
+constexpr int kWgDoneRing = 4;              // row-completion barriers (more than kWgInSlots)
 constexpr int kWgZeroRow = -64;             // a row far outside any image: TMA fills zeros
 // kind::f16, FP32 accumulate, BF16 A and B, both MN-major (bits 15, 16), N = 96, M = 128
 constexpr uint32_t kIdescMN =
@@ -750,6 +762,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     __shared__ __align__(8) uint64_t in_empty[kWgInSlots];
     __shared__ __align__(8) uint64_t dy_full[kWgDySlots];
     __shared__ __align__(8) uint64_t dy_empty[kWgDySlots];
+    __shared__ __align__(8) uint64_t row_done[kWgDoneRing];
     __shared__ __align__(8) uint64_t done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
@@ -777,6 +790,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             mbar_init(smem_addr(&dy_full[k]), 1);
             mbar_init(smem_addr(&dy_empty[k]), 1);
         }
+        for (int k = 0; k < kWgDoneRing; ++k) mbar_init(smem_addr(&row_done[k]), 1);
         mbar_init(smem_addr(&done), 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -857,6 +871,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 bd[ks] = sw64_mn_desc(dy_s + ks * 1024, kWgCopy);
             }
             int isl = 0, tm = 0, last = 0;  // input slot; stream row mod kWgDySlots; slot of the last row waited for
+            int dr = 0;                     // row_done slot of this input row
             uint32_t ipar = 0, tpar = 0;
             bool first = true, ok = true;
             for (int u = blockIdx.x; u < sh.n_units && ok && !abort_flag; u += gridDim.x) {
@@ -886,18 +901,15 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                     for (int ks = 0; ks < 8; ++ks)
                         umma_f16_mn(tmem, ad[ks] + ao, bd[ks] + bo, (first && ks == 0) ? 0u : 1u);
                     first = false;
-                    umma_commit(smem_addr(&in_empty[isl]));
+                    // one commit a row (it costs the issuing thread about as much as
+                    // two MMAs); the relay thread frees the slots this row read
+                    umma_commit(smem_addr(&row_done[dr]));
+                    if (++dr == kWgDoneRing) dr = 0;
                     if (++isl == kWgInSlots) {
                         isl = 0;
                         ipar ^= 1u;
                     }
-                    // stream row t0 + i leaves the window: two rows behind the last
-                    umma_commit(smem_addr(&dy_empty[last + 2 < kWgDySlots ? last + 2 : last + 2 - kWgDySlots]));
                 }
-                if (!ok) break;
-                // the window's last two rows are free as well
-                umma_commit(smem_addr(&dy_empty[last]));
-                umma_commit(smem_addr(&dy_empty[last + 1 < kWgDySlots ? last + 1 : 0]));
             }
             if (!ok) abort_flag = 1;
             // every MMA issued completes before the epilogue reads or the memory is freed
@@ -905,6 +917,41 @@ __global__ void __launch_bounds__(kWgThreads, 1)
         }
         __syncwarp();
     } else {
+        // ---------------- relay: one thread follows the input rows in the MMA
+        // issuer's order and, as each row's MMAs complete, frees its input slot
+        // and the output-gradient row that leaves the window (at a unit's last
+        // row also the window's last two).  The issuer runs at most kWgInSlots
+        // rows ahead of it, so a row_done barrier is never a phase ahead of it.
+        if (warp == 2 && lane == 0) {
+            int isl = 0, tm = 0, dr = 0;  // as in the issuer
+            uint32_t dpar = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < sh.n_units && ok; u += gridDim.x) {
+                int b, y0, y1, x0;
+                wg_unit(sh, u, b, y0, y1, x0);
+                const int n_out = y1 - y0;
+                for (int i = 0; i < n_out + 2 && ok; ++i) {
+                    ok = mbar_wait_cycles(smem_addr(&row_done[dr]), dpar, kTcWaitCycles);
+                    if (!ok) break;
+                    if (++dr == kWgDoneRing) {
+                        dr = 0;
+                        dpar ^= 1u;
+                    }
+                    mbar_arrive(smem_addr(&in_empty[isl]));
+                    if (++isl == kWgInSlots) isl = 0;
+                    // stream row t0 + i (slot kWgDySlots - 1 - (t0 + i) mod kWgDySlots)
+                    mbar_arrive(smem_addr(&dy_empty[kWgDySlots - 1 - tm]));
+                    if (++tm == kWgDySlots) tm = 0;
+                }
+                if (!ok) break;
+                for (int k = 0; k < 2; ++k) {  // stream rows t0 + n_out + 2, t0 + n_out + 3
+                    mbar_arrive(smem_addr(&dy_empty[kWgDySlots - 1 - tm]));
+                    if (++tm == kWgDySlots) tm = 0;
+                }
+            }
+            if (!ok) abort_flag = 1;
+        }
+        __syncwarp();
         // ---------------- epilogue: warp w reads tensor-memory lanes 32 (w % 4) ..
         const int q = warp & 3, m = 32 * q + lane;
         float* out = partial + (int64_t)blockIdx.x * 32 * 304;
