@@ -40,6 +40,7 @@ constexpr int kC = 32;                     // channels of every hidden layer
 constexpr int kCin0 = 8;                   // input channels (3 fields + 5 zeros)
 constexpr int kLayers = 4;
 constexpr int kWgradBlocks = 608;          // 4 per SM on 152 SMs
+constexpr int kInputConvBlocks = 1216;     // 8 per SM on 152 SMs
 
 __host__ __device__ constexpr int kpad_fwd(int cin) { return cin == 32 ? 304 : 80; }
 
@@ -207,6 +208,139 @@ __global__ void __launch_bounds__(128) conv3x3_kernel(const bf16* __restrict__ x
                 *reinterpret_cast<__nv_bfloat162*>(out + o) = __floats2bfloat162_rn(v0, v1);
             }
         }
+    }
+}
+
+// 16 bytes global -> shared through L2 (cp.async); src_bytes = 0 fills zeros
+__device__ inline void cp_async16(void* dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// The input layer's forward pass: out = ReLU(conv3x3(x, w) + bias) from the
+// 8-channel input (three fields and five zero channels).  It moves 16 B in and
+// 64 B out per pixel for 2 x 80 x 32 FLOP, so HBM bounds it.  Persistent
+// blocks stage the weights once, fetch the next tile's halo with cp.async while
+// the current tile is computed, and stage each output tile in shared memory
+// (80-byte pixel stride: the fragment writes are free of bank conflicts) so
+// that it leaves as whole 512-byte runs of 16-byte stores.
+constexpr int kOutStride = kC + 8;  // elements per pixel of the staged output tile
+
+__global__ void __launch_bounds__(128, 8) input_conv_kernel(const bf16* __restrict__ x, const bf16* __restrict__ w,
+                                                         bf16* __restrict__ out, int B, int H, int W)
+{
+    constexpr int CIN = kCin0, KP = kpad_fwd(kCin0), KS = KP + 8, NSTEP = KP / 16;
+    __shared__ __align__(16) bf16 s_in[2][kHPix * CIN];
+    __shared__ __align__(16) bf16 s_w[kC * KS];
+    __shared__ __align__(16) bf16 s_out[kTH * kTW * kOutStride];
+    const int tiles_x = W / kTW, tiles_y = H / kTH;
+    const int total = B * tiles_x * tiles_y;
+    for (int i = threadIdx.x; i < kC * KP / 8; i += blockDim.x) {
+        const int co = i / (KP / 8), kc = i - co * (KP / 8);
+        *reinterpret_cast<uint4*>(s_w + co * KS + kc * 8) = *reinterpret_cast<const uint4*>(w + co * KP + kc * 8);
+    }
+    auto origin = [&](int tile, int& b, int& ty0, int& tx0) {
+        b = tile / (tiles_x * tiles_y);
+        const int rem = tile - b * tiles_x * tiles_y;
+        ty0 = (rem / tiles_x) * kTH;
+        tx0 = (rem - (rem / tiles_x) * tiles_x) * kTW;
+    };
+    // the halo of a tile into buffer buf: one 16-byte pixel per copy, zeros outside the image
+    auto fetch = [&](int tile, int buf) {
+        int b, ty0, tx0;
+        origin(tile, b, ty0, tx0);
+        for (int pix = threadIdx.x; pix < kHPix; pix += blockDim.x) {
+            const int hr = pix / kHW, hc = pix - hr * kHW;
+            const int gy = ty0 + hr - 1, gx = tx0 + hc - 1;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            const bf16* src = in ? x + (((int64_t)b * H + gy) * W + gx) * CIN : x;
+            cp_async16(s_in[buf] + pix * CIN, src, in ? 16u : 0u);
+        }
+        cp_async_commit();
+    };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int arow = (lane & 7) + ((lane >> 3) & 1) * 8;
+    const int akh = lane >> 4;
+    const int bn = (lane >> 4) * 8 + (lane & 7);
+    const int bkh = (lane >> 3) & 1;
+
+    if ((int)blockIdx.x < total) fetch(blockIdx.x, 0);
+    for (int tile = blockIdx.x, k = 0; tile < total; tile += gridDim.x, ++k) {
+        const int buf = k & 1;
+        if (tile + (int)gridDim.x < total) {
+            fetch(tile + gridDim.x, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // this tile's halo (and, the first time, the weights) is in place
+        const bf16* si = s_in[buf];
+        float acc[2][4][4];
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[m][n][r] = 0.f;
+#pragma unroll
+        for (int st = 0; st < NSTEP; ++st) {
+            uint32_t a[2][4];
+            int pos = 2 * st + akh;
+            if (pos > 8) pos = 8;  // the bias half of the last step is set below
+            const int ky = pos / 3, kx = pos - ky * 3;
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int hpix = (warp * 2 + m + ky) * kHW + arow + kx;
+                ldsm_x4(smem_u32(si + hpix * CIN), a[m][0], a[m][1], a[m][2], a[m][3]);
+            }
+            if (st == NSTEP - 1) {  // k 8..15 of the last step: the bias column, then zeros
+                const uint32_t one = t == 0 ? kBf16One : 0u;
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    a[m][2] = one;
+                    a[m][3] = one;
+                }
+            }
+            uint32_t bfr[4][2];
+#pragma unroll
+            for (int np = 0; np < 2; ++np) {
+                const int co = np * 16 + bn, kk = st * 16 + bkh * 8;
+                ldsm_x4(smem_u32(s_w + co * KS + kk), bfr[2 * np][0], bfr[2 * np][1], bfr[2 * np + 1][0],
+                        bfr[2 * np + 1][1]);
+            }
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int n = 0; n < 4; ++n) mma_bf16(acc[m][n], a[m], bfr[n][0], bfr[n][1]);
+        }
+        // ReLU, BF16, into the staged tile: pixel (row warp*2 + m, column g + 8h)
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int n = 0; n < 4; ++n)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int pix = (warp * 2 + m) * kTW + g + 8 * h;
+                    *reinterpret_cast<__nv_bfloat162*>(s_out + pix * kOutStride + n * 8 + 2 * t) =
+                        __floats2bfloat162_rn(fmaxf(acc[m][n][2 * h], 0.f), fmaxf(acc[m][n][2 * h + 1], 0.f));
+                }
+        __syncthreads();
+        int b, ty0, tx0;
+        origin(tile, b, ty0, tx0);
+#pragma unroll
+        for (int j = 0; j < kTH * kTW * 4 / 128; ++j) {
+            const int i = threadIdx.x + j * 128, pix = i >> 2, c = i & 3;
+            const int gy = ty0 + pix / kTW, gx = tx0 + (pix & (kTW - 1));
+            *reinterpret_cast<uint4*>(out + (((int64_t)b * H + gy) * W + gx) * kC + c * 8) =
+                *reinterpret_cast<const uint4*>(s_out + pix * kOutStride + c * 8);
+        }
+        __syncthreads();  // the staged tile and this halo buffer are free again
     }
 }
 
@@ -586,8 +720,9 @@ int conv32(cnn_model* m, const bf16* x, const bf16* w, const bf16* mask, bf16* o
 
 int forward(cnn_model* m, const bf16* x, int batch, cudaStream_t s)
 {
-    const dim3 grid(m->W / kTW, m->H / kTH, batch);
-    conv3x3_kernel<kCin0, false><<<grid, 128, 0, s>>>(x, m->w[0], nullptr, m->act[0], m->H, m->W);
+    const int tiles = batch * (m->H / kTH) * (m->W / kTW);
+    const int blocks = tiles < kInputConvBlocks ? tiles : kInputConvBlocks;
+    input_conv_kernel<<<blocks, 128, 0, s>>>(x, m->w[0], m->act[0], batch, m->H, m->W);
     LBM_CUDA(cudaGetLastError());
     count_launches(1);
     for (int l = 1; l < kLayers; ++l)
@@ -609,7 +744,11 @@ int wgrad(cnn_model* m, int l, const bf16* x, const bf16* dy, int batch, cudaStr
         if (int rc = conv3x3_wgrad_tc(x, dy, m->wpart, batch, m->H, m->W, m->err, s, &nblk)) return rc;
     } else {
         const int tiles = batch * (m->H / kTH) * (m->W / kTW);
-        nblk = tiles < kWgradBlocks ? tiles : kWgradBlocks;
+        // the input layer's partials (32 x 80) are a quarter of a hidden layer's
+        // (32 x 304), so twice the blocks fit the same buffer: 8 resident per SM,
+        // twice the loads in flight for a kernel bound by their latency
+        const int cap = cin == kC ? kWgradBlocks : 2 * kWgradBlocks;
+        nblk = tiles < cap ? tiles : cap;
         if (cin == kC)
             conv_wgrad_kernel<kC><<<nblk, 128, 0, s>>>(x, dy, batch, m->H, m->W, m->wpart);
         else

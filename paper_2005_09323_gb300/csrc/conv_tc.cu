@@ -352,7 +352,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // barrier, the last reader also for the readers a run edge leaves out (12
 // arrivals a use).
 constexpr int kRowSlots = 12;                         // input-row ring
+constexpr int kRowPairSlots = kRowSlots / 2;          // its pairs (one full / empty barrier each)
 constexpr int kRowBufs = 4;                           // accumulators in tensor memory, 128 columns apart
+constexpr int kRowPairBufs = kRowBufs / 2;            // accumulator pairs (one dfull / dfree barrier each)
 constexpr int kRowEpi = 4;                            // epilogue warpgroups: output rows k = e mod kRowEpi
 constexpr int kRowThreads = 64 + 128 * kRowEpi;
 constexpr uint32_t kRowCols = 512;
@@ -417,6 +419,13 @@ __device__ inline void walk_rows(const RowShape& sh, int64_t g0, int64_t g1, F&&
     }
 }
 
+// input rows a CTA computes D for: its output rows [g0, g1) plus two per run
+// down a column (a run ends where a column does)
+__device__ inline int row_count(const RowShape& sh, int64_t g0, int64_t g1)
+{
+    return g1 > g0 ? (int)(g1 - g0) + 2 * (int)((g1 - 1) / sh.H - g0 / sh.H + 1) : 0;
+}
+
 // stacked weights: for each kx, rows n = 32 ky + co of W[co][3 ky + kx][.],
 // 64-byte swizzled (16-byte chunk c of row n at chunk c ^ ((n >> 1) & 3))
 template <int KS>
@@ -436,10 +445,10 @@ __global__ void __launch_bounds__(kRowThreads, 1)
                     const bf16* __restrict__ mask, bf16* __restrict__ out, const RowShape sh, int32_t* err)
 {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kRowSlots];
-    __shared__ __align__(8) uint64_t empty[kRowSlots];
-    __shared__ __align__(8) uint64_t dfull[kRowBufs];
-    __shared__ __align__(8) uint64_t dfree[kRowBufs];
+    __shared__ __align__(8) uint64_t full[kRowPairSlots];   // per pair of input rows
+    __shared__ __align__(8) uint64_t empty[kRowPairSlots];
+    __shared__ __align__(8) uint64_t dfull[kRowPairBufs];   // per pair of accumulators
+    __shared__ __align__(8) uint64_t dfree[kRowPairBufs];
     __shared__ __align__(8) uint64_t done;
     __shared__ uint32_t tmem_slot;
     __shared__ float bias_s[32];
@@ -456,13 +465,13 @@ __global__ void __launch_bounds__(kRowThreads, 1)
     stage_stacked_weights<KS>(smem, w, kRowThreads);
     if (!BWD && threadIdx.x < 32) bias_s[threadIdx.x] = __bfloat162float(w[threadIdx.x * KS + 288]);
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kRowSlots; ++i) {
+        for (int i = 0; i < kRowPairSlots; ++i) {
             mbar_init(smem_addr(&full[i]), 1);
-            mbar_init(smem_addr(&empty[i]), 1);
+            mbar_init(smem_addr(&empty[i]), 2);  // one arrival per input row of the pair
         }
-        for (int i = 0; i < kRowBufs; ++i) {
+        for (int i = 0; i < kRowPairBufs; ++i) {
             mbar_init(smem_addr(&dfull[i]), 1);
-            mbar_init(smem_addr(&dfree[i]), 12);
+            mbar_init(smem_addr(&dfree[i]), 24);  // 3 readers x 4 warps per accumulator
         }
         mbar_init(smem_addr(&done), 1);
         abort_flag = 0;
@@ -481,26 +490,29 @@ __global__ void __launch_bounds__(kRowThreads, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0) {
-        // ---------------- TMA producer: input rows in the order the MMAs use them.
-        // The single thread's loop is the pipeline's pace, so its bookkeeping is
-        // 32-bit ring counters (slot, phase) rather than divisions of the row count.
+        // ---------------- TMA producer: input rows in the order the MMAs use them,
+        // in pairs that share a full/empty barrier (the last pair of an odd count
+        // holds one row).  The single thread's loop is the pipeline's pace, so its
+        // bookkeeping is ring counters (pair slot, phase) rather than divisions.
         if (lane == 0) {
-            int n = 0, i = 0;
-            uint32_t par = 0;  // phase parity of the current pass over the slots
+            const int n_in = row_count(sh, g0, g1);
+            int n = 0, ps = 0;
+            uint32_t par = 0;  // phase parity of the current pass over the pair slots
             auto load_row = [&](int b, int yr, int x0) -> bool {
-                if (n >= kRowSlots && !mbar_wait_cycles(smem_addr(&empty[i]), par ^ 1u, kTcWaitCycles)) {
-                    abort_flag = 1;
-                    return false;
+                const uint32_t bar = smem_addr(&full[ps]);
+                if ((n & 1) == 0) {  // the first row of a pair claims the pair slot
+                    if (n >= 2 * kRowPairSlots && !mbar_wait_cycles(smem_addr(&empty[ps]), par ^ 1u, kTcWaitCycles)) {
+                        abort_flag = 1;
+                        return false;
+                    }
+                    if (abort_flag) return false;
+                    mbar_expect_tx(bar, n + 1 < n_in ? 2 * kRowBoxBytes : kRowBoxBytes);
                 }
-                if (abort_flag) return false;
-                const uint32_t bar = smem_addr(&full[i]);
-                const uint32_t dst = ring_s + (uint32_t)i * kSlotBytes;
-                mbar_expect_tx(bar, kRowBoxBytes);
+                const uint32_t dst = ring_s + (uint32_t)(2 * ps + (n & 1)) * kSlotBytes;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) tma_load_4d(dst + c * kChunkBytes, &tmap, 8 * c, x0 - 1, yr, b, bar);
-                ++n;
-                if (++i == kRowSlots) {
-                    i = 0;
+                if ((++n & 1) == 0 && ++ps == kRowPairSlots) {
+                    ps = 0;
                     par ^= 1u;
                 }
                 return true;
@@ -509,19 +521,25 @@ __global__ void __launch_bounds__(kRowThreads, 1)
                 if (y == ya && !(load_row(b, y - 1, x0) && load_row(b, y, x0))) return false;
                 return load_row(b, y + 1, x0);
             });
-            for (int k = n - kRowSlots > 0 ? n - kRowSlots : 0; k < n; ++k)
-                mbar_wait_cycles(smem_addr(&full[k % kRowSlots]), (uint32_t)((k / kRowSlots) & 1), kTcWaitCycles);
+            const int np = (n + 1) >> 1;  // pairs issued
+            for (int k = np - kRowPairSlots > 0 ? np - kRowPairSlots : 0; k < np; ++k)
+                mbar_wait_cycles(smem_addr(&full[k % kRowPairSlots]), (uint32_t)((k / kRowPairSlots) & 1),
+                                 kTcWaitCycles);
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ---------------- MMA issuer: D_s for every input row s, in order.  The
-        // input rows are the output rows plus two per run down a column; their
-        // MMAs do not depend on which output row they serve, so the loop is a
-        // plain count with ring counters, and the descriptors of slot i are those
-        // of slot 0 advanced by i slots (the start-address field holds address /
-        // 16 in 14 bits, which no shared-memory address overflows).
+        // ---------------- MMA issuer: D_s for every input row s, in order, two
+        // rows an iteration.  The issuing thread's loop is the layer's pace: a
+        // barrier wait, a commit and the loop cost it about as much as the six
+        // MMAs of a row, so each iteration waits once for a pair of input rows
+        // and a pair of accumulators and commits once.  The input rows are the
+        // output rows plus two per run down a column; their MMAs do not depend on
+        // which output row they serve, so the loop is a plain count, and the
+        // descriptors of slot i are those of slot 0 advanced by i slots (the
+        // start-address field holds address / 16 in 14 bits, which no
+        // shared-memory address overflows).
         if (lane == 0) {
-            const int n_in = g1 > g0 ? (int)(g1 - g0) + 2 * (int)((g1 - 1) / sh.H - g0 / sh.H + 1) : 0;
+            const int n_in = row_count(sh, g0, g1);
             uint64_t ad[6], bd[6];
 #pragma unroll
             for (int kx = 0; kx < 3; ++kx)
@@ -530,29 +548,32 @@ __global__ void __launch_bounds__(kRowThreads, 1)
                     ad[2 * kx + ks] = interleave_desc(ring_s + 2 * ks * kChunkBytes + 16 * kx, kChunkBytes, 128);
                     bd[2 * kx + ks] = sw64_desc(w_s + kx * kStackBytes + ks * 32);
                 }
-            int i = 0, bi = 0;
-            uint32_t fpar = 0, dround = 0;  // full's phase parity; passes over the accumulators
-            for (int sq = 0; sq < n_in; ++sq) {
+            int ps = 0, pb = 0;
+            uint32_t fpar = 0, dround = 0;  // full's phase parity; passes over the accumulator pairs
+            for (int sq = 0; sq < n_in; sq += 2) {
                 // a failed wait elsewhere ends this loop through a failed wait here
-                if (!mbar_wait_cycles(smem_addr(&full[i]), fpar, kTcWaitCycles) ||
-                    (sq >= kRowBufs && !mbar_wait_cycles(smem_addr(&dfree[bi]), (dround - 1u) & 1u, kTcWaitCycles))) {
+                if (!mbar_wait_cycles(smem_addr(&full[ps]), fpar, kTcWaitCycles) ||
+                    (sq >= 2 * kRowPairBufs &&
+                     !mbar_wait_cycles(smem_addr(&dfree[pb]), (dround - 1u) & 1u, kTcWaitCycles))) {
                     abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint64_t so = (uint64_t)(((uint32_t)i * kSlotBytes) >> 4);
-                const uint32_t d = tmem + (uint32_t)(bi * 128);
+                const int rows = sq + 1 < n_in ? 2 : 1;
+                for (int r = 0; r < rows; ++r) {
+                    const uint64_t so = (uint64_t)(((uint32_t)(2 * ps + r) * kSlotBytes) >> 4);
+                    const uint32_t d = tmem + (uint32_t)((2 * pb + r) * 128);
 #pragma unroll
-                for (int j = 0; j < 6; ++j) umma_f16_n96(d, ad[j] + so, bd[j], j != 0);
-                // D_s ready for the epilogue, which also frees the input slot: a
-                // commit costs the issuing thread about as much as two MMAs
-                umma_commit(smem_addr(&dfull[bi]));
-                if (++i == kRowSlots) {
-                    i = 0;
+                    for (int j = 0; j < 6; ++j) umma_f16_n96(d, ad[j] + so, bd[j], j != 0);
+                }
+                // both D ready for the epilogue, which also frees the input slots
+                umma_commit(smem_addr(&dfull[pb]));
+                if (++ps == kRowPairSlots) {
+                    ps = 0;
                     fpar ^= 1u;
                 }
-                if (++bi == kRowBufs) {
-                    bi = 0;
+                if (++pb == kRowPairBufs) {
+                    pb = 0;
                     ++dround;
                 }
             }
@@ -576,22 +597,25 @@ __global__ void __launch_bounds__(kRowThreads, 1)
             const int64_t sq[3] = {n - 2, n - 1, n};  // input rows y - 1, y, y + 1
             ++n;
             if (k++ % kRowEpi != e) return true;
-            for (int j = 0; j < 3; ++j)
-                if (!mbar_wait_cycles(smem_addr(&dfull[sq[j] % kRowBufs]), (uint32_t)((sq[j] / kRowBufs) & 1),
+            // the pairs of input rows sq[0..2] (D of pair p in accumulator pair p mod 2)
+            for (int j = 0; j < 3; ++j) {
+                const int64_t pr = sq[j] >> 1;
+                if (!mbar_wait_cycles(smem_addr(&dfull[pr % kRowPairBufs]), (uint32_t)((pr / kRowPairBufs) & 1),
                                       kTcWaitCycles)) {
                     abort_flag = 1;
                     return false;
                 }
+            }
             if (abort_flag) return false;
             tc_fence_after();
             // the MMAs of input rows sq[0..2] are complete: free the input slot of
             // the last (each input row is some output row's sq[2], but for the
             // two rows before a run's first, which its first output row frees)
             if (q == 0 && lane == 0) {
-                mbar_arrive(smem_addr(&empty[(int)(sq[2] % kRowSlots)]));
+                mbar_arrive(smem_addr(&empty[(int)((sq[2] >> 1) % kRowPairSlots)]));
                 if (y == ya) {
-                    mbar_arrive(smem_addr(&empty[(int)(sq[0] % kRowSlots)]));
-                    mbar_arrive(smem_addr(&empty[(int)(sq[1] % kRowSlots)]));
+                    mbar_arrive(smem_addr(&empty[(int)((sq[0] >> 1) % kRowPairSlots)]));
+                    mbar_arrive(smem_addr(&empty[(int)((sq[1] >> 1) % kRowPairSlots)]));
                 }
             }
             uint32_t r[32], t[32];
@@ -609,13 +633,13 @@ __global__ void __launch_bounds__(kRowThreads, 1)
                 // readers of input row y - 1: output rows y - 2 .. y within the run;
                 // this row is its last, so it also arrives for the readers outside
                 const uint32_t users_m1 = (uint32_t)(y - (y - 2 > ya ? y - 2 : ya) + 1);
-                mbar_arrive_n(smem_addr(&dfree[sq[0] % kRowBufs]), 4 - users_m1);
+                mbar_arrive_n(smem_addr(&dfree[(sq[0] >> 1) % kRowPairBufs]), 4 - users_m1);
                 if (y == yb) {  // input rows y and y + 1 are read by no later row of the run
-                    mbar_arrive_n(smem_addr(&dfree[sq[1] % kRowBufs]), y > ya ? 2u : 3u);
-                    mbar_arrive_n(smem_addr(&dfree[sq[2] % kRowBufs]), 3);
+                    mbar_arrive_n(smem_addr(&dfree[(sq[1] >> 1) % kRowPairBufs]), y > ya ? 2u : 3u);
+                    mbar_arrive_n(smem_addr(&dfree[(sq[2] >> 1) % kRowPairBufs]), 3);
                 } else {
-                    mbar_arrive_n(smem_addr(&dfree[sq[1] % kRowBufs]), 1);
-                    mbar_arrive_n(smem_addr(&dfree[sq[2] % kRowBufs]), 1);
+                    mbar_arrive_n(smem_addr(&dfree[(sq[1] >> 1) % kRowPairBufs]), 1);
+                    mbar_arrive_n(smem_addr(&dfree[(sq[2] >> 1) % kRowPairBufs]), 1);
                 }
             }
             epilogue_pixel<BWD>(r, bias_s, mask, out, (((int64_t)b * sh.H + y) * sh.W + x0 + m) * 32);
