@@ -784,7 +784,6 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t in_full[kWgInSlots];
     __shared__ __align__(8) uint64_t in_empty[kWgInSlots];
-    __shared__ __align__(8) uint64_t dy_full[kWgDySlots];
     __shared__ __align__(8) uint64_t dy_empty[kWgDySlots];
     __shared__ __align__(8) uint64_t row_done[kWgDoneRing];
     __shared__ __align__(8) uint64_t done;
@@ -810,10 +809,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             mbar_init(smem_addr(&in_full[k]), 1);
             mbar_init(smem_addr(&in_empty[k]), 1);
         }
-        for (int k = 0; k < kWgDySlots; ++k) {
-            mbar_init(smem_addr(&dy_full[k]), 1);
-            mbar_init(smem_addr(&dy_empty[k]), 1);
-        }
+        for (int k = 0; k < kWgDySlots; ++k) mbar_init(smem_addr(&dy_empty[k]), 1);
         for (int k = 0; k < kWgDoneRing; ++k) mbar_init(smem_addr(&row_done[k]), 1);
         mbar_init(smem_addr(&done), 1);
         abort_flag = 0;
@@ -834,51 +830,57 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer.  Per unit the stream of output-
         // gradient rows is: zero, zero, dy rows y0 .. y1 - 1, zero, zero; input
-        // row i (r = y0 - 1 + i) is issued after stream row i + 2, which its
-        // window (stream rows i .. i + 2) needs last.
+        // row i (r = y0 - 1 + i) needs stream rows i .. i + 2.  The stream rows an
+        // input row needs first (three for the unit's first, then one) complete
+        // on that input row's barrier with its own copies, so that the MMA
+        // issuer waits once a row: its shared-memory accesses queue behind the
+        // tensor core's operand reads and cost it about as much as three MMAs.
         if (lane == 0) {
             int nin = 0, ndy = 0;
-            auto issue_dy = [&](int y, int b, int x0) -> bool {
-                const int sl = wg_dy_slot(ndy);
-                if (ndy >= kWgDySlots &&
-                    !mbar_wait_cycles(smem_addr(&dy_empty[sl]), ((ndy / kWgDySlots) - 1) & 1, kTcWaitCycles))
-                    return false;
-                const uint32_t bar = smem_addr(&dy_full[sl]);
-                const bool mirror = sl < 2;
-                mbar_expect_tx(bar, mirror ? 2 * kWgCopy : kWgCopy);
-                tma_load_4d(dy_s + sl * kWgCopy, &dymap, 0, x0, y, b, bar);
-                if (mirror) tma_load_4d(dy_s + (kWgDySlots + sl) * kWgCopy, &dymap, 0, x0, y, b, bar);
-                ++ndy;
-                return true;
-            };
-            for (int u = blockIdx.x; u < sh.n_units && !abort_flag; u += gridDim.x) {
+            bool ok = true;
+            for (int u = blockIdx.x; u < sh.n_units && ok; u += gridDim.x) {
                 int b, y0, y1, x0;
                 wg_unit(sh, u, b, y0, y1, x0);
                 const int n_out = y1 - y0;
-                bool ok = issue_dy(kWgZeroRow, b, x0) && issue_dy(kWgZeroRow, b, x0);
                 for (int i = 0; i < n_out + 2 && ok; ++i) {
-                    ok = issue_dy(i < n_out ? y0 + i : kWgZeroRow, b, x0);
-                    if (!ok) break;
+                    // claim the slots: the input row's, then its new stream rows'
                     const int sl = nin % kWgInSlots;
                     if (nin >= kWgInSlots &&
                         !mbar_wait_cycles(smem_addr(&in_empty[sl]), ((nin / kWgInSlots) - 1) & 1, kTcWaitCycles)) {
                         ok = false;
                         break;
                     }
+                    const int n_new = i == 0 ? 3 : 1;
+                    uint32_t bytes = 3 * kWgCopy;
+                    for (int k = 0; k < n_new && ok; ++k) {
+                        const int t = ndy + k, dsl = wg_dy_slot(t);
+                        if (t >= kWgDySlots &&
+                            !mbar_wait_cycles(smem_addr(&dy_empty[dsl]), ((t / kWgDySlots) - 1) & 1, kTcWaitCycles))
+                            ok = false;
+                        bytes += dsl < 2 ? 2 * kWgCopy : kWgCopy;  // slots 0 and 1 are mirrored past the end
+                    }
+                    if (!ok) break;
                     const uint32_t bar = smem_addr(&in_full[sl]);
-                    mbar_expect_tx(bar, 3 * kWgCopy);
+                    mbar_expect_tx(bar, bytes);
+                    for (int k = 0; k < n_new; ++k) {
+                        // stream row i + 2 - (n_new - 1 - k): zero rows before and after the band
+                        const int srow = i + 2 - (n_new - 1 - k);
+                        const int y = srow >= 2 && srow - 2 < n_out ? y0 + srow - 2 : kWgZeroRow;
+                        const int dsl = wg_dy_slot(ndy);
+                        tma_load_4d(dy_s + dsl * kWgCopy, &dymap, 0, x0, y, b, bar);
+                        if (dsl < 2) tma_load_4d(dy_s + (kWgDySlots + dsl) * kWgCopy, &dymap, 0, x0, y, b, bar);
+                        ++ndy;
+                    }
 #pragma unroll
                     for (int kx = 0; kx < 3; ++kx)
                         tma_load_4d(in_s + sl * kWgSlot + kx * kWgCopy, &xmap, 0, x0 + kx - 1, y0 - 1 + i, b, bar);
                     ++nin;
                 }
-                if (!ok) abort_flag = 1;
             }
+            if (!ok) abort_flag = 1;
             // the shared memory must outlive every copy issued into it
             for (int kk = nin - kWgInSlots > 0 ? nin - kWgInSlots : 0; kk < nin; ++kk)
                 mbar_wait_cycles(smem_addr(&in_full[kk % kWgInSlots]), (kk / kWgInSlots) & 1, kTcWaitCycles);
-            for (int kk = ndy - kWgDySlots > 0 ? ndy - kWgDySlots : 0; kk < ndy; ++kk)
-                mbar_wait_cycles(smem_addr(&dy_full[wg_dy_slot(kk)]), (kk / kWgDySlots) & 1, kTcWaitCycles);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -894,25 +896,22 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 ad[ks] = sw64_mn_desc(in_s + ks * 1024, kWgCopy);
                 bd[ks] = sw64_mn_desc(dy_s + ks * 1024, kWgCopy);
             }
-            int isl = 0, tm = 0, last = 0;  // input slot; stream row mod kWgDySlots; slot of the last row waited for
+            int isl = 0, tm = 0, last = 0;  // input slot; stream row mod kWgDySlots; slot of the newest stream row
             int dr = 0;                     // row_done slot of this input row
-            uint32_t ipar = 0, tpar = 0;
+            uint32_t ipar = 0;
             bool first = true, ok = true;
             for (int u = blockIdx.x; u < sh.n_units && ok && !abort_flag; u += gridDim.x) {
                 int b, y0, y1, x0;
                 wg_unit(sh, u, b, y0, y1, x0);
                 const int n_out = y1 - y0;
                 for (int i = 0; i < n_out + 2 && ok; ++i) {
-                    // stream rows up to t0 + i + 2: three for the unit's first input row, then one
-                    for (int k = i == 0 ? 3 : 1; k > 0 && ok; --k) {
+                    // stream rows up to t0 + i + 2 (three new for the unit's first input
+                    // row, then one) arrive on the input row's own barrier
+                    for (int k = i == 0 ? 3 : 1; k > 0; --k) {
                         last = kWgDySlots - 1 - tm;
-                        ok = mbar_wait_cycles(smem_addr(&dy_full[last]), tpar, kTcWaitCycles);
-                        if (++tm == kWgDySlots) {
-                            tm = 0;
-                            tpar ^= 1u;
-                        }
+                        if (++tm == kWgDySlots) tm = 0;
                     }
-                    if (ok) ok = mbar_wait_cycles(smem_addr(&in_full[isl]), ipar, kTcWaitCycles);
+                    ok = mbar_wait_cycles(smem_addr(&in_full[isl]), ipar, kTcWaitCycles);
                     if (!ok || abort_flag) {
                         ok = false;
                         break;
