@@ -940,7 +940,8 @@ def run_ams_branch(args):
     the AMS workload with a checkpoint every 250 steps, taken in turn from a
     pool of 16 trajectories; timed with step-chunk graphs (the default) and
     with one direct launch per lattice step.  --ams-channel open: the same on
-    one trajectory of the open channel of Sec. 2 (two launches per step)."""
+    one trajectory of the open channel of Sec. 2 (its outlet column written by a
+    second kernel at the end of each chunk)."""
     import torch
 
     from paper_2005_09323_gb300 import lbmrare as L
