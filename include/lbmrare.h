@@ -236,6 +236,29 @@ int lbm_ensemble_moments(lbm_ensemble* e, double* mass, double* px, double* py);
 int lbm_ensemble_get_populations(lbm_ensemble* e, int32_t clone, double* host);
 int lbm_ensemble_set_populations(lbm_ensemble* e, int32_t clone, const double* host);
 
+/* Run resume.  No passage of the paper defines it: it lets a long direct-
+ * sampling run (Sec. 3) or a GKTL loop driven step by step (App. C.1) stop and
+ * continue in a later process.
+ * lbm_ensemble_save writes the ensemble's run state into the caller-owned host
+ * buffer dst of capacity bytes: a versioned header with the configuration,
+ * then each clone's time and current populations in the storage format, the
+ * drag history up to the latest clone time (and the observables' history when
+ * enabled), the App. D snapshot bank with its masses, and the AMS checkpoints
+ * up to the latest clone time.  *bytes receives the size the state needs;
+ * dst = NULL only reports it.  Waits.  Errors: LBM_ERR_ARG (null e or bytes,
+ * capacity too small; nothing written).
+ * lbm_ensemble_load overwrites ensemble e with a state written by
+ * lbm_ensemble_save.  e must have been created with the same configuration
+ * (every lbm_config field equal) and clone count, and with observables enabled
+ * exactly when the saved ensemble had them; its seed becomes the saved one.
+ * An attached learned score is not part of the state: attach it after loading
+ * (LBM_ERR_STATE otherwise).  The loaded ensemble continues bit for bit as the
+ * saved one would have.  Waits.  Errors: LBM_ERR_ARG (not a saved state,
+ * another version, size, configuration or layout; nothing changed),
+ * LBM_ERR_STATE, LBM_ERR_CUDA. */
+int lbm_ensemble_save(lbm_ensemble* e, void* dst, uint64_t capacity, uint64_t* bytes);
+int lbm_ensemble_load(lbm_ensemble* e, const void* src, uint64_t bytes);
+
 /* Pick the fastest compiled variant of the fused step (sites per thread, warps
  * per block) for this ensemble by timing each on its own state; the state and
  * the drag history are left unchanged.  *variant (may be NULL) gets the index. */

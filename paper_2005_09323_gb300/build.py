@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(PKG, "lib")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "liblbmrare.so")
 
-SOURCES = ["lbm_ensemble.cu", "selection.cu", "step_fp32.cu", "step_fp16.cu", "step_bf16.cu", "step_open_fp32.cu", "step_open_16.cu", "noalloc.cu", "drivers.cu", "cnn.cu", "conv_tc.cu", "surrogate.cu", "stats.cu", "observables.cu"]
+SOURCES = ["lbm_ensemble.cu", "selection.cu", "step_fp32.cu", "step_fp16.cu", "step_bf16.cu", "step_open_fp32.cu", "step_open_16.cu", "noalloc.cu", "drivers.cu", "cnn.cu", "conv_tc.cu", "surrogate.cu", "stats.cu", "observables.cu", "resume.cu"]
 HEADERS = ["lbm_device.cuh", "lbm_step.cuh", "lbm_step_rows.cuh", "lbm_step_tb.cuh", "async_copy.cuh", "internal.h", "step_params.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "cnn_shape", "cnn_predict", "cnn_fit", "lbm_ensemble_attach_score", "lbm_ensemble_evaluate_score",
     "lbm_ensemble_score_history", "lbm_surrogate_dataset", "lbm_ensemble_set_snapshots_from_checkpoint",
     "lbm_selftest_bounded_wait", "lbm_ensemble_perturb", "lbm_ensemble_set_observables",
-    "lbm_ensemble_observables",
+    "lbm_ensemble_observables", "lbm_ensemble_save", "lbm_ensemble_load",
 ]
 
 
@@ -123,6 +123,8 @@ def lib():
             "lbm_ensemble_moments": ([p, p, p, p], C.c_int),
             "lbm_ensemble_get_populations": ([p, i32, p], C.c_int),
             "lbm_ensemble_set_populations": ([p, i32, p], C.c_int),
+            "lbm_ensemble_save": ([p, p, u64, p], C.c_int),
+            "lbm_ensemble_load": ([p, p, u64], C.c_int),
             "lbm_ensemble_autotune": ([p, p], C.c_int),
             "lbm_ensemble_set_variant": ([p, i32], C.c_int),
             "lbm_step_variant_info": ([i32, p, p, p], C.c_int),
@@ -324,6 +326,21 @@ def lbm_ensemble_get_populations(e, clone: int, nx: int, ny: int) -> np.ndarray:
 def lbm_ensemble_set_populations(e, clone: int, f: np.ndarray):
     f = np.ascontiguousarray(f, dtype=np.float64)
     _check(lib().lbm_ensemble_set_populations(e, clone, _host(f)))
+
+
+def lbm_ensemble_save(e) -> bytes:
+    """The ensemble's run state as a byte string (lbm_ensemble_save)."""
+    n = C.c_uint64(0)
+    _check(lib().lbm_ensemble_save(e, None, 0, C.byref(n)))
+    buf = C.create_string_buffer(max(n.value, 1))
+    _check(lib().lbm_ensemble_save(e, buf, n.value, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def lbm_ensemble_load(e, state: bytes):
+    """Overwrite the ensemble with a state from lbm_ensemble_save."""
+    state = bytes(state)
+    _check(lib().lbm_ensemble_load(e, state, len(state)))
 
 
 def lbm_ensemble_autotune(e) -> int:

@@ -51,6 +51,9 @@ def test_host_argument_checks_need_no_gpu(L):
     assert lib.gktl_select(5000, None, 0, 0, None, None, None) == L.LBM_ERR_ARG
     assert lib.ams_select(0, None, 0, 0, None, None, None, None, None) == L.LBM_ERR_ARG
     assert lib.lbm_ensemble_step(None, 1) == L.LBM_ERR_ARG
+    n = C.c_uint64(7)
+    assert lib.lbm_ensemble_save(None, None, 0, C.byref(n)) == L.LBM_ERR_ARG
+    assert lib.lbm_ensemble_load(None, b"LBMRUN", 6) == L.LBM_ERR_ARG
 
 
 def test_variant_table(L):
