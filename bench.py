@@ -687,7 +687,8 @@ def run_return_time(args):
     seconds per replica x (relative error / 0.2)^2.  The learned score is
     trained on --rt-snapshots states (default 10^5) of a run of its own, with
     the last tenth held out for its R^2.  Every ensemble is autotuned before it
-    is stepped."""
+    is stepped.  --perturbation centred gives every replica the centred App. D
+    coefficients (lbm_ensemble_set_perturbation)."""
     import math
 
     import numpy as np
@@ -746,6 +747,7 @@ def run_return_time(args):
     def replica(storage, k, kappa, learned, seed):
         e = make(storage, seed)
         L.lbm_ensemble_autotune(e)
+        L.lbm_ensemble_set_perturbation(e, args.perturbation == "centred")
         if learned:
             L.lbm_ensemble_attach_score(e, m, factor, rho_s, u_s)
         L.lbm_ensemble_step(e, spin)
@@ -856,6 +858,7 @@ def run_return_time(args):
                                f"{'open channel of Sec. 2' if open_ch else 'periodic channel'}, T_a=T={t_a} steps, "
                                f"cloning every {period} steps, k sigma_I = z for level mean + z sigma of F_T, "
                                f"z = {zs}, eps={EPS}, spin-up {spin} steps", "channel": args.rt_channel,
+                   "perturbation": args.perturbation,
                    "replicas": R, "sigma_I": sd_i, "F_T_mean": mu, "F_T_std": sd},
         "variants": out, "best_variant_at_highest_level": best_name, "credited_variants": credited,
         "direct_P_per_level": p_direct,
@@ -868,6 +871,99 @@ def run_return_time(args):
         "surrogate_training": {"seconds": t_train, "samples": n_tr, "held_out": n_snaps * n - n_tr,
                                "epochs": len(losses), "loss_first_last": [float(losses[0]), float(losses[-1])],
                                "r2_held_out": r2_held_out}}))
+
+
+# ---------------------------------------------------------------- App. D perturbation against direct sampling
+def run_perturbation_bias(args):
+    """GKTL's estimate of P(F_T >= mu + 2 sigma) on the open channel of Sec. 2
+    against direct sampling, for the App. D perturbation as printed
+    (coefficients alpha_n uniform in [0, 1), eps = 0.0002, 0.002, 0.02) and with
+    centred coefficients (alpha_n - 1/2, eps = 0.002, 0.02).
+
+    The set-up of the return-time workload: 64 trajectories of 513 x 129, a
+    15000-step spin-up per replica, T_a = T = 20000 steps, cloning every 1000
+    steps, the App. D bank refilled before each cloning, k sigma_I = 2.  The
+    direct arm (k = 0, seeds 100 + r) gives the level and sigma_I; every GKTL
+    arm runs the replicas of seeds 200 + r (the seeds of the return-time
+    workload's FP32 GKTL at z = 2).  R = max(16, --steps) replicas per arm.
+    The direct standard error is given both binomial (all trajectories
+    independent) and from the spread of the replicas' frequencies."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2005_09323_gb300 import lbmrare as L
+    torch.cuda.set_device(0)
+    L.lib()
+    w = workload(argparse.Namespace(workload="open", clones=args.clones or 64, collision=args.collision))
+    nx, ny, n, obst = w["nx"], w["ny"], w["clones"], w["obst"]
+    chan = dict(channel_kwargs(w), collision=w["collision"])
+    spin, t_a, periods, period, z = 15000, 20000, 20, 1000, 2.0
+    R = max(16, args.steps)
+    stream = torch.cuda.current_stream()
+
+    def replica(k, eps, centred, seed):
+        cfg = L.config(nx, ny, obstacle=obst, max_steps=spin + t_a, n_snapshots=N_SNAP, storage="fp32", **chan)
+        e = L.lbm_ensemble_create(cfg, n, seed, stream)
+        L.lbm_ensemble_autotune(e)
+        L.lbm_ensemble_set_perturbation(e, centred)
+        L.lbm_ensemble_step(e, spin)
+        L.lbm_ensemble_set_snapshots(e, list(range(N_SNAP)))
+        logR = torch.zeros(periods, dtype=torch.float64, device="cuda")
+        parent = torch.zeros(periods * n, dtype=torch.int32, device="cuda")
+        integ = torch.zeros(n, dtype=torch.float64, device="cuda")
+        maxima = torch.zeros(n, dtype=torch.float64, device="cuda")
+        L.lbm_gktl_run(e, period, periods, k, eps, seed, t_a, logR, parent, integ, maxima, refresh_snapshots=True)
+        par = parent.cpu().numpy().reshape(periods, n)
+        anc = np.arange(n)
+        for i in range(periods - 1, -1, -1):
+            anc = par[i][anc]
+        L.lbm_ensemble_destroy(e)
+        return dict(logR=logR, integ=integ, maxima=maxima, ancestors=len(set(anc.tolist())))
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    direct = [replica(0.0, EPS, False, 100 + r) for r in range(R)]
+    F = np.stack([d["maxima"].cpu().numpy() for d in direct])
+    I = np.stack([d["integ"].cpu().numpy() for d in direct])
+    mu, sd, sd_i = float(F.mean()), float(F.std()), float(I.std())
+    level = mu + z * sd
+    freq = (F >= level).mean(axis=1)
+    p_dir = float(freq.mean())
+    se_bin = math.sqrt(p_dir * (1 - p_dir) / F.size)
+    se_rep = float(freq.std(ddof=1) / math.sqrt(R))
+    lv = torch.tensor([level], dtype=torch.float64, device="cuda")
+    k = z / sd_i
+    arms = []
+    for centred, eps in ((False, 0.0002), (False, EPS), (False, 0.02), (True, EPS), (True, 0.02)):
+        ps, anc = [], []
+        for r in range(R):
+            d = replica(k, eps, centred, 200 + r)
+            p = torch.zeros(1, dtype=torch.float64, device="cuda")
+            L.gktl_probability(k, d["logR"], d["integ"], d["maxima"], lv, float(t_a), float(t_a), p)
+            ps.append(float(p[0]))
+            anc.append(d["ancestors"])
+        ps = np.array(ps)
+        se = float(ps.std(ddof=1) / math.sqrt(R))
+        arms.append({"coefficients": "centred alpha_n - 1/2" if centred else "uniform [0, 1) (printed)", "eps": eps,
+                     "P_mean": float(ps.mean()), "P_median": float(np.median(ps)), "standard_error": se,
+                     "ratio_to_direct": float(ps.mean()) / p_dir if p_dir > 0 else None,
+                     "standard_errors_from_direct": (float(ps.mean()) - p_dir) / math.sqrt(se ** 2 + se_bin ** 2),
+                     "distinct_ancestors_mean": float(np.mean(anc)), "per_replica": ps.tolist()})
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "GKTL estimate of P(F_T >= mean + 2 std) against direct sampling, by App. D perturbation",
+        "value": arms[-2]["ratio_to_direct"], "unit": "ratio to direct sampling (centred, eps 0.002)",
+        "higher_is_better": None, "n_gpus": 1, "steps": R, "warmup": 0, "data": "synthetic", "dtype": "f32",
+        "seconds": seconds,
+        "config": {"workload": f"open channel of Sec. 2, N={n} trajectories of {nx}x{ny}, spin-up {spin} steps, "
+                               f"T_a=T={t_a} steps, cloning every {period} steps, k sigma_I = {z:g}",
+                   "replicas_per_arm": R, "F_T_mean": mu, "F_T_std": sd, "sigma_I": sd_i, "level": level},
+        "direct": {"P": p_dir, "standard_error_binomial": se_bin, "standard_error_replicas": se_rep,
+                   "trajectories": int(F.size)},
+        "gktl": arms}))
 
 
 # ---------------------------------------------------------------- CNN
@@ -1342,7 +1438,7 @@ def main():
     ap.add_argument("--clones", type=int, default=0,
                     help="ensemble size (default: the workload's; smaller only for profiling captures)")
     ap.add_argument("--workload", default="gktl", choices=sorted(WORKLOADS) + ["cnn", "return-time", "precision-report", "ams-branch", "ams-run", "ams-estimate",
-                                              "perturb-check", "long-run-precision"])
+                                              "perturb-check", "long-run-precision", "perturbation-bias"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--collision", default=None, choices=["bgk", "cm"],
                     help="BGK or the central-moment collision (default: central moments for the open "
@@ -1357,6 +1453,8 @@ def main():
     ap.add_argument("--rt-snapshots", type=int, default=100000,
                     help="return-time workload: flow states the learned score is trained on")
     ap.add_argument("--rt-epochs", type=int, default=20, help="return-time workload: training epochs")
+    ap.add_argument("--perturbation", default="printed", choices=["printed", "centred"],
+                    help="return-time workload: App. D coefficients uniform in [0, 1) as printed, or centred")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()
@@ -1378,6 +1476,8 @@ def main():
         run_ams_run(args)
     elif args.workload == "perturb-check":
         run_perturb_check(args)
+    elif args.workload == "perturbation-bias":
+        run_perturbation_bias(args)
     else:
         run_ours(args)
 

@@ -181,7 +181,8 @@ int lbm_ensemble_set_snapshots_from_checkpoint(lbm_ensemble* e, int32_t n_s, con
  * time and drag history, perturbed by eq. (perturb_pop),
  *   f <- (f + eps sum_n alpha_n f^(n)) * M / (M + eps sum_n alpha_n M^(n)),
  * M the fluid mass, alpha_n uniform from Philox4x64-10 counter (4, iter, s, n),
- * key (seed, 0).  A parent must keep its own slot (parent_dev[p] == p), as
+ * key (seed, 0), minus 1/2 in the centred mode (lbm_ensemble_set_perturbation).
+ * A parent must keep its own slot (parent_dev[p] == p), as
  * gktl_select guarantees.  eps = 0 copies exactly.  Needs the snapshot bank
  * when eps != 0.  A parent index outside [0, N) (a rejected selection writes
  * -1) leaves that slot unchanged and is reported as LBM_ERR_NONFINITE by the
@@ -206,6 +207,17 @@ int lbm_ensemble_branch(lbm_ensemble* e, int32_t dst, int32_t src, int32_t t_b, 
  * snapshot bank.  Waits.  Errors: LBM_ERR_ARG, LBM_ERR_STATE. */
 int lbm_ensemble_perturb(lbm_ensemble* e, int32_t n, const int32_t* clones, double eps, uint64_t seed,
                          uint64_t iter);
+
+/* The coefficients alpha_n of every App. D perturbation of the ensemble
+ * (cloning, branching, lbm_ensemble_perturb).  mode 0 (the default): uniform in
+ * [0, 1), as eq. (perturb_pop) prints them.  Since they are positive, each
+ * application then moves the state about eps sum_n alpha_n / 2 ~ 1% of the way
+ * towards the mean of the bank's snapshots, which carries weaker fluctuations;
+ * GKTL copies the trajectories that carry the tail again and again, and its
+ * estimate of a tail probability falls with eps.  mode 1 (centred): alpha_n - 1/2,
+ * uniform in [-1/2, 1/2): the same random directions with no mean pull.
+ * Kept by lbm_ensemble_save.  Errors: LBM_ERR_ARG. */
+int lbm_ensemble_set_perturbation(lbm_ensemble* e, int32_t mode);
 
 /* Observables of the square after every step (Sec. 2.1 eq. drag_approx, Sec.
  * 3.2 eq. avg_shear_def), recorded from the next step on while enabled, from
@@ -250,7 +262,8 @@ int lbm_ensemble_set_populations(lbm_ensemble* e, int32_t clone, const double* h
  * lbm_ensemble_load overwrites ensemble e with a state written by
  * lbm_ensemble_save.  e must have been created with the same configuration
  * (every lbm_config field equal) and clone count, and with observables enabled
- * exactly when the saved ensemble had them; its seed becomes the saved one.
+ * exactly when the saved ensemble had them; its seed and perturbation mode
+ * become the saved ones.
  * An attached learned score is not part of the state: attach it after loading
  * (LBM_ERR_STATE otherwise).  The loaded ensemble continues bit for bit as the
  * saved one would have.  Waits.  Errors: LBM_ERR_ARG (not a saved state,

@@ -226,10 +226,14 @@ def solid_mask(c: Cfg) -> np.ndarray:
     return m
 
 
-def perturb_alphas(seed, it, slot, n_s):
+def perturb_alphas(seed, it, slot, n_s, centred=False):
+    """App. D coefficients alpha_n, uniform in [0, 1) from the counter
+    (4, iter, slot, n); centred=True subtracts 1/2 (the centred reading of the
+    perturbation: the same random combination of snapshots with no mean pull
+    towards them)"""
     a = np.zeros(n_s)
     lib().orc_perturb_alphas(seed, it, slot, n_s, _ptr(a))
-    return a
+    return a - 0.5 if centred else a
 
 
 def perturb(c: Cfg, f, snaps, alpha, eps):

@@ -98,6 +98,7 @@ struct lbm_ensemble {
     int32_t* flag_dev;        // [0]: nonzero once a drag value was not finite; [1]: scratch int
     // App. D snapshot bank
     void* snaps;
+    int32_t perturb_mode;     // coefficients alpha_n: 0 uniform in [0, 1) (App. D); 1 centred, minus 1/2
     double* snap_mass;        // [n_snapshots]
     int32_t n_snaps_set;
     // AMS checkpoints every ckpt_stride steps: [N][n_ckpt] states

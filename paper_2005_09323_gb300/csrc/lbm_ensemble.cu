@@ -299,14 +299,16 @@ constexpr int32_t kAllInPlace = -2;
 // App. D: slot s with parent p != s (or s == inplace, or every listed slot
 // with inplace == kAllInPlace) becomes
 //   f_s = (f_p + eps sum_n alpha_n f^(n)) * M_p / (M_p + eps sum_n alpha_n M^(n))
-// on fluid nodes, written in the shifted variable g = f - w.
+// on fluid nodes, written in the shifted variable g = f - w.  alpha_n is the
+// counter-based uniform in [0, 1) minus alpha_shift: 0 for the printed form,
+// 1/2 for the centred coefficients (lbm_ensemble_set_perturbation).
 template <int S>
 __global__ void perturb_kernel(void* buf0, void* buf1, const int32_t* parity, const int32_t* parent, int32_t n_clones,
                                int32_t* flag, int32_t inplace, const int32_t* slots,
                                int64_t clone_stride, int64_t plane, int32_t pitch, int32_t nx, int32_t ny,
                                Solids sol, const void* snaps, int32_t n_s,
                                const double* snap_mass, const double* mass, double eps, uint64_t seed, uint64_t iter,
-                               float scale, float inv_scale)
+                               double alpha_shift, float scale, float inv_scale)
 {
     using T = typename Codec<S>::T;
     const int s = slots ? slots[blockIdx.y] : (int)blockIdx.y;
@@ -322,7 +324,7 @@ __global__ void perturb_kernel(void* buf0, void* buf1, const int32_t* parity, co
         double lin = 0.0;
         for (int k = 0; k < n_s; ++k) {
             const u64x4 r = philox(kStreamPerturb, iter, (uint64_t)s, (uint64_t)k, seed, 0u);
-            const double a = unit_double(r.v[0]);
+            const double a = unit_double(r.v[0]) - alpha_shift;
             alpha_eps[k] = (float)(eps * a);
             lin += eps * a * snap_mass[k];
         }
@@ -786,8 +788,8 @@ int run_perturb(lbm_ensemble* e, const int32_t* parent_dev, int32_t inplace, dou
         dim3 grid(bx, slots ? n_slots : e->n);
         perturb_kernel<S><<<grid, 256, 0, e->stream>>>(
             e->buf[0], e->buf[1], e->parity_dev, parent_dev, e->n, e->flag_dev, inplace, slots, e->clone_stride, e->plane, e->pitch, e->cfg.nx,
-            e->cfg.ny, sol, e->snaps, n_s, e->snap_mass, e->mass_dev, eps, seed, iter, e->scale,
-            e->inv_scale);
+            e->cfg.ny, sol, e->snaps, n_s, e->snap_mass, e->mass_dev, eps, seed, iter,
+            e->perturb_mode ? 0.5 : 0.0, e->scale, e->inv_scale);
         count_launches(1);
         LBM_CUDA(cudaGetLastError());
         return LBM_OK;
@@ -863,6 +865,7 @@ int lbm_ensemble_create(const lbm_config* cfg, int32_t n_clones, uint64_t seed, 
     e->scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : c.shift_exp);
     e->inv_scale = (float)std::ldexp(1.0, c.storage == kFP32 ? 0 : -c.shift_exp);
     e->variant = default_variant(c.storage);
+    e->perturb_mode = 0;
     e->variant_small = default_variant_small(c.storage, c.open_x != 0);
     e->use_graphs = true;
     e->batch_cap = kBatchCap;
@@ -1241,6 +1244,14 @@ int lbm_ensemble_perturb(lbm_ensemble* e, int32_t n, const int32_t* clones, doub
     rc = run_perturb(e, e->all_dev, kAllInPlace, eps, seed, iter, e->list_dev, n);
     if (rc) return rc;
     LBM_CUDA(cudaStreamSynchronize(e->stream));
+    return LBM_OK;
+}
+
+int lbm_ensemble_set_perturbation(lbm_ensemble* e, int32_t mode)
+{
+    if (!e) return fail(LBM_ERR_ARG, "null ensemble");
+    if (mode != 0 && mode != 1) return fail(LBM_ERR_ARG, "perturbation mode must be 0 (App. D) or 1 (centred)");
+    e->perturb_mode = mode;
     return LBM_OK;
 }
 

@@ -13,6 +13,7 @@
 //   double obs[N][tmax][4]             only with observables enabled
 //   snapshots [n_snaps][clone_bytes], double snap_mass[n_snaps]
 //   checkpoints [N][n_ck][clone_bytes] n_ck = min(n_ckpt, tmax / stride + 1)
+// The header also carries the perturbation mode (lbm_ensemble_set_perturbation).
 // Host byte order; the header carries a magic, a version and the total size.
 #include <algorithm>
 #include <cstring>
@@ -32,7 +33,7 @@ struct SaveHeader {
     uint64_t total_bytes, seed, clone_bytes;
     double cfg_d[kCfgDoubles];  // the configuration, field by field (lbm_config has padding)
     int32_t n, elem_bytes, pitch, tmax;
-    int32_t observe, n_snaps, n_ck, reserved;
+    int32_t observe, n_snaps, n_ck, perturb_mode;
     int32_t cfg_i[kCfgInts];
 };
 static_assert(sizeof(SaveHeader) == 216, "saved-state header layout");
@@ -107,6 +108,7 @@ int lbm_ensemble_save(lbm_ensemble* e, void* dst, uint64_t capacity, uint64_t* b
     h.observe = e->observe ? 1 : 0;
     h.n_snaps = e->n_snaps_set;
     h.n_ck = l.n_ck;
+    h.perturb_mode = e->perturb_mode;
     char* p = static_cast<char*>(dst);
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;
@@ -164,7 +166,7 @@ int lbm_ensemble_load(lbm_ensemble* e, const void* src, uint64_t bytes)
         return fail(LBM_ERR_ARG, "lbm_ensemble_load: enable or disable observables as in the saved ensemble");
     if (e->cnn) return fail(LBM_ERR_STATE, "lbm_ensemble_load: attach the learned score after loading");
     if (h.tmax < 0 || h.tmax > e->cfg.max_steps || h.n_snaps < 0 || h.n_snaps > e->cfg.n_snapshots ||
-        h.n_ck != checkpoints_saved(e, h.tmax))
+        h.n_ck != checkpoints_saved(e, h.tmax) || (h.perturb_mode != 0 && h.perturb_mode != 1))
         return fail(LBM_ERR_ARG, "lbm_ensemble_load: inconsistent saved header");
     const Layout l = layout(cb, h.n, h.tmax, h.observe != 0, h.n_snaps, h.n_ck);
     if (l.total != bytes) return fail(LBM_ERR_ARG, "lbm_ensemble_load: inconsistent saved header");
@@ -215,6 +217,7 @@ int lbm_ensemble_load(lbm_ensemble* e, const void* src, uint64_t bytes)
     e->parity_host = par;
     e->n_snaps_set = h.n_snaps;
     e->seed = h.seed;
+    e->perturb_mode = h.perturb_mode;
     e->score_window = 0;  // trailing means are recomputed by lbm_ensemble_scores
     return LBM_OK;
 }

@@ -37,6 +37,7 @@ EXPORTS = [
     "lbm_ensemble_score_history", "lbm_surrogate_dataset", "lbm_ensemble_set_snapshots_from_checkpoint",
     "lbm_selftest_bounded_wait", "lbm_ensemble_perturb", "lbm_ensemble_set_observables",
     "lbm_ensemble_observables", "lbm_ensemble_save", "lbm_ensemble_load",
+    "lbm_ensemble_set_perturbation",
 ]
 
 
@@ -125,6 +126,7 @@ def lib():
             "lbm_ensemble_set_populations": ([p, i32, p], C.c_int),
             "lbm_ensemble_save": ([p, p, u64, p], C.c_int),
             "lbm_ensemble_load": ([p, p, u64], C.c_int),
+            "lbm_ensemble_set_perturbation": ([p, i32], C.c_int),
             "lbm_ensemble_autotune": ([p, p], C.c_int),
             "lbm_ensemble_set_variant": ([p, i32], C.c_int),
             "lbm_step_variant_info": ([i32, p, p, p], C.c_int),
@@ -235,6 +237,11 @@ def lbm_ensemble_time(e, n: int) -> np.ndarray:
     t = np.zeros(n, dtype=np.int32)
     _check(lib().lbm_ensemble_time(e, _host(t)))
     return t
+
+
+def lbm_ensemble_set_perturbation(e, centred: bool):
+    """App. D coefficients: uniform in [0, 1) (False, as printed) or centred (True)"""
+    _check(lib().lbm_ensemble_set_perturbation(e, 1 if centred else 0))
 
 
 def lbm_ensemble_perturb(e, clones, eps: float, seed: int, it: int):

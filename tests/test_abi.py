@@ -54,6 +54,7 @@ def test_host_argument_checks_need_no_gpu(L):
     n = C.c_uint64(7)
     assert lib.lbm_ensemble_save(None, None, 0, C.byref(n)) == L.LBM_ERR_ARG
     assert lib.lbm_ensemble_load(None, b"LBMRUN", 6) == L.LBM_ERR_ARG
+    assert lib.lbm_ensemble_set_perturbation(None, 1) == L.LBM_ERR_ARG
 
 
 def test_variant_table(L):

@@ -330,6 +330,33 @@ def test_clone_exact_copy_and_perturbation(L, orc):
         assert np.array_equal(e.pops(3), before[2])  # kept its own slot (a copy of 2 since the first call)
 
 
+def test_centred_perturbation_matches_oracle(L, orc):
+    """the centred App. D coefficients (alpha_n - 1/2, lbm_ensemble_set_perturbation):
+    a cloned slot equals the oracle's perturbation with the centred coefficients
+    of the same counters, keeps the parent's mass, and differs from the printed
+    form; switching back restores the printed form"""
+    kw = dict(RAGGED, max_steps=100, n_snapshots=3)
+    oc = oracle_cfg(orc, kw)
+    with Ens(L, 5, seed=2, **kw) as e:
+        L.lbm_ensemble_step(e.h, 20)
+        L.lbm_ensemble_set_snapshots(e.h, [4, 2, 0])
+        at20 = {c: orc.run(oc, orc.init(oc, 2, c, 0.01), 20)[0] for c in (0, 2, 4)}
+        snaps = np.stack([at20[4], at20[2], at20[0]])
+        L.lbm_ensemble_set_perturbation(e.h, True)
+        L.lbm_ensemble_clone(e.h, torch.tensor([0, 4, 2, 3, 4], dtype=torch.int32, device="cuda"), 0.002, 77, 5)
+        ref = orc.perturb(oc, at20[4], snaps, orc.perturb_alphas(77, 5, 1, 3, centred=True), 0.002)
+        printed = orc.perturb(oc, at20[4], snaps, orc.perturb_alphas(77, 5, 1, 3), 0.002)
+        got = e.pops(1)
+        assert rel(got, ref) < 1e-6
+        assert rel(got, printed) > 5e-6
+        assert abs(orc.moments(oc, got)[0] - orc.moments(oc, at20[4])[0]) / orc.moments(oc, at20[4])[0] < 1e-6
+        L.lbm_ensemble_set_perturbation(e.h, False)
+        L.lbm_ensemble_clone(e.h, torch.tensor([0, 1, 2, 4, 4], dtype=torch.int32, device="cuda"), 0.002, 77, 5)
+        ref3 = orc.perturb(oc, at20[4], snaps, orc.perturb_alphas(77, 5, 3, 3), 0.002)
+        assert rel(e.pops(3), ref3) < 1e-6
+        assert L.lib().lbm_ensemble_set_perturbation(e.h, 2) == L.LBM_ERR_ARG
+
+
 def test_clone_with_a_rejected_parent(L):
     """a parent index outside [0, N) (a rejected selection writes -1) leaves its
     slot unchanged while the other slots are cloned, and the next synchronising

@@ -1,10 +1,10 @@
 """Run resume through the C ABI: lbm_ensemble_save writes an ensemble's run
 state to host bytes and lbm_ensemble_load reads it into a fresh ensemble of
 the same configuration, which then continues bit for bit as the saved one
-does - populations, drag history, observables, the App. D snapshot bank (a
-perturbed branch after the load) and the AMS checkpoints (a branch to a time
-before the save).  Loads that do not fit the ensemble are rejected and leave
-it unchanged."""
+does - populations, drag history, observables, the App. D snapshot bank and
+perturbation mode (a perturbed branch after the load) and the AMS checkpoints
+(a branch to a time before the save).  Loads that do not fit the ensemble are
+rejected and leave it unchanged."""
 import numpy as np
 import pytest
 import torch
@@ -55,11 +55,13 @@ def same_state(L, a, b, t):
     assert np.array_equal(a.drag(0, t), b.drag(0, t))
 
 
-def run_history(L, e, observe):
+def run_history(L, e, observe, centred):
     """steps, an App. D snapshot bank, a cloning step and a perturbed AMS branch:
-    the pieces of state a resumed run needs"""
+    the pieces of state a resumed run needs (with the printed or the centred
+    perturbation coefficients)"""
     if observe:
         L.lbm_ensemble_set_observables(e.h, True)
+    L.lbm_ensemble_set_perturbation(e.h, centred)
     L.lbm_ensemble_step(e.h, 90)
     L.lbm_ensemble_set_snapshots(e.h, [0, 2, 3])
     parent = torch.tensor([0, 0, 2, 1], dtype=torch.int32, device="cuda")
@@ -69,13 +71,15 @@ def run_history(L, e, observe):
     L.lbm_ensemble_step_clones(e.h, 60, [3])
 
 
-@pytest.mark.parametrize("kw,storage,observe", [(PERIODIC, "fp32", False), (PERIODIC, "fp16", False),
-                                                (PERIODIC, "bf16", True), (OPEN, "fp32", True)],
-                         ids=["periodic-fp32", "periodic-fp16", "periodic-bf16-observables", "open-cm-fp32"])
-def test_loaded_ensemble_continues_bitwise(L, kw, storage, observe):
+@pytest.mark.parametrize("kw,storage,observe,centred", [(PERIODIC, "fp32", False, False),
+                                                        (PERIODIC, "fp16", False, False),
+                                                        (PERIODIC, "bf16", True, False), (OPEN, "fp32", True, True)],
+                         ids=["periodic-fp32", "periodic-fp16", "periodic-bf16-observables",
+                              "open-cm-fp32-centred-perturbation"])
+def test_loaded_ensemble_continues_bitwise(L, kw, storage, observe, centred):
     kw = dict(kw, storage=storage)
     with Ens(L, 4, seed=3, **kw) as a:
-        run_history(L, a, observe)
+        run_history(L, a, observe, centred)
         state = L.lbm_ensemble_save(a.h)
         with Ens(L, 4, seed=99, **kw) as b:
             if observe:

@@ -239,3 +239,30 @@ def test_perturbation_preserves_mass(orc):
     lin = f + 0.002 * np.tensordot(alpha, snaps, axes=1)
     scale = m0 / lin[:, fluid].sum()
     assert np.abs(g[:, fluid] - scale * lin[:, fluid]).max() < 1e-15
+
+
+def test_centred_perturbation_has_no_mean_pull(orc):
+    """Reading 24 (App. D): with the coefficients as eq. (perturb_pop) prints
+    them (uniform in [0, 1)) the mass-rescaled perturbation moves a state on
+    average by eps/2 sum_n (f^(n) - f M^(n)/M), towards the snapshots, to first
+    order in eps; with centred coefficients (alpha_n - 1/2) the mean
+    displacement vanishes.  Averaged over 4000 draws of the counter-based
+    coefficients, against the first-order expansion written out here."""
+    nx, ny = 32, 12
+    c = orc.cfg(nx, ny, obstacle=si.channel(nx, ny, 4), tau=0.6, gx=1e-5)
+    f = orc.init(c, 1, 0, 0.05)
+    snaps = np.stack([orc.init(c, 2, k, 0.05) for k in range(10)])
+    eps, K = 0.002, 4000
+    fluid = ~orc.solid_mask(c)
+    m0 = orc.moments(c, f)[0]
+    ms = np.array([orc.moments(c, sn)[0] for sn in snaps])
+    pull = 0.5 * eps * (snaps.sum(axis=0) - f * ms.sum() / m0)
+    mean = {False: np.zeros_like(f), True: np.zeros_like(f)}
+    for it in range(K):
+        for centred in (False, True):
+            a = orc.perturb_alphas(5, it, 1, 10, centred=centred)
+            assert np.all((a >= -0.5) & (a < 0.5)) if centred else np.all((a >= 0) & (a < 1))
+            mean[centred] += (orc.perturb(c, f, snaps, a, eps) - f) / K
+    scale = np.abs(pull[:, fluid]).max()
+    assert np.abs(mean[False] - pull)[:, fluid].max() < 0.05 * scale
+    assert np.abs(mean[True])[:, fluid].max() < 0.05 * scale
