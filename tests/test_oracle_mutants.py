@@ -94,6 +94,7 @@ PINS = {
     "GKTL with a potential against direct sampling": gktl_potential,
     "GKTL potential bookkeeping": T_est.test_gktl_potential_bookkeeping,
     "AMS with another score against direct sampling": T_est.test_ams_estimator_with_another_score_matches_direct_sampling,
+    "centred perturbation has no mean pull": T_lbm.test_centred_perturbation_has_no_mean_pull,
 }
 
 # (case, file, text in the oracle, planted text, pin that must fail)
@@ -344,6 +345,7 @@ ESTIMATOR_PINS = {
     "GKTL with a potential against direct sampling": gktl_potential,
     "AMS estimator hand computed": T_est.test_ams_probability_hand_computed,
     "AMS with another score against direct sampling": T_est.test_ams_estimator_with_another_score_matches_direct_sampling,
+    "centred perturbation has no mean pull": T_lbm.test_centred_perturbation_has_no_mean_pull,
 }
 
 ESTIMATOR_MUTANTS = [
@@ -372,6 +374,10 @@ ESTIMATOR_MUTANTS = [
     ("AMS killed records left out",
      "p += np.sum(np.exp(lw_k) * (mx_k >= level)) / n", "p += 0.0",
      "AMS with another score against direct sampling"),
+    ("centred App. D coefficients left uncentred",
+     "return a - 0.5 if centred else a", "return a if centred else a", "centred perturbation has no mean pull"),
+    ("centred App. D coefficients shifted by a quarter",
+     "return a - 0.5 if centred else a", "return a - 0.25 if centred else a", "centred perturbation has no mean pull"),
 ]
 
 
