@@ -357,6 +357,23 @@ def test_centred_perturbation_matches_oracle(L, orc):
         assert L.lib().lbm_ensemble_set_perturbation(e.h, 2) == L.LBM_ERR_ARG
 
 
+def test_step_timing_and_launch_count(L):
+    """the tracing hooks: the library's launch counter grows with a step call,
+    and with timing on, CUDA events around each step chunk on the ensemble's
+    stream report a positive time and the number of timed steps, which reset
+    clears"""
+    with Ens(L, 2, seed=1, **dict(RAGGED, max_steps=100)) as e:
+        n0 = L.lbm_launch_count()
+        L.lbm_ensemble_step(e.h, 10)
+        assert L.lbm_launch_count() - n0 >= 2  # fused steps and the drag finalisation
+        assert L.lbm_ensemble_kernel_time(e.h) == (0.0, 0)  # timing is off by default
+        L.lbm_ensemble_set_timing(e.h, True)
+        L.lbm_ensemble_step(e.h, 30)
+        ms, n = L.lbm_ensemble_kernel_time(e.h, reset=True)
+        assert n == 30 and ms > 0.0
+        assert L.lbm_ensemble_kernel_time(e.h) == (0.0, 0)
+
+
 def test_clone_with_a_rejected_parent(L):
     """a parent index outside [0, N) (a rejected selection writes -1) leaves its
     slot unchanged while the other slots are cloned, and the next synchronising
