@@ -1340,7 +1340,8 @@ def run_perturb_check(args):
     perturbations and the observables included.  Reported: GLUPS, and the
     statistics of each half over the timed steps, with the KS distance between
     the halves against that between the two quarters of the unperturbed half
-    (a null reference of the same sample size)."""
+    (a null reference of the same sample size).  --perturbation centred
+    perturbs with centred App. D coefficients."""
     import numpy as np
     import torch
 
@@ -1356,6 +1357,7 @@ def run_perturb_check(args):
                    storage=args.storage, collision=w["collision"], **channel_kwargs(w))
     e = L.lbm_ensemble_create(cfg, n, 31, stream)
     L.lbm_ensemble_set_observables(e, True)
+    L.lbm_ensemble_set_perturbation(e, args.perturbation == "centred")
     state = {"it": 0}
     bank = [n // 2 + i * (n // 2) // N_SNAP for i in range(N_SNAP)]  # unperturbed trajectories
 
@@ -1418,7 +1420,7 @@ def run_perturb_check(args):
                                f"observables every step; {CHECK_STEPS} steps per step",
                    "storage": args.storage, "collision": w["collision"]},
         "perturbation_check": {
-            "window_steps": [t0, t1], "period_steps": period, "eps": EPS,
+            "window_steps": [t0, t1], "period_steps": period, "eps": EPS, "coefficients": args.perturbation,
             "perturbed": stats(pert), "unperturbed": stats(unpert),
             "ks_drag_perturbed_vs_unperturbed": ks_distance(drag[pert], drag[unpert]),
             "ks_drag_null_unperturbed_quarters": ks_distance(drag[unpert[:q]], drag[unpert[q:]]),
@@ -1454,7 +1456,8 @@ def main():
                     help="return-time workload: flow states the learned score is trained on")
     ap.add_argument("--rt-epochs", type=int, default=20, help="return-time workload: training epochs")
     ap.add_argument("--perturbation", default="printed", choices=["printed", "centred"],
-                    help="return-time workload: App. D coefficients uniform in [0, 1) as printed, or centred")
+                    help="return-time and perturb-check workloads: App. D coefficients uniform in [0, 1) as "
+                         "printed, or centred")
     ap.add_argument("--ams-window", type=int, default=1,
                     help="ams-run: score window in steps (1 = the instantaneous drag)")
     args = ap.parse_args()
