@@ -213,9 +213,10 @@ int lbm_ensemble_perturb(lbm_ensemble* e, int32_t n, const int32_t* clones, doub
  * [0, 1), as eq. (perturb_pop) prints them.  Since they are positive, each
  * application then moves the state about eps sum_n alpha_n / 2 ~ 1% of the way
  * towards the mean of the bank's snapshots, which carries weaker fluctuations;
- * GKTL copies the trajectories that carry the tail again and again, and its
- * estimate of a tail probability falls with eps.  mode 1 (centred): alpha_n - 1/2,
- * uniform in [-1/2, 1/2): the same random directions with no mean pull.
+ * GKTL copies the trajectories that carry the tail again and again, and on the
+ * open channel of Sec. 2 its estimate of a tail probability was measured to
+ * fall as eps grows.  mode 1 (centred): alpha_n - 1/2, uniform in [-1/2, 1/2):
+ * the same random directions with no mean pull.
  * Kept by lbm_ensemble_save.  Errors: LBM_ERR_ARG. */
 int lbm_ensemble_set_perturbation(lbm_ensemble* e, int32_t mode);
 
