@@ -724,7 +724,11 @@ size_t tc_smem_bytes(const TcShape& sh) { return 1024 + kWBytes + (size_t)kTcSta
 // share; the epilogue writes the CTA's partial sums in the layout of the
 // fixed-order cross-CTA reduction ([co][304], bias at column 288).
 constexpr int kWgThreads = 192;             // TMA producer, MMA issuer, 4 epilogue warps
-constexpr int kWgBand = 16;                 // output rows per work unit
+// output rows per work unit: a unit loads its band's input rows plus one halo
+// row on each side, and the CTAs take whole units, so the slowest CTA's input
+// rows are ceil(units / CTAs) x (kWgBand + 2); at 64 rows x 2 halves x 256
+// images on 152 CTAs that is 7 x 34 = 238 for 32 against 14 x 18 = 252 for 16
+constexpr int kWgBand = 32;
 constexpr int kWgInSlots = 3;               // input-row ring (5 slots measured the same)
 constexpr int kWgDySlots = 6;               // output-gradient ring (plus two mirror slots)
 constexpr uint32_t kWgCopy = 128 * 64;      // one 128-pixel row of 32 channels
